@@ -1,0 +1,276 @@
+"""Seeded synthetic inputs for the screening path.
+
+This module holds the input recipes only: images, templates, planted copies,
+the scale lists and the tolerance rationals.  It contains none of the
+screening arithmetic (no tables, no window sums, no features, no bounds), so
+the CPU oracle and the CUDA path can both read its outputs without sharing any
+of the method's code.
+
+Workload shapes follow the paper's experiments (640x480 .. 1280x960 images,
+32^2 .. 128^2 templates, scale range [0.5, 2], Table 1 of Sec. 6) scaled to the
+five benchmark configurations below.  The paper's own datasets (MIT CSAIL,
+VTB) are not available; these seeded blob fields stand in for them.
+
+Image recipe (all configurations):
+  float field = 128 + sum of 64 Gaussian blobs, centre uniform over the image,
+  sigma ~ U[4, 40] px, amplitude ~ U[-96, 96] (each blob evaluated inside
+  +-4 sigma); planted copies are written into the float field; then integer
+  noise ~ U{-8..8} is added, the result rounded and clipped to 0..255.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from fractions import Fraction
+
+import numpy as np
+
+F_MEAN, F_VAR, F_GRAD = 1, 2, 4
+
+BASE_SEED = 1000
+
+
+def rng_for(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def blob_field(rng: np.random.Generator, H: int, W: int, n_blobs: int = 64,
+               sigma=(4.0, 40.0), amp=(-96.0, 96.0), base: float = 128.0) -> np.ndarray:
+    """Float64 H x W field: base + n_blobs isotropic Gaussian bumps."""
+    f = np.full((H, W), base, dtype=np.float64)
+    cy = rng.uniform(0, H, n_blobs)
+    cx = rng.uniform(0, W, n_blobs)
+    sg = rng.uniform(sigma[0], sigma[1], n_blobs)
+    am = rng.uniform(amp[0], amp[1], n_blobs)
+    for k in range(n_blobs):
+        rad = 4.0 * sg[k]
+        y0 = max(0, int(math.floor(cy[k] - rad)))
+        y1 = min(H, int(math.ceil(cy[k] + rad)) + 1)
+        x0 = max(0, int(math.floor(cx[k] - rad)))
+        x1 = min(W, int(math.ceil(cx[k] + rad)) + 1)
+        if y0 >= y1 or x0 >= x1:
+            continue
+        yy = np.arange(y0, y1, dtype=np.float64)[:, None] - cy[k]
+        xx = np.arange(x0, x1, dtype=np.float64)[None, :] - cx[k]
+        f[y0:y1, x0:x1] += am[k] * np.exp(-(yy * yy + xx * xx) / (2.0 * sg[k] * sg[k]))
+    return f
+
+
+def quantize_with_noise(f: np.ndarray, rng: np.random.Generator, noise: int = 8) -> np.ndarray:
+    """Add integer noise U{-noise..noise}, round half away from zero, clip to uint8."""
+    nz = rng.integers(-noise, noise + 1, size=f.shape, dtype=np.int16)
+    g = np.floor(f + nz + 0.5)
+    return np.clip(g, 0, 255).astype(np.uint8)
+
+
+def bilinear(src: np.ndarray, ys: np.ndarray, xs: np.ndarray) -> np.ndarray:
+    """Bilinear sample of a 2-D float array at fractional (ys, xs) inside [0, n-1]."""
+    h, w = src.shape
+    y0 = np.clip(np.floor(ys).astype(np.int64), 0, h - 2)
+    x0 = np.clip(np.floor(xs).astype(np.int64), 0, w - 2)
+    fy = ys - y0
+    fx = xs - x0
+    a = src[y0, x0]
+    b = src[y0, x0 + 1]
+    c = src[y0 + 1, x0]
+    d = src[y0 + 1, x0 + 1]
+    return (a * (1 - fx) + b * fx) * (1 - fy) + (c * (1 - fx) + d * fx) * fy
+
+
+def plain_std(a: np.ndarray) -> float:
+    """Plain population std of all pixels of a patch (template texture floor)."""
+    return float(np.asarray(a, dtype=np.float64).std())
+
+
+def paste(field_: np.ndarray, tmpl: np.ndarray, cy: float, cx: float, theta: float,
+          scale: float, gain: float = 1.0) -> None:
+    """Write a rotated, scaled copy of `tmpl` into the float field, in place.
+
+    The template point q maps to image point c_I + scale * Rot(theta) (q - c_T),
+    with c_T = (r + 1/2, r + 1/2) the template's star centre and c_I = (cy, cx).
+    Every image pixel whose pre-image falls inside the template square takes the
+    bilinear sample of the template there (times `gain`).
+    """
+    side = tmpl.shape[0]
+    r = (side - 1) // 2
+    cT = r + 0.5
+    H, W = field_.shape
+    ext = scale * (side + 2) * math.sqrt(2.0) / 2.0 + 2.0
+    y0 = max(0, int(math.floor(cy - ext)))
+    y1 = min(H, int(math.ceil(cy + ext)) + 1)
+    x0 = max(0, int(math.floor(cx - ext)))
+    x1 = min(W, int(math.ceil(cx + ext)) + 1)
+    py, px = np.mgrid[y0:y1, x0:x1].astype(np.float64)
+    dy = (py - cy) / scale
+    dx = (px - cx) / scale
+    c, s = math.cos(theta), math.sin(theta)
+    # inverse rotation Rot(-theta) applied to (dy, dx)
+    qy = cT + c * dy + s * dx
+    qx = cT - s * dy + c * dx
+    inside = (qy >= 0) & (qy <= side - 1) & (qx >= 0) & (qx <= side - 1)
+    vals = bilinear(tmpl.astype(np.float64), qy[inside], qx[inside])
+    sub = field_[y0:y1, x0:x1]
+    sub[inside] = gain * vals
+
+
+def geometric_scales(s_min: float, s_max: float, count: int) -> list[float]:
+    if count == 1:
+        return [s_min]
+    return [s_min * (s_max / s_min) ** (i / (count - 1)) for i in range(count)]
+
+
+def radii_for(r: int, scales: list[float]) -> list[int]:
+    """Star radius per scale, R_s = floor(r * s + 1/2)."""
+    return [int(math.floor(r * s + 0.5)) for s in scales]
+
+
+def t_min_for(r: int, scales: list[float]) -> int:
+    """Smallest template central radius of a scale band, ceil(r / lambda)."""
+    if len(scales) < 2:
+        return r
+    lam = scales[1] / scales[0]
+    return int(math.ceil(r / lam - 1e-9))
+
+
+@dataclass
+class Tolerances:
+    mean_rel: Fraction = Fraction(1, 20)
+    std_rel: Fraction = Fraction(1, 10)
+    grad_rel: Fraction = Fraction(1, 10)
+    grad_abs: Fraction = Fraction(4, 1)
+
+
+@dataclass
+class Workload:
+    name: str
+    image: np.ndarray                 # uint8 H x W
+    template: np.ndarray              # uint8 (2r+1) x (2r+1)
+    r: int
+    radii: list[int]
+    t_min: int
+    features: int
+    tol: Tolerances
+    sum_bits: int
+    sq_bits: int
+    planted: tuple[int, int]          # candidate (y*, x*) of the true match
+    s_true: float
+    theta: float
+    scales: list[float] = field(default_factory=list)
+    distractors: list[tuple[int, int, float]] = field(default_factory=list)
+
+
+def _pick_site(rng, H, W, side, margin, floor_std, img, tries=400):
+    best = None
+    for _ in range(tries):
+        y0 = int(rng.integers(margin, H - margin - side))
+        x0 = int(rng.integers(margin, W - margin - side))
+        sd = plain_std(img[y0:y0 + side, x0:x0 + side])
+        if best is None or sd > best[0]:
+            best = (sd, y0, x0)
+        if sd >= floor_std:
+            return y0, x0
+    return best[1], best[2]
+
+
+def config1(seed: int = BASE_SEED + 0) -> Workload:
+    """512x512 image, 33x33 rotated template cut from the image, R = 16, 1 scale."""
+    rng = rng_for(seed)
+    H = W = 512
+    img = quantize_with_noise(blob_field(rng, H, W), rng)
+    big, r = 49, 16
+    side = 2 * r + 1
+    off = (big - side) // 2
+    # texture floor on the central 33x33 part of the cut
+    y0, x0 = _pick_site(rng, H, W, big, 8, 16.0, img)
+    while plain_std(img[y0 + off:y0 + off + side, x0 + off:x0 + off + side]) < 16.0:
+        y0, x0 = _pick_site(rng, H, W, big, 8, 16.0, img)
+    patch = img[y0:y0 + big, x0:x0 + big].astype(np.float64)
+    theta = float(rng.uniform(0.0, 2.0 * math.pi))
+    c = (big - 1) / 2.0 + 0.5          # 24.5: star centre of candidate (24, 24)
+    ii, jj = np.mgrid[0:side, 0:side].astype(np.float64)
+    dy = ii + off - c
+    dx = jj + off - c
+    cs, sn = math.cos(theta), math.sin(theta)
+    sy = c + cs * dy - sn * dx
+    sx = c + sn * dy + cs * dx
+    tm = np.clip(np.floor(bilinear(patch, sy, sx) + 0.5), 0, 255).astype(np.uint8)
+    return Workload(name="512x512, R=16, 1 scale, mean+var, u32/u32",
+                    image=img, template=tm, r=r, radii=[16], t_min=16,
+                    features=F_MEAN | F_VAR, tol=Tolerances(), sum_bits=32, sq_bits=32,
+                    planted=(y0 + 24, x0 + 24), s_true=1.0, theta=theta, scales=[1.0])
+
+
+def _template_from_source(rng, r, src_side=512):
+    side = 2 * r + 1
+    src = quantize_with_noise(blob_field(rng, src_side, src_side), rng)
+    y0, x0 = _pick_site(rng, src_side, src_side, side, 4, 16.0, src)
+    return src[y0:y0 + side, x0:x0 + side].copy()
+
+
+def _planted_workload(name, seed, H, r, s_min, s_max, n_scales, sum_bits, sq_bits,
+                      n_distractors=0, distractor_gain=0.03, true_range=(0.5, 2.0)) -> Workload:
+    rng = rng_for(seed)
+    W = H
+    fld = blob_field(rng, H, W)
+    trng = rng_for(seed + 7919)
+    tmpl = _template_from_source(trng, r)
+    s_true = float(math.exp(rng.uniform(math.log(true_range[0]), math.log(true_range[1]))))
+    theta = float(rng.uniform(0.0, 2.0 * math.pi))
+    side = 2 * r + 1
+    margin = int(math.ceil(s_max * side)) + 8
+    ys = int(rng.integers(margin, H - margin))
+    xs = int(rng.integers(margin, W - margin))
+    distractors = []
+    for _ in range(n_distractors):
+        dy = int(rng.integers(margin, H - margin))
+        dx = int(rng.integers(margin, W - margin))
+        g = 1.0 + (distractor_gain if rng.integers(0, 2) else -distractor_gain)
+        paste(fld, tmpl, dy + 0.5, dx + 0.5, float(rng.uniform(0, 2 * math.pi)),
+              float(math.exp(rng.uniform(math.log(0.5), math.log(2.0)))), gain=g)
+        distractors.append((dy, dx, g))
+    # the true copy is pasted last so no distractor overwrites it
+    paste(fld, tmpl, ys + 0.5, xs + 0.5, theta, s_true)
+    img = quantize_with_noise(fld, rng)
+    scales = geometric_scales(s_min, s_max, n_scales)
+    return Workload(name=name, image=img, template=tmpl, r=r, radii=radii_for(r, scales),
+                    t_min=t_min_for(r, scales), features=F_MEAN | F_VAR | F_GRAD,
+                    tol=Tolerances(), sum_bits=sum_bits, sq_bits=sq_bits,
+                    planted=(ys, xs), s_true=s_true, theta=theta, scales=scales,
+                    distractors=distractors)
+
+
+def config2(seed: int = BASE_SEED + 1) -> Workload:
+    """4096x4096, planted r=48 template, 8 scales 0.5..2, 3 features, u32 sum / u64 sum^2."""
+    return _planted_workload("4096x4096, r=48, 8 scales 0.5-2, 3 features, u32/u64",
+                             seed, 4096, 48, 0.5, 2.0, 8, 32, 64)
+
+
+def config3(seed: int = BASE_SEED + 2) -> Workload:
+    """8192x8192, r=64, 16 scales 0.35..2.8, 3 features, u64/u64, 8 distractors (+-3%)."""
+    return _planted_workload("8192x8192, r=64, 16 scales 0.35-2.8, 3 features, u64/u64",
+                             seed, 8192, 64, 0.35, 2.8, 16, 64, 64, n_distractors=8)
+
+
+def small_planted(seed: int, H: int = 384, r: int = 20, n_scales: int = 4,
+                  s_min: float = 0.6, s_max: float = 1.6, sum_bits: int = 32,
+                  sq_bits: int = 64) -> Workload:
+    """Reduced planted workload (config 2's recipe at a size the oracle finishes fast)."""
+    return _planted_workload(f"{H}x{H}, r={r}, {n_scales} scales", seed, H, r, s_min, s_max,
+                             n_scales, sum_bits, sq_bits, true_range=(s_min, s_max))
+
+
+def random_image(seed: int, H: int, W: int, kind: str = "uniform") -> np.ndarray:
+    """Small seeded test images: uniform noise, constant, ramps, blobs."""
+    rng = rng_for(seed)
+    if kind == "uniform":
+        return rng.integers(0, 256, size=(H, W), dtype=np.uint8)
+    if kind == "blobs":
+        return quantize_with_noise(blob_field(rng, H, W, n_blobs=max(4, H * W // 4096)), rng)
+    if kind == "max":
+        return np.full((H, W), 255, dtype=np.uint8)
+    if kind == "zero":
+        return np.zeros((H, W), dtype=np.uint8)
+    raise ValueError(kind)
+
+
+CONFIGS = {1: config1, 2: config2, 3: config3}
