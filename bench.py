@@ -1,0 +1,296 @@
+"""Benchmark of the screening hot path on GB300.
+
+One step = the whole path on one synthetic 4096x4096 image (the single-large-
+image workload: 8 scales 0.5..2 of a radius-48 template, mean + variance +
+contrast, uint32 sum / uint64 sum^2 tables):
+  build_tables (upright + cone tables)  ->  screen_features (star features and
+  thresholds -> bitmask)  ->  compact_mask (bitmask -> sorted survivor list).
+`value` = candidate (position x scale) evaluations per second with the image
+already resident in HBM; `e2e` = the same metric through screen_host() with the
+image in pinned host memory and the count + list copied back every step.
+
+--impl reference times the CPU oracle (the slow plain implementation the GPU
+path is checked against) on the host cores instead.
+Under torchrun each rank screens its own image (weak scaling, no collective on
+the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "candidate (position x scale) evaluations/s"
+UNIT = "evals/s"
+
+
+def candidates(H, W, radii):
+    """Number of valid (scale, y, x) candidates: the star lies inside the image."""
+    tot = 0
+    for R in radii:
+        n = 0
+        while (2 * n + 1) ** 2 < 2 * R * R:
+            n += 1
+        h = R
+        ylo, yhi = max(n, h) - 1, H - 1 - max(n, h)
+        xlo, xhi = max(n, h) - 1, min(W - 1 - n, W - h)
+        if yhi >= ylo and xhi >= xlo:
+            tot += (yhi - ylo + 1) * (xhi - xlo + 1)
+    return tot
+
+
+def per_scale_bytes(H, W, n_scales, sum_bits, sq_bits):
+    """Algorithmic bytes of one screening launch under the per-scale model of
+    Algorithm 1: every scale pass reads the four tables once and writes its mask."""
+    tables = ((H + 1) * (W + 1) + (H + 1) * (W + 2)) * (sum_bits + sq_bits) // 8
+    mask = n_scales * H * ((W + 31) // 32) * 4
+    return n_scales * tables + mask
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                self.out = ""
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            f = [v.strip() for v in line.split(",")]
+            if len(f) >= 8:
+                rows.append(f)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[4 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+                if any(r[2].replace(".", "").isdigit() for r in rows) else None}
+
+
+def measured_peak_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def oracle_baseline(wl, max_rows=None):
+    """CPU oracle (tables + screen) on the host cores; returns (evals/s, sample, cores, seconds)."""
+    import oracle
+    img = wl.image if max_rows is None else wl.image[:max_rows]
+    H, W = img.shape
+    t0 = time.perf_counter()
+    oracle.screen_workload(img, wl.template, wl.r, wl.t_min, wl.radii, wl.features, wl.tol)
+    dt = time.perf_counter() - t0
+    n = candidates(H, W, wl.radii)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return n / dt, f"{H}x{W} rows of the same image, all {len(wl.radii)} scales, tables + screen", cores, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import synth
+    wl = synth.config2()
+    rows = 512
+    for _ in range(args.warmup):
+        oracle_baseline(wl, rows)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        v, sample, cores, dt = oracle_baseline(wl, rows)
+        vals.append(v)
+        secs.append(dt)
+    value = len(secs) * candidates(rows, wl.image.shape[1], wl.radii) / sum(secs)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic", "config": config_dict(wl),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def config_dict(wl):
+    return {"workload": "single large image: 4096x4096 u8, planted r=48 template, 8 scales 0.5-2, "
+                        "mean+variance+contrast, u32 sum / u64 sum^2 tables",
+            "image": f"{wl.image.shape[0]}x{wl.image.shape[1]}", "radii": wl.radii, "t_min": wl.t_min,
+            "features": "mean+var+contrast", "tables": f"u{wl.sum_bits} sum / u{wl.sq_bits} sum^2",
+            "l2": "flushed between timed steps (256 MiB write); tables 403 MB > L2",
+            "candidates_per_step": candidates(*wl.image.shape, wl.radii)}
+
+
+def run_ours(args):
+    import torch
+    import synth
+    import paper_1707_05647_gb300 as scr
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    wl = synth.config2(synth.BASE_SEED + 1 + 1000 * rank)
+    H, W = wl.image.shape
+    S = len(wl.radii)
+    ncand = candidates(H, W, wl.radii)
+    ctx = scr.screen_init(local, 0)
+    p = scr.Params(wl.radii, wl.features, wl.tol.mean_rel, wl.tol.std_rel, wl.tol.grad_rel, wl.tol.grad_abs)
+    tm = scr.template_features(ctx, wl.template, wl.r, wl.t_min, wl.features)
+    stream = torch.cuda.current_stream()
+    img = torch.from_numpy(wl.image).cuda()
+    mask = torch.empty(scr.mask_words(S, H, W), dtype=torch.int32, device="cuda")
+    cap = 1 << 22
+    lst = torch.empty(cap, dtype=torch.int64, device="cuda")
+    count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step(evs=None):
+        tb = scr.build_tables(ctx, img, wl.sum_bits, wl.sq_bits, stream)
+        if evs:
+            evs[0].record(stream)
+        scr.screen_features(ctx, tb, tm, p, mask, stream)
+        if evs:
+            evs[1].record(stream)
+        scr.compact_mask(ctx, mask, S, H, W, lst, count, stream)
+        scr.tables_release(ctx, tb)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = scr.screen_stats(ctx)["kernel_launches"]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step(kev[k])
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = scr.screen_stats(ctx)["kernel_launches"] - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    k3_ms = [a.elapsed_time(b) for a, b in kev]
+    total_s = sum(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * ncand * args.steps / total_s
+    n_surv = int(count.item())
+
+    # end to end through the C ABI with host buffers
+    img_host = torch.from_numpy(wl.image).pin_memory()
+    lst_host = torch.empty(cap, dtype=torch.int64).pin_memory()
+    for _ in range(2):
+        scr.screen_host(ctx, img_host.numpy(), wl.sum_bits, wl.sq_bits, tm, p, lst_host.numpy())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_steps = max(3, min(args.steps, 10))
+    for _ in range(e2e_steps):
+        n_e2e, _ = scr.screen_host(ctx, img_host.numpy(), wl.sum_bits, wl.sq_bits, tm, p, lst_host.numpy())
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": ncand / e2e_s, "unit": UNIT, "h2d_bytes_per_step": H * W,
+           "d2h_bytes_per_step": 8 + 8 * min(n_e2e, cap)}
+
+    if rank == 0:
+        peak, src = measured_peak_gbs()
+        k3 = statistics.mean(k3_ms) / 1e3
+        alg = per_scale_bytes(H, W, S, wl.sum_bits, wl.sq_bits)
+        achieved = alg / k3 / 1e9
+        prof = os.path.join(ROOT, "profiles", "traffic_screen_4096.json")
+        traffic = None
+        if os.path.exists(prof):
+            try:
+                traffic = json.load(open(prof)).get("dram_bytes_per_launch")
+            except Exception:
+                traffic = None
+        cpu = None
+        if not args.no_cpu_baseline:
+            v, sample, cores, dt = oracle_baseline(wl)
+            cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                   "seconds": round(dt, 2)}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32+u64", "data": "synthetic",
+            "config": config_dict(wl),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_source": src,
+                         "kernel": "k_screen", "model": "Algorithm 1 per-scale: 4 tables read once per "
+                         "scale + mask written", "kernel_ms": 1e3 * k3},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk.summary(), "survivors": n_surv,
+            "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
+        }
+        print(json.dumps(line), flush=True)
+    scr.template_release(ctx, tm)
+    scr.screen_shutdown(ctx)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

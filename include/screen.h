@@ -1,0 +1,228 @@
+/*
+ * screen.h -- C ABI of the GPU screening library (libscreen.so).
+ *
+ * The library implements the data-parallel hot path of the rotation- and
+ * scale-invariant template-matching pre-screener of Liu, Shu and Wu,
+ * "Fast Screening Algorithm for Rotation and Scale Invariant Template
+ * Matching" (arXiv 1707.05647):
+ *
+ *   a1  upright summed-area tables of I and I^2        (Sec. 3, Eq. T_1, S_sigma)
+ *   a2  45-degree ("cone") summed-area tables of I, I^2 (Sec. 4, triangular map)
+ *   a3  octagonal-star features at every position and scale by table-corner
+ *       lookups: mean, variance, inner-star-vs-ring contrast
+ *                                         (Sec. 3 Eq. S_1; Sec. 4 Eq. S_os; Sec. 5)
+ *   a4  threshold against the template's feature bounds -> candidate bitmask
+ *                                         (Sec. 5, Algorithm 1)
+ *   a5  compaction of the bitmask -> ascending list of surviving candidates
+ *                                         (Sec. 5, Algorithm 1, R <- R u {P})
+ *
+ * Every result is an exact integer: the tables are exact modulo 2^w, window sums
+ * are exact whenever they are below 2^32 (checked per scale), and the threshold
+ * tests compare integers against bounds computed from exact rationals, so the
+ * mask and the list are bit-exact against any correct implementation.
+ *
+ * Geometry (definitions used throughout):
+ *   Image I: H x W uint8, row y (slow index), column x.
+ *   Star radius R >= 1: diamond half-diagonal h = R, square half-side n = the
+ *   unique integer with (2n-1)^2 < 2R^2 < (2n+1)^2; star = square (rows
+ *   y-n+1..y+n, columns x-n+1..x+n) superposed on the diamond (pixels with
+ *   |x'-x| < h and y-h+|x'-x| < y' <= y+h-|x'-x|); sums pooled over area
+ *   A = 4n^2 + 2h^2.  Inner star: radius floor(R/2).  A candidate (y, x) is
+ *   valid when its whole star lies inside the image.
+ *
+ * Conventions:
+ *   - Every entry point returns SCR_OK (0) or a negative SCR_E* code; the
+ *     message of the last failure on the calling thread is screen_last_error().
+ *     No C++ exception crosses the ABI.  On failure, outputs are unspecified.
+ *   - "_dev" pointers are CUDA device pointers on the context's device; they are
+ *     owned by the caller unless stated otherwise.  "_host" pointers are host
+ *     memory.  Handles (scr_tables, scr_tmpl) are owned by the library and freed
+ *     by their *_release call; their device memory counts against the context's
+ *     HBM budget.
+ *   - A stream argument is a cudaStream_t (NULL = the legacy default stream).
+ *     Calls are stream-ordered and return without waiting unless documented.
+ *   - A context may be used from several host threads; calls are serialised
+ *     on the context's host-side state.
+ *   - There is no CPU fallback: if the device is missing or the kernels cannot
+ *     run, calls fail with SCR_ECUDA.
+ */
+#ifndef SCREEN_H
+#define SCREEN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct scr_ctx scr_ctx;
+typedef struct scr_tables scr_tables;
+typedef struct scr_tmpl scr_tmpl;
+typedef void *scr_stream; /* cudaStream_t */
+
+enum {
+    SCR_OK = 0,
+    SCR_EINVAL = -1,      /* bad argument (sizes, null pointers, radii, tolerances) */
+    SCR_ENOMEM = -2,      /* device or host allocation failed */
+    SCR_EBUDGET = -3,     /* the allocation would exceed the context's HBM budget */
+    SCR_ECUDA = -4,       /* a CUDA runtime call or kernel launch failed */
+    SCR_ETIMEOUT = -5,    /* reserved: a bounded device-side wait gave up */
+    SCR_EOVERFLOW = -6,   /* more survivors than list capacity (mask still complete) */
+    SCR_EUNSUPPORTED = -8 /* valid request outside what this build implements */
+};
+
+enum { SCR_F_MEAN = 1, SCR_F_VAR = 2, SCR_F_GRAD = 4 };
+
+/* Exact rational num/den, den > 0, |num| and den <= 2^20. */
+typedef struct {
+    int64_t num, den;
+} scr_rat;
+
+/* Screening parameters.
+ *   radii[n_scales]: star radius R_s per scale (host array, 1 <= n_scales <= 32,
+ *                    2 <= R_s <= 181 so that every window sum of I^2 is below 2^32).
+ *   features:        OR of SCR_F_*; a candidate must pass every enabled test.
+ *   mean_rel tm, std_rel ts, grad_rel tg (each in [0, 1)), grad_abs dg (>= 0):
+ *     mean     S/A in [(1-tm) mu_lo, (1+tm) mu_hi]
+ *     std      sqrt(V)/A in [(1-ts) sd_lo, (1+ts) sd_hi]         (compared squared)
+ *     contrast N/(A_in A_ring) in [g_lo - tg|g_lo| - dg, g_hi + tg|g_hi| + dg]
+ *   where [mu_lo, mu_hi], ... are the template's feature hulls over its central
+ *   radii t in [t_min, r] (Sec. 5, Eq. F_n; see template_features). */
+typedef struct {
+    int32_t n_scales;
+    const int32_t *radii;
+    uint32_t features;
+    scr_rat mean_rel, std_rel, grad_rel, grad_abs;
+} scr_params;
+
+/* Inclusive integer bounds of one scale (INT64_MIN / INT64_MAX when the
+ * feature is disabled).  S = pooled star sum, V = A*Q - S^2, N = S_in*A_ring -
+ * S_ring*A_in. */
+typedef struct {
+    int64_t S_lo, S_hi, V_lo, V_hi, N_lo, N_hi;
+} scr_bounds;
+
+typedef struct {
+    uint64_t kernel_launches; /* kernels launched by this context so far */
+    uint64_t bytes_in_use;    /* live device bytes charged to the budget */
+    uint64_t bytes_peak;      /* high-water mark of bytes_in_use */
+    uint64_t budget;          /* the HBM budget given to screen_init */
+} scr_stats;
+
+/* ---- context ---------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the device
+ * memory the context may hold at once (0 = no cap).  Fails with SCR_ECUDA if
+ * the device is absent or not an sm_103 part the kernels were built for. */
+int screen_init(scr_ctx **ctx, int device, uint64_t hbm_budget_bytes);
+
+/* Wait for the context's work, free every handle it still owns, destroy it. */
+void screen_shutdown(scr_ctx *ctx);
+
+/* Message of the last failed call on this host thread ("" if none).  The
+ * pointer stays valid until the thread's next failing call. */
+const char *screen_last_error(void);
+
+int screen_stats(const scr_ctx *ctx, scr_stats *out);
+
+/* ---- a1, a2: tables --------------------------------------------------- */
+
+/* Build the four tables of the H x W image at img_dev (row pitch `pitch` bytes,
+ * pitch >= W), 1 <= H, W <= 65535.
+ *   which 0: L1, upright table of I,   (H+1) x (W+1), L[a][b] = sum_{y<a,x<b} I(y,x)
+ *   which 1: L2, upright table of I^2, (H+1) x (W+1)
+ *   which 2: T1, cone table of I,      (H+1) x (W+2), T[a][b] = cone(a-1, b-1),
+ *            cone(r,c) = sum of I(y,x) over y <= r, |x-c| <= r-y (inside the image)
+ *   which 3: T2, cone table of I^2
+ * L1 and T1 are stored with sum_bits, L2 and T2 with sq_bits (32 or 64); values
+ * are exact modulo 2^bits.  (Sec. 3, Eq. T_1: built in linear time by row and
+ * column passes; Sec. 4: the rotated table by two diagonal passes.)
+ * Stream-ordered on `stream`; the image must stay valid until the work ends. */
+int build_tables(scr_ctx *ctx, const uint8_t *img_dev, int32_t H, int32_t W, int64_t pitch,
+                 int32_t sum_bits, int32_t sq_bits, scr_stream stream, scr_tables **out);
+
+/* Borrowed device view of table `which` (0..3).  Layout: 32-bit words; element
+ * (a, b) of a 32-bit table is word a*pitch + b + offset of *dev_ptr, where
+ * *dev_ptr points at word 0; a 64-bit table is two such planes, the low 32 bits
+ * at *dev_ptr and the high 32 bits plane_stride words further.  rows x cols is
+ * the logical size; pitch and plane_stride are in 32-bit words. */
+int tables_view(const scr_tables *t, int which, const void **dev_ptr, int64_t *rows,
+                int64_t *cols, int64_t *pitch, int64_t *offset, int64_t *plane_stride,
+                int32_t *bits);
+
+/* Copy table `which` into a dense rows x cols uint64 host array (values zero-
+ * extended from 32-bit tables).  Synchronous. */
+int tables_copy_to_host(scr_ctx *ctx, const scr_tables *t, int which, uint64_t *dst_host);
+
+void tables_release(scr_ctx *ctx, scr_tables *t);
+
+/* ---- template side (Sec. 5, Eq. F_n) ----------------------------------- */
+
+/* Features of a (2r+1) x (2r+1) template (host array, row-major, side = 2r+1,
+ * 2 <= r <= 181): star sums S_t, Q_t, S_in,t of the central star of radius t at
+ * the template centre (r, r) for every t in [t_min, r] (t_min >= 2 when
+ * SCR_F_GRAD is used), and the hulls of mean, variance and contrast over t.
+ * Computed on the device with the same table kernels; synchronous. */
+int template_features(scr_ctx *ctx, const uint8_t *tmpl_host, int32_t side, int32_t r,
+                      int32_t t_min, uint32_t features, scr_tmpl **out);
+
+/* out[0..2] = S_t, Q_t, S_in,t of central radius t in [t_min, r]. */
+int template_sums(const scr_tmpl *tm, int32_t t, int64_t out[3]);
+
+void template_release(scr_ctx *ctx, scr_tmpl *tm);
+
+/* Per-scale inclusive integer bounds (host computation, exact 128-bit
+ * rationals).  out has p->n_scales entries. */
+int screen_bounds(const scr_tmpl *tm, const scr_params *p, scr_bounds *out);
+
+/* ---- a3, a4: features and threshold ------------------------------------ */
+
+/* Evaluate every candidate (s, y, x) and write the bitmask
+ *   mask_dev[(s*H + y)*ceil(W/32) + x/32] bit (x % 32) = candidate survives,
+ * zero for invalid positions.  mask_words must be >= n_scales*H*ceil(W/32).
+ * Stream-ordered. */
+int screen_features(scr_ctx *ctx, const scr_tables *t, const scr_tmpl *tm, const scr_params *p,
+                    uint32_t *mask_dev, uint64_t mask_words, scr_stream stream);
+
+/* ---- a5: compaction ----------------------------------------------------- */
+
+/* Ascending keys (s << 48) | (y << 24) | x of the set bits of a mask laid out
+ * as above, written to list_dev[0 .. min(count, list_cap)); the exact count is
+ * written to *count_dev (device).  list_dev may be NULL when list_cap == 0.
+ * Stream-ordered. */
+int compact_mask(scr_ctx *ctx, const uint32_t *mask_dev, int32_t n_scales, int32_t H, int32_t W,
+                 uint64_t *list_dev, uint64_t list_cap, uint64_t *count_dev, scr_stream stream);
+
+/* ---- a3..a5 together ----------------------------------------------------- */
+
+/* screen_features + compact_mask, then wait for the stream and return the
+ * survivor count in *n_survivors (host).  Returns SCR_EOVERFLOW when the count
+ * exceeds list_cap (the mask is complete and the list holds the first list_cap
+ * keys). */
+int screen_positions(scr_ctx *ctx, const scr_tables *t, const scr_tmpl *tm, const scr_params *p,
+                     uint32_t *mask_dev, uint64_t mask_words, uint64_t *list_dev,
+                     uint64_t list_cap, uint64_t *n_survivors, scr_stream stream);
+
+/* As screen_positions, but the count goes to *count_dev and nothing waits. */
+int screen_positions_async(scr_ctx *ctx, const scr_tables *t, const scr_tmpl *tm,
+                           const scr_params *p, uint32_t *mask_dev, uint64_t mask_words,
+                           uint64_t *list_dev, uint64_t list_cap, uint64_t *count_dev,
+                           scr_stream stream);
+
+/* ---- whole path from host memory ----------------------------------------- */
+
+/* End-to-end call for host-resident data: copy the image (host, pitch bytes per
+ * row) to the device, build its tables, screen it against the template, copy
+ * the count and the first list_cap keys back to list_host.  Device buffers come
+ * from the context's pool and are returned before the call ends.  Synchronous;
+ * returns SCR_EOVERFLOW like screen_positions. */
+int screen_host(scr_ctx *ctx, const uint8_t *img_host, int32_t H, int32_t W, int64_t pitch,
+                int32_t sum_bits, int32_t sq_bits, const scr_tmpl *tm, const scr_params *p,
+                uint64_t *list_host, uint64_t list_cap, uint64_t *n_survivors,
+                scr_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCREEN_H */

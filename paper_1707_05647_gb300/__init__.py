@@ -1,0 +1,268 @@
+"""Python binding of libscreen.so -- argument marshalling only.
+
+Every function here has the name of the C-ABI entry point it calls (see
+include/screen.h); all computation happens in the library's CUDA kernels.
+PyTorch supplies device memory (tensors) and streams.  There is no CPU
+fallback: importing works without a GPU, but every call that needs the device
+raises ScreenError when the library or the device is unavailable.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from fractions import Fraction
+
+import numpy as np
+
+from . import _build
+
+F_MEAN, F_VAR, F_GRAD = 1, 2, 4
+SCR_OK, SCR_EINVAL, SCR_ENOMEM, SCR_EBUDGET, SCR_ECUDA, SCR_ETIMEOUT, SCR_EOVERFLOW = 0, -1, -2, -3, -4, -5, -6
+SCR_EUNSUPPORTED = -8
+MAX_SCALES = 32
+
+
+class ScreenError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class _Rat(ctypes.Structure):
+    _fields_ = [("num", ctypes.c_int64), ("den", ctypes.c_int64)]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("n_scales", ctypes.c_int32), ("radii", ctypes.POINTER(ctypes.c_int32)),
+                ("features", ctypes.c_uint32), ("mean_rel", _Rat), ("std_rel", _Rat),
+                ("grad_rel", _Rat), ("grad_abs", _Rat)]
+
+
+class _Bounds(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("S_lo", "S_hi", "V_lo", "V_hi", "N_lo", "N_hi")]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("kernel_launches", "bytes_in_use", "bytes_peak", "budget")]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libscreen.so (building it first if asked and stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ScreenError(SCR_ECUDA, f"libscreen.so missing at {_build.LIB}; run __graft_entry__.build()")
+    L = ctypes.CDLL(_build.LIB)
+    vp, i32, i64, u32, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "screen_init": ([pp, ctypes.c_int, u64], ctypes.c_int),
+        "screen_shutdown": ([vp], None),
+        "screen_last_error": ([], ctypes.c_char_p),
+        "screen_stats": ([vp, ctypes.POINTER(_Stats)], ctypes.c_int),
+        "build_tables": ([vp, vp, i32, i32, i64, i32, i32, vp, pp], ctypes.c_int),
+        "tables_view": ([vp, ctypes.c_int, pp] + [ctypes.POINTER(i64)] * 5 + [ctypes.POINTER(i32)], ctypes.c_int),
+        "tables_copy_to_host": ([vp, vp, ctypes.c_int, vp], ctypes.c_int),
+        "tables_release": ([vp, vp], None),
+        "template_features": ([vp, vp, i32, i32, i32, u32, pp], ctypes.c_int),
+        "template_sums": ([vp, i32, ctypes.POINTER(i64)], ctypes.c_int),
+        "template_release": ([vp, vp], None),
+        "screen_bounds": ([vp, ctypes.POINTER(_Params), ctypes.POINTER(_Bounds)], ctypes.c_int),
+        "screen_features": ([vp, vp, vp, ctypes.POINTER(_Params), vp, u64, vp], ctypes.c_int),
+        "compact_mask": ([vp, vp, i32, i32, i32, vp, u64, vp, vp], ctypes.c_int),
+        "screen_positions": ([vp, vp, vp, ctypes.POINTER(_Params), vp, u64, vp, u64, ctypes.POINTER(u64), vp],
+                             ctypes.c_int),
+        "screen_positions_async": ([vp, vp, vp, ctypes.POINTER(_Params), vp, u64, vp, u64, vp, vp], ctypes.c_int),
+        "screen_host": ([vp, vp, i32, i32, i64, i32, i32, vp, ctypes.POINTER(_Params), vp, u64,
+                         ctypes.POINTER(u64), vp], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    return ["screen_init", "screen_shutdown", "screen_last_error", "screen_stats", "build_tables",
+            "tables_view", "tables_copy_to_host", "tables_release", "template_features", "template_sums",
+            "template_release", "screen_bounds", "screen_features", "compact_mask", "screen_positions",
+            "screen_positions_async", "screen_host"]
+
+
+def _check(rc: int, allow=()):
+    if rc != SCR_OK and rc not in allow:
+        msg = load().screen_last_error()
+        raise ScreenError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    if t is None:
+        return ctypes.c_void_p(0)
+    if isinstance(t, np.ndarray):
+        return ctypes.c_void_p(t.ctypes.data)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _rat(v) -> _Rat:
+    f = Fraction(v)
+    return _Rat(f.numerator, f.denominator)
+
+
+class Params:
+    """scr_params: radii per scale, feature bits and the four tolerances."""
+
+    def __init__(self, radii, features, mean_rel=Fraction(1, 20), std_rel=Fraction(1, 10),
+                 grad_rel=Fraction(1, 10), grad_abs=Fraction(4)):
+        self.radii = np.ascontiguousarray(radii, dtype=np.int32)
+        self.c = _Params(len(self.radii), self.radii.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                         int(features), _rat(mean_rel), _rat(std_rel), _rat(grad_rel), _rat(grad_abs))
+
+    @property
+    def n_scales(self):
+        return len(self.radii)
+
+
+# ---- context ----------------------------------------------------------------
+
+def screen_init(device: int = 0, hbm_budget_bytes: int = 0) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    _check(load().screen_init(ctypes.byref(ctx), device, hbm_budget_bytes))
+    return ctx
+
+
+def screen_shutdown(ctx) -> None:
+    load().screen_shutdown(ctx)
+
+
+def screen_last_error() -> str:
+    return load().screen_last_error().decode()
+
+
+def screen_stats(ctx) -> dict:
+    s = _Stats()
+    _check(load().screen_stats(ctx, ctypes.byref(s)))
+    return {n: int(getattr(s, n)) for n, _ in _Stats._fields_}
+
+
+# ---- tables -----------------------------------------------------------------
+
+def build_tables(ctx, img, sum_bits: int = 32, sq_bits: int = 64, stream=None, H=None, W=None, pitch=None):
+    """img: 2-D uint8 CUDA tensor (row pitch from its stride)."""
+    if H is None:
+        H, W = img.shape
+        pitch = img.stride(0)
+    out = ctypes.c_void_p()
+    _check(load().build_tables(ctx, _ptr(img), H, W, pitch, sum_bits, sq_bits, _stream(stream), ctypes.byref(out)))
+    return out
+
+
+def tables_view(tables, which: int) -> dict:
+    p = ctypes.c_void_p()
+    v = [ctypes.c_int64() for _ in range(5)]
+    bits = ctypes.c_int32()
+    _check(load().tables_view(tables, which, ctypes.byref(p), *[ctypes.byref(x) for x in v], ctypes.byref(bits)))
+    return dict(ptr=p.value, rows=v[0].value, cols=v[1].value, pitch=v[2].value, offset=v[3].value,
+                plane_stride=v[4].value, bits=bits.value)
+
+
+def tables_copy_to_host(ctx, tables, which: int) -> np.ndarray:
+    v = tables_view(tables, which)
+    out = np.empty((v["rows"], v["cols"]), np.uint64)
+    _check(load().tables_copy_to_host(ctx, tables, which, _ptr(out)))
+    return out
+
+
+def tables_release(ctx, tables) -> None:
+    load().tables_release(ctx, tables)
+
+
+# ---- template ---------------------------------------------------------------
+
+def template_features(ctx, tmpl: np.ndarray, r: int, t_min: int, features: int):
+    tmpl = np.ascontiguousarray(tmpl, dtype=np.uint8)
+    out = ctypes.c_void_p()
+    _check(load().template_features(ctx, _ptr(tmpl), tmpl.shape[0], r, t_min, features, ctypes.byref(out)))
+    return out
+
+
+def template_sums(tm, t: int):
+    out = (ctypes.c_int64 * 3)()
+    _check(load().template_sums(tm, t, out))
+    return int(out[0]), int(out[1]), int(out[2])
+
+
+def template_release(ctx, tm) -> None:
+    load().template_release(ctx, tm)
+
+
+def screen_bounds(tm, params: Params) -> np.ndarray:
+    out = (_Bounds * params.n_scales)()
+    _check(load().screen_bounds(tm, ctypes.byref(params.c), out))
+    return np.array([[getattr(b, n) for n, _ in _Bounds._fields_] for b in out], np.int64)
+
+
+# ---- screening --------------------------------------------------------------
+
+def mask_words(n_scales: int, H: int, W: int) -> int:
+    return n_scales * H * ((W + 31) // 32)
+
+
+def screen_features(ctx, tables, tm, params: Params, mask, stream=None) -> None:
+    _check(load().screen_features(ctx, tables, tm, ctypes.byref(params.c), _ptr(mask), mask.numel(),
+                                  _stream(stream)))
+
+
+def compact_mask(ctx, mask, n_scales, H, W, lst, count, stream=None) -> None:
+    cap = 0 if lst is None else lst.numel()
+    _check(load().compact_mask(ctx, _ptr(mask), n_scales, H, W, _ptr(lst), cap, _ptr(count), _stream(stream)))
+
+
+def screen_positions(ctx, tables, tm, params: Params, mask, lst, stream=None) -> tuple[int, bool]:
+    """Returns (survivor count, overflowed)."""
+    n = ctypes.c_uint64()
+    cap = 0 if lst is None else lst.numel()
+    rc = _check(load().screen_positions(ctx, tables, tm, ctypes.byref(params.c), _ptr(mask), mask.numel(),
+                                        _ptr(lst), cap, ctypes.byref(n), _stream(stream)), allow=(SCR_EOVERFLOW,))
+    return int(n.value), rc == SCR_EOVERFLOW
+
+
+def screen_positions_async(ctx, tables, tm, params: Params, mask, lst, count, stream=None) -> None:
+    cap = 0 if lst is None else lst.numel()
+    _check(load().screen_positions_async(ctx, tables, tm, ctypes.byref(params.c), _ptr(mask), mask.numel(),
+                                         _ptr(lst), cap, _ptr(count), _stream(stream)))
+
+
+def screen_host(ctx, img: np.ndarray, sum_bits: int, sq_bits: int, tm, params: Params, lst: np.ndarray,
+                stream=None) -> tuple[int, bool]:
+    """img and lst are host arrays (pinned memory makes the copies asynchronous)."""
+    n = ctypes.c_uint64()
+    H, W = img.shape
+    rc = _check(load().screen_host(ctx, _ptr(img), H, W, img.strides[0], sum_bits, sq_bits, tm,
+                                   ctypes.byref(params.c), _ptr(lst), 0 if lst is None else lst.size,
+                                   ctypes.byref(n), _stream(stream)), allow=(SCR_EOVERFLOW,))
+    return int(n.value), rc == SCR_EOVERFLOW
+
+
+__all__ = [n for n in dir() if not n.startswith("_")]

@@ -1,0 +1,780 @@
+// Host side of the C ABI declared in include/screen.h: contexts, the device
+// memory pool with its HBM budget, table and template handles, the exact
+// bound computation, and the entry points that enqueue the kernels.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <new>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "screen.h"
+
+using namespace scr;
+
+typedef __int128 i128;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+static int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                     \
+    do {                                                                                   \
+        cudaError_t e__ = (expr);                                                          \
+        if (e__ != cudaSuccess)                                                            \
+            return fail(SCR_ECUDA, "%s: %s (%s)", #expr, cudaGetErrorName(e__),            \
+                        cudaGetErrorString(e__));                                          \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct scr_tables {
+    TableDesc t[4];
+    void *base = nullptr;
+    size_t bytes = 0;
+    int H = 0, W = 0;
+    cudaStream_t stream = nullptr;   // stream of the last use (frees are ordered on it)
+};
+
+struct scr_tmpl {
+    int r = 0, t_min = 0;
+    uint32_t features = 0;
+    std::vector<int64_t> S, Q, Si;   // index t - t_min
+    // hulls as exact rationals num/den (den > 0)
+    int64_t mu_lo_n = 0, mu_lo_d = 1, mu_hi_n = 0, mu_hi_d = 1;
+    int64_t v_lo_n = 0, v_lo_d = 1, v_hi_n = 0, v_hi_d = 1;
+    int64_t g_lo_n = 0, g_lo_d = 1, g_hi_n = 0, g_hi_d = 1;
+};
+
+struct scr_ctx {
+    int device = 0;
+    uint64_t budget = 0;
+    std::atomic<uint64_t> in_use{0}, peak{0}, launches{0};
+    cudaMemPool_t pool = nullptr;
+    std::mutex mu;
+    std::set<scr_tables *> tables;
+    std::set<scr_tmpl *> tmpls;
+    uint64_t *pinned = nullptr;      // 8-byte pinned slot for counts
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess)
+            prev = -1;
+        if (prev != dev)
+            ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev)
+            cudaSetDevice(prev);
+    }
+};
+
+int dev_alloc(scr_ctx *c, size_t bytes, cudaStream_t st, void **p) {
+    bytes = std::max<size_t>(bytes, 256);
+    const uint64_t now = c->in_use.fetch_add(bytes) + bytes;
+    if (c->budget && now > c->budget) {
+        c->in_use.fetch_sub(bytes);
+        return fail(SCR_EBUDGET, "allocation of %zu bytes exceeds the HBM budget (%llu in use, budget %llu)",
+                    bytes, (unsigned long long)(now - bytes), (unsigned long long)c->budget);
+    }
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, c->pool, st);
+    if (e != cudaSuccess) {
+        c->in_use.fetch_sub(bytes);
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? SCR_ENOMEM : SCR_ECUDA,
+                    "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    }
+    uint64_t pk = c->peak.load();
+    while (now > pk && !c->peak.compare_exchange_weak(pk, now)) {
+    }
+    return SCR_OK;
+}
+
+void dev_free(scr_ctx *c, void *p, size_t bytes, cudaStream_t st) {
+    if (!p)
+        return;
+    bytes = std::max<size_t>(bytes, 256);
+    cudaFreeAsync(p, st);
+    c->in_use.fetch_sub(bytes);
+}
+
+// A device buffer charged to the context and returned on scope exit
+// (stream-ordered on the stream it was taken on).
+struct Scoped {
+    scr_ctx *c;
+    void *p = nullptr;
+    size_t bytes = 0;
+    cudaStream_t st;
+    Scoped(scr_ctx *c_, cudaStream_t st_) : c(c_), st(st_) {}
+    int take(size_t b) {
+        bytes = b;
+        return dev_alloc(c, b, st, &p);
+    }
+    ~Scoped() { dev_free(c, p, bytes, st); }
+};
+
+int check_ctx(const scr_ctx *c) {
+    if (!c)
+        return fail(SCR_EINVAL, "null context");
+    return SCR_OK;
+}
+
+// (2n-1)^2 < 2R^2 < (2n+1)^2 via the integer square root of 2R^2.
+int64_t isqrt64(int64_t v) {
+    int64_t m = (int64_t)__builtin_sqrt((double)v);
+    while (m * m > v) --m;
+    while ((m + 1) * (m + 1) <= v) ++m;
+    return m;
+}
+
+struct Geo {
+    int n, h, ni, hi;
+    int64_t A, Ain, Aring;
+};
+
+Geo geometry(int R) {
+    Geo g;
+    g.n = square_half(R);
+    g.h = R;
+    g.hi = R / 2;
+    g.ni = square_half(g.hi);
+    g.A = 4 * (int64_t)g.n * g.n + 2 * (int64_t)g.h * g.h;
+    g.Ain = 4 * (int64_t)g.ni * g.ni + 2 * (int64_t)g.hi * g.hi;
+    g.Aring = g.A - g.Ain;
+    return g;
+}
+
+i128 floor_div(i128 a, i128 b) {   // b > 0
+    i128 q = a / b;
+    if ((a % b != 0) && (a < 0))
+        --q;
+    return q;
+}
+
+i128 ceil_div(i128 a, i128 b) {    // b > 0
+    i128 q = a / b;
+    if ((a % b != 0) && (a > 0))
+        ++q;
+    return q;
+}
+
+int64_t clamp64(i128 v) {
+    const i128 lo = (i128)INT64_MIN, hi = (i128)INT64_MAX;
+    return (int64_t)(v < lo ? lo : (v > hi ? hi : v));
+}
+
+int check_rat(const scr_rat &r, bool below_one, const char *name) {
+    const int64_t lim = (int64_t)1 << 20;
+    if (r.den <= 0 || r.den > lim || r.num < 0 || r.num > lim)
+        return fail(SCR_EINVAL, "%s = %lld/%lld: need 0 <= num <= 2^20, 0 < den <= 2^20", name,
+                    (long long)r.num, (long long)r.den);
+    if (below_one && r.num >= r.den)
+        return fail(SCR_EINVAL, "%s must be below 1", name);
+    return SCR_OK;
+}
+
+int validate_params(const scr_params *p) {
+    if (!p)
+        return fail(SCR_EINVAL, "null params");
+    if (p->n_scales < 1 || p->n_scales > kMaxScales || !p->radii)
+        return fail(SCR_EINVAL, "n_scales must be in [1, %d] with a radii array", kMaxScales);
+    if (p->features & ~7u)
+        return fail(SCR_EINVAL, "unknown feature bits 0x%x", p->features);
+    for (int s = 0; s < p->n_scales; ++s) {
+        const int R = p->radii[s];
+        if (R < 2 || R > 181)
+            return fail(SCR_EINVAL, "radius %d at scale %d outside [2, 181] (window sums of I^2 must stay below 2^32)", R, s);
+    }
+    int rc;
+    if ((rc = check_rat(p->mean_rel, true, "mean_rel")) || (rc = check_rat(p->std_rel, true, "std_rel")) ||
+        (rc = check_rat(p->grad_rel, true, "grad_rel")) || (rc = check_rat(p->grad_abs, false, "grad_abs")))
+        return rc;
+    return SCR_OK;
+}
+
+// Per-scale bounds from the template hulls (exact; see include/screen.h).
+void bounds_for(const scr_tmpl *tm, const scr_params *p, int R, scr_bounds *b) {
+    const Geo g = geometry(R);
+    b->S_lo = INT64_MIN;
+    b->S_hi = INT64_MAX;
+    b->V_lo = INT64_MIN;
+    b->V_hi = INT64_MAX;
+    b->N_lo = INT64_MIN;
+    b->N_hi = INT64_MAX;
+    if (p->features & SCR_F_MEAN) {
+        const i128 a = p->mean_rel.num, d = p->mean_rel.den;
+        b->S_lo = clamp64(ceil_div((d - a) * tm->mu_lo_n * g.A, d * tm->mu_lo_d));
+        b->S_hi = clamp64(floor_div((d + a) * tm->mu_hi_n * g.A, d * tm->mu_hi_d));
+    }
+    if (p->features & SCR_F_VAR) {
+        const i128 a = p->std_rel.num, d = p->std_rel.den;
+        const i128 A2 = (i128)g.A * g.A;
+        b->V_lo = clamp64(ceil_div((d - a) * (d - a) * tm->v_lo_n * A2, d * d * tm->v_lo_d));
+        b->V_hi = clamp64(floor_div((d + a) * (d + a) * tm->v_hi_n * A2, d * d * tm->v_hi_d));
+    }
+    if (p->features & SCR_F_GRAD) {
+        const i128 a = p->grad_rel.num, bb = p->grad_rel.den;
+        const i128 e = p->grad_abs.num, f = p->grad_abs.den;
+        const i128 D = (i128)g.Ain * g.Aring;
+        {
+            const i128 Nn = tm->g_lo_n, Nd = tm->g_lo_d;
+            const i128 absN = Nn < 0 ? -Nn : Nn;
+            const i128 num = Nn * bb * f - a * absN * f - e * bb * Nd;
+            b->N_lo = clamp64(ceil_div(num * D, bb * f * Nd));
+        }
+        {
+            const i128 Nn = tm->g_hi_n, Nd = tm->g_hi_d;
+            const i128 absN = Nn < 0 ? -Nn : Nn;
+            const i128 num = Nn * bb * f + a * absN * f + e * bb * Nd;
+            b->N_hi = clamp64(floor_div(num * D, bb * f * Nd));
+        }
+    }
+}
+
+int alloc_tables(scr_ctx *c, int H, int W, int sum_bits, int sq_bits, cudaStream_t st, scr_tables **out) {
+    auto *t = new (std::nothrow) scr_tables();
+    if (!t)
+        return fail(SCR_ENOMEM, "host allocation failed");
+    const int64_t pitch = table_pitch_words(W);
+    const int64_t rows = (int64_t)H + 1;
+    const int64_t plane = ((rows * pitch + 63) / 64) * 64;   // words, 256-byte multiple
+    const int bits[4] = {sum_bits, sq_bits, sum_bits, sq_bits};
+    const int64_t cols[4] = {(int64_t)W + 1, (int64_t)W + 1, (int64_t)W + 2, (int64_t)W + 2};
+    int64_t words = 0;
+    for (int k = 0; k < 4; ++k)
+        words += plane * (bits[k] / 32);
+    t->bytes = (size_t)words * 4;
+    int rc = dev_alloc(c, t->bytes, st, &t->base);
+    if (rc) {
+        delete t;
+        return rc;
+    }
+    uint32_t *p = (uint32_t *)t->base;
+    for (int k = 0; k < 4; ++k) {
+        TableDesc &d = t->t[k];
+        d.lo = p;
+        p += plane;
+        d.hi = nullptr;
+        if (bits[k] == 64) {
+            d.hi = p;
+            p += plane;
+        }
+        d.pitch = pitch;
+        d.rows = rows;
+        d.cols = cols[k];
+        d.bits = bits[k];
+    }
+    t->H = H;
+    t->W = W;
+    t->stream = st;
+    *out = t;
+    return SCR_OK;
+}
+
+int run_build(scr_ctx *c, const uint8_t *img, int H, int W, int64_t pitch, scr_tables *t, cudaStream_t st) {
+    Scoped scratch(c, st);
+    int rc = scratch.take(TableScratch::bytes(H, W, t->t[0].bits, t->t[1].bits));
+    if (rc)
+        return rc;
+    uint64_t n = 0;
+    cudaError_t e = launch_build_tables(img, H, W, pitch, t->t[0], t->t[1], t->t[2], t->t[3], scratch.p, st, &n);
+    c->launches += n;
+    CUDA_TRY(e);
+    return SCR_OK;
+}
+
+void free_tables(scr_ctx *c, scr_tables *t) {
+    dev_free(c, t->base, t->bytes, t->stream);
+    delete t;
+}
+
+int fill_screen_args(const scr_tables *t, const scr_tmpl *tm, const scr_params *p, ScreenArgs *a) {
+    memset(a, 0, sizeof *a);
+    a->L1 = t->t[0].lo;
+    a->L2 = t->t[1].lo;
+    a->T1 = t->t[2].lo;
+    a->T2 = t->t[3].lo;
+    a->pitchL = t->t[0].pitch;
+    a->pitchT = t->t[2].pitch;
+    a->H = t->H;
+    a->W = t->W;
+    a->Wwords = (t->W + 31) / 32;
+    a->n_scales = p->n_scales;
+    a->features = p->features;
+    for (int s = 0; s < p->n_scales; ++s) {
+        const int R = p->radii[s];
+        const Geo g = geometry(R);
+        ScaleParam &sp = a->sp[s];
+        sp.R = R;
+        sp.n = g.n;
+        sp.h = g.h;
+        sp.ni = g.ni;
+        sp.hi = g.hi;
+        sp.y_lo = std::max(g.n, g.h) - 1;
+        sp.y_hi = t->H - 1 - std::max(g.n, g.h);
+        sp.x_lo = std::max(g.n, g.h) - 1;
+        sp.x_hi = std::min(t->W - 1 - g.n, t->W - g.h);
+        sp.A = g.A;
+        sp.Ain = g.Ain;
+        sp.Aring = g.Aring;
+        scr_bounds b;
+        bounds_for(tm, p, R, &b);
+        sp.S_lo = b.S_lo;
+        sp.S_hi = b.S_hi;
+        sp.V_lo = b.V_lo;
+        sp.V_hi = b.V_hi;
+        sp.N_lo = b.N_lo;
+        sp.N_hi = b.N_hi;
+    }
+    return SCR_OK;
+}
+
+int check_screen_inputs(const scr_tables *t, const scr_tmpl *tm, const scr_params *p) {
+    if (!t || !tm)
+        return fail(SCR_EINVAL, "null tables or template");
+    int rc = validate_params(p);
+    if (rc)
+        return rc;
+    if ((p->features & SCR_F_GRAD) && !(tm->features & SCR_F_GRAD))
+        return fail(SCR_EINVAL, "template features were computed without SCR_F_GRAD");
+    return SCR_OK;
+}
+
+}  // namespace
+
+int scr::square_half(int R) {
+    const int64_t m = isqrt64(2 * (int64_t)R * R);
+    return (int)((m + 1) / 2);
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *screen_last_error(void) { return g_last_error.c_str(); }
+
+int screen_init(scr_ctx **ctx, int device, uint64_t hbm_budget_bytes) {
+    if (!ctx)
+        return fail(SCR_EINVAL, "null ctx out-pointer");
+    *ctx = nullptr;
+    int ndev = 0;
+    CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev)
+        return fail(SCR_EINVAL, "device %d out of range (%d devices)", device, ndev);
+    cudaDeviceProp prop;
+    CUDA_TRY(cudaGetDeviceProperties(&prop, device));
+    if (prop.major * 10 + prop.minor != 103)
+        return fail(SCR_ECUDA, "device %d is sm_%d%d; this library is built for sm_103a only", device,
+                    prop.major, prop.minor);
+    DeviceGuard dg(device);
+    if (!dg.ok)
+        return fail(SCR_ECUDA, "cudaSetDevice(%d) failed", device);
+    auto *c = new (std::nothrow) scr_ctx();
+    if (!c)
+        return fail(SCR_ENOMEM, "host allocation failed");
+    c->device = device;
+    c->budget = hbm_budget_bytes;
+    cudaMemPoolProps pp;
+    memset(&pp, 0, sizeof pp);
+    pp.allocType = cudaMemAllocationTypePinned;
+    pp.handleTypes = cudaMemHandleTypeNone;
+    pp.location.type = cudaMemLocationTypeDevice;
+    pp.location.id = device;
+    cudaError_t e = cudaMemPoolCreate(&c->pool, &pp);
+    if (e == cudaSuccess) {
+        uint64_t thr = hbm_budget_bytes ? hbm_budget_bytes : UINT64_MAX;
+        e = cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    if (e == cudaSuccess)
+        e = cudaMallocHost((void **)&c->pinned, 64);
+    if (e != cudaSuccess) {
+        if (c->pool)
+            cudaMemPoolDestroy(c->pool);
+        delete c;
+        return fail(SCR_ECUDA, "context setup failed: %s", cudaGetErrorString(e));
+    }
+    *ctx = c;
+    return SCR_OK;
+}
+
+void screen_shutdown(scr_ctx *c) {
+    if (!c)
+        return;
+    DeviceGuard dg(c->device);
+    cudaDeviceSynchronize();
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        for (auto *t : c->tables) {
+            cudaFreeAsync(t->base, nullptr);
+            delete t;
+        }
+        c->tables.clear();
+        for (auto *tm : c->tmpls)
+            delete tm;
+        c->tmpls.clear();
+    }
+    cudaDeviceSynchronize();
+    if (c->pinned)
+        cudaFreeHost(c->pinned);
+    cudaMemPoolDestroy(c->pool);
+    delete c;
+}
+
+int screen_stats(const scr_ctx *c, scr_stats *out) {
+    if (check_ctx(c) || !out)
+        return fail(SCR_EINVAL, "null argument");
+    out->kernel_launches = c->launches.load();
+    out->bytes_in_use = c->in_use.load();
+    out->bytes_peak = c->peak.load();
+    out->budget = c->budget;
+    return SCR_OK;
+}
+
+int build_tables(scr_ctx *c, const uint8_t *img_dev, int32_t H, int32_t W, int64_t pitch, int32_t sum_bits,
+                 int32_t sq_bits, scr_stream stream, scr_tables **out) {
+    int rc;
+    if ((rc = check_ctx(c)))
+        return rc;
+    if (!img_dev || !out)
+        return fail(SCR_EINVAL, "null image or out-pointer");
+    if (H < 1 || W < 1 || H > 65535 || W > 65535)
+        return fail(SCR_EINVAL, "image %d x %d outside 1..65535", H, W);
+    if (pitch < W)
+        return fail(SCR_EINVAL, "pitch %lld < width %d", (long long)pitch, W);
+    if ((sum_bits != 32 && sum_bits != 64) || (sq_bits != 32 && sq_bits != 64))
+        return fail(SCR_EINVAL, "table widths must be 32 or 64 bits");
+    *out = nullptr;
+    DeviceGuard dg(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(c->mu);
+    scr_tables *t = nullptr;
+    if ((rc = alloc_tables(c, H, W, sum_bits, sq_bits, st, &t)))
+        return rc;
+    if ((rc = run_build(c, img_dev, H, W, pitch, t, st))) {
+        free_tables(c, t);
+        return rc;
+    }
+    c->tables.insert(t);
+    *out = t;
+    return SCR_OK;
+}
+
+int tables_view(const scr_tables *t, int which, const void **dev_ptr, int64_t *rows, int64_t *cols, int64_t *pitch,
+                int64_t *offset, int64_t *plane_stride, int32_t *bits) {
+    if (!t || which < 0 || which > 3)
+        return fail(SCR_EINVAL, "bad tables handle or index %d", which);
+    const TableDesc &d = t->t[which];
+    if (dev_ptr) *dev_ptr = d.lo;
+    if (rows) *rows = d.rows;
+    if (cols) *cols = d.cols;
+    if (pitch) *pitch = d.pitch;
+    if (offset) *offset = kColOffset;
+    if (plane_stride) *plane_stride = d.hi ? (int64_t)(d.hi - d.lo) : 0;
+    if (bits) *bits = d.bits;
+    return SCR_OK;
+}
+
+int tables_copy_to_host(scr_ctx *c, const scr_tables *t, int which, uint64_t *dst) {
+    int rc;
+    if ((rc = check_ctx(c)))
+        return rc;
+    if (!t || which < 0 || which > 3 || !dst)
+        return fail(SCR_EINVAL, "bad arguments");
+    DeviceGuard dg(c->device);
+    const TableDesc &d = t->t[which];
+    std::vector<uint32_t> lo((size_t)d.rows * d.cols), hi;
+    CUDA_TRY(cudaStreamSynchronize(t->stream));
+    CUDA_TRY(cudaMemcpy2D(lo.data(), d.cols * 4, d.lo + kColOffset, d.pitch * 4, d.cols * 4, d.rows,
+                          cudaMemcpyDeviceToHost));
+    if (d.hi) {
+        hi.resize(lo.size());
+        CUDA_TRY(cudaMemcpy2D(hi.data(), d.cols * 4, d.hi + kColOffset, d.pitch * 4, d.cols * 4, d.rows,
+                              cudaMemcpyDeviceToHost));
+    }
+    for (size_t k = 0; k < lo.size(); ++k)
+        dst[k] = (uint64_t)lo[k] | (d.hi ? ((uint64_t)hi[k] << 32) : 0);
+    return SCR_OK;
+}
+
+void tables_release(scr_ctx *c, scr_tables *t) {
+    if (!c || !t)
+        return;
+    DeviceGuard dg(c->device);
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (c->tables.erase(t))
+        free_tables(c, t);
+}
+
+int template_features(scr_ctx *c, const uint8_t *tmpl_host, int32_t side, int32_t r, int32_t t_min,
+                      uint32_t features, scr_tmpl **out) {
+    int rc;
+    if ((rc = check_ctx(c)))
+        return rc;
+    if (!tmpl_host || !out)
+        return fail(SCR_EINVAL, "null template or out-pointer");
+    if (r < 2 || r > 181 || side != 2 * r + 1)
+        return fail(SCR_EINVAL, "template side %d must be 2r+1 with 2 <= r <= 181 (r = %d)", side, r);
+    if (t_min < 1 || t_min > r || ((features & SCR_F_GRAD) && t_min < 2))
+        return fail(SCR_EINVAL, "t_min %d outside [%d, r]", t_min, (features & SCR_F_GRAD) ? 2 : 1);
+    if (features & ~7u)
+        return fail(SCR_EINVAL, "unknown feature bits");
+    *out = nullptr;
+    DeviceGuard dg(c->device);
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaStream_t st = nullptr;
+    const int cnt = r - t_min + 1;
+    Scoped img(c, st), sums(c, st);
+    if ((rc = img.take((size_t)side * side)) || (rc = sums.take((size_t)cnt * 3 * 8)))
+        return rc;
+    CUDA_TRY(cudaMemcpyAsync(img.p, tmpl_host, (size_t)side * side, cudaMemcpyHostToDevice, st));
+    scr_tables *t = nullptr;
+    if ((rc = alloc_tables(c, side, side, 64, 64, st, &t)))
+        return rc;
+    rc = run_build(c, (const uint8_t *)img.p, side, side, side, t, st);
+    if (!rc) {
+        uint64_t n = 0;
+        cudaError_t e = launch_template_sums(t->t[0], t->t[1], t->t[2], t->t[3], r, t_min, (int64_t *)sums.p, st, &n);
+        c->launches += n;
+        if (e != cudaSuccess)
+            rc = fail(SCR_ECUDA, "template kernel: %s", cudaGetErrorString(e));
+    }
+    std::vector<int64_t> host((size_t)cnt * 3);
+    if (!rc) {
+        cudaError_t e = cudaMemcpyAsync(host.data(), sums.p, host.size() * 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess)
+            rc = fail(SCR_ECUDA, "template sums: %s", cudaGetErrorString(e));
+    }
+    free_tables(c, t);
+    if (rc)
+        return rc;
+    auto *tm = new (std::nothrow) scr_tmpl();
+    if (!tm)
+        return fail(SCR_ENOMEM, "host allocation failed");
+    tm->r = r;
+    tm->t_min = t_min;
+    tm->features = features;
+    bool first = true;
+    for (int k = 0; k < cnt; ++k) {
+        const int tt = t_min + k;
+        const int64_t S = host[3 * k], Q = host[3 * k + 1], Si = host[3 * k + 2];
+        tm->S.push_back(S);
+        tm->Q.push_back(Q);
+        tm->Si.push_back(Si);
+        const Geo g = geometry(tt);
+        // mean S/A, variance V/A^2, contrast N/(Ain*Aring)
+        const int64_t mu_n = S, mu_d = g.A;
+        const int64_t v_n = g.A * Q - S * S, v_d = g.A * g.A;
+        const int64_t g_n = Si * g.Aring - (S - Si) * g.Ain, g_d = g.Ain * g.Aring;
+        if (first) {
+            tm->mu_lo_n = tm->mu_hi_n = mu_n;
+            tm->mu_lo_d = tm->mu_hi_d = mu_d;
+            tm->v_lo_n = tm->v_hi_n = v_n;
+            tm->v_lo_d = tm->v_hi_d = v_d;
+            tm->g_lo_n = tm->g_hi_n = g_n;
+            tm->g_lo_d = tm->g_hi_d = g_d > 0 ? g_d : 1;
+            first = false;
+            continue;
+        }
+        if ((i128)mu_n * tm->mu_lo_d < (i128)tm->mu_lo_n * mu_d) { tm->mu_lo_n = mu_n; tm->mu_lo_d = mu_d; }
+        if ((i128)mu_n * tm->mu_hi_d > (i128)tm->mu_hi_n * mu_d) { tm->mu_hi_n = mu_n; tm->mu_hi_d = mu_d; }
+        if ((i128)v_n * tm->v_lo_d < (i128)tm->v_lo_n * v_d) { tm->v_lo_n = v_n; tm->v_lo_d = v_d; }
+        if ((i128)v_n * tm->v_hi_d > (i128)tm->v_hi_n * v_d) { tm->v_hi_n = v_n; tm->v_hi_d = v_d; }
+        if (g_d > 0) {
+            if ((i128)g_n * tm->g_lo_d < (i128)tm->g_lo_n * g_d) { tm->g_lo_n = g_n; tm->g_lo_d = g_d; }
+            if ((i128)g_n * tm->g_hi_d > (i128)tm->g_hi_n * g_d) { tm->g_hi_n = g_n; tm->g_hi_d = g_d; }
+        }
+    }
+    c->tmpls.insert(tm);
+    *out = tm;
+    return SCR_OK;
+}
+
+int template_sums(const scr_tmpl *tm, int32_t t, int64_t out[3]) {
+    if (!tm || !out || t < tm->t_min || t > tm->r)
+        return fail(SCR_EINVAL, "bad template handle or radius %d", t);
+    const int k = t - tm->t_min;
+    out[0] = tm->S[k];
+    out[1] = tm->Q[k];
+    out[2] = tm->Si[k];
+    return SCR_OK;
+}
+
+void template_release(scr_ctx *c, scr_tmpl *tm) {
+    if (!c || !tm)
+        return;
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (c->tmpls.erase(tm))
+        delete tm;
+}
+
+int screen_bounds(const scr_tmpl *tm, const scr_params *p, scr_bounds *out) {
+    if (!tm || !out)
+        return fail(SCR_EINVAL, "null argument");
+    int rc = validate_params(p);
+    if (rc)
+        return rc;
+    for (int s = 0; s < p->n_scales; ++s)
+        bounds_for(tm, p, p->radii[s], &out[s]);
+    return SCR_OK;
+}
+
+int screen_features(scr_ctx *c, const scr_tables *t, const scr_tmpl *tm, const scr_params *p, uint32_t *mask_dev,
+                    uint64_t mask_words, scr_stream stream) {
+    int rc;
+    if ((rc = check_ctx(c)) || (rc = check_screen_inputs(t, tm, p)))
+        return rc;
+    const uint64_t need = (uint64_t)p->n_scales * t->H * ((t->W + 31) / 32);
+    if (!mask_dev || mask_words < need)
+        return fail(SCR_EINVAL, "mask needs %llu words, got %llu", (unsigned long long)need,
+                    (unsigned long long)mask_words);
+    DeviceGuard dg(c->device);
+    ScreenArgs a;
+    fill_screen_args(t, tm, p, &a);
+    a.mask = mask_dev;
+    uint64_t n = 0;
+    cudaError_t e = launch_screen(a, (cudaStream_t)stream, &n);
+    c->launches += n;
+    CUDA_TRY(e);
+    const_cast<scr_tables *>(t)->stream = (cudaStream_t)stream;
+    return SCR_OK;
+}
+
+int compact_mask(scr_ctx *c, const uint32_t *mask_dev, int32_t n_scales, int32_t H, int32_t W, uint64_t *list_dev,
+                 uint64_t list_cap, uint64_t *count_dev, scr_stream stream) {
+    int rc;
+    if ((rc = check_ctx(c)))
+        return rc;
+    if (!mask_dev || !count_dev || (list_cap && !list_dev))
+        return fail(SCR_EINVAL, "null mask, count or list");
+    if (((uintptr_t)mask_dev & 15) || ((uintptr_t)count_dev & 7) || ((uintptr_t)list_dev & 7))
+        return fail(SCR_EINVAL, "mask must be 16-byte aligned, list and count 8-byte aligned");
+    if (n_scales < 1 || n_scales > 65535 || H < 1 || W < 1 || H > 65535 || W > 65535)
+        return fail(SCR_EINVAL, "bad mask geometry");
+    DeviceGuard dg(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int Ww = (W + 31) / 32;
+    const uint64_t total = (uint64_t)n_scales * H * Ww;
+    Scoped scratch(c, st);
+    if ((rc = scratch.take(compact_scratch_bytes(total))))
+        return rc;
+    uint64_t n = 0;
+    cudaError_t e = launch_compact(mask_dev, total, H, Ww, list_dev, list_cap, count_dev, scratch.p, st, &n);
+    c->launches += n;
+    CUDA_TRY(e);
+    return SCR_OK;
+}
+
+int screen_positions_async(scr_ctx *c, const scr_tables *t, const scr_tmpl *tm, const scr_params *p,
+                           uint32_t *mask_dev, uint64_t mask_words, uint64_t *list_dev, uint64_t list_cap,
+                           uint64_t *count_dev, scr_stream stream) {
+    int rc = screen_features(c, t, tm, p, mask_dev, mask_words, stream);
+    if (rc)
+        return rc;
+    return compact_mask(c, mask_dev, p->n_scales, t->H, t->W, list_dev, list_cap, count_dev, stream);
+}
+
+int screen_positions(scr_ctx *c, const scr_tables *t, const scr_tmpl *tm, const scr_params *p, uint32_t *mask_dev,
+                     uint64_t mask_words, uint64_t *list_dev, uint64_t list_cap, uint64_t *n_survivors,
+                     scr_stream stream) {
+    int rc;
+    if ((rc = check_ctx(c)))
+        return rc;
+    if (!n_survivors)
+        return fail(SCR_EINVAL, "null n_survivors");
+    DeviceGuard dg(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    Scoped cnt(c, st);
+    if ((rc = cnt.take(8)))
+        return rc;
+    if ((rc = screen_positions_async(c, t, tm, p, mask_dev, mask_words, list_dev, list_cap, (uint64_t *)cnt.p, stream)))
+        return rc;
+    std::lock_guard<std::mutex> lk(c->mu);
+    CUDA_TRY(cudaMemcpyAsync(c->pinned, cnt.p, 8, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    *n_survivors = c->pinned[0];
+    if (*n_survivors > list_cap)
+        return fail(SCR_EOVERFLOW, "%llu survivors exceed list capacity %llu", (unsigned long long)*n_survivors,
+                    (unsigned long long)list_cap);
+    return SCR_OK;
+}
+
+int screen_host(scr_ctx *c, const uint8_t *img_host, int32_t H, int32_t W, int64_t pitch, int32_t sum_bits,
+                int32_t sq_bits, const scr_tmpl *tm, const scr_params *p, uint64_t *list_host, uint64_t list_cap,
+                uint64_t *n_survivors, scr_stream stream) {
+    int rc;
+    if ((rc = check_ctx(c)))
+        return rc;
+    if (!img_host || !n_survivors || (list_cap && !list_host))
+        return fail(SCR_EINVAL, "null argument");
+    if (H < 1 || W < 1 || H > 65535 || W > 65535 || pitch < W)
+        return fail(SCR_EINVAL, "bad image geometry");
+    if ((rc = validate_params(p)))
+        return rc;
+    DeviceGuard dg(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t dpitch = (W + 15) / 16 * 16;
+    Scoped img(c, st), mask(c, st), list(c, st);
+    const uint64_t words = (uint64_t)p->n_scales * H * ((W + 31) / 32);
+    if ((rc = img.take((size_t)dpitch * H)) || (rc = mask.take(words * 4)) ||
+        (rc = list.take(std::max<uint64_t>(list_cap, 1) * 8 + 64)))
+        return rc;
+    CUDA_TRY(cudaMemcpy2DAsync(img.p, dpitch, img_host, pitch, W, H, cudaMemcpyHostToDevice, st));
+    scr_tables *t = nullptr;
+    if ((rc = build_tables(c, (const uint8_t *)img.p, H, W, dpitch, sum_bits, sq_bits, stream, &t)))
+        return rc;
+    uint64_t *cnt_dev = (uint64_t *)((char *)list.p + std::max<uint64_t>(list_cap, 1) * 8);
+    rc = screen_positions_async(c, t, tm, p, (uint32_t *)mask.p, words, list_cap ? (uint64_t *)list.p : nullptr,
+                                list_cap, cnt_dev, stream);
+    if (!rc) {
+        std::lock_guard<std::mutex> lk(c->mu);
+        cudaError_t e = cudaMemcpyAsync(c->pinned, cnt_dev, 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) {
+            *n_survivors = c->pinned[0];
+            const uint64_t k = std::min<uint64_t>(*n_survivors, list_cap);
+            if (k)
+                e = cudaMemcpyAsync(list_host, list.p, k * 8, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess)
+                e = cudaStreamSynchronize(st);
+        }
+        if (e != cudaSuccess)
+            rc = fail(SCR_ECUDA, "screen_host: %s", cudaGetErrorString(e));
+    }
+    tables_release(c, t);
+    if (!rc && *n_survivors > list_cap)
+        return fail(SCR_EOVERFLOW, "%llu survivors exceed list capacity %llu", (unsigned long long)*n_survivors,
+                    (unsigned long long)list_cap);
+    return rc;
+}
+
+}  // extern "C"

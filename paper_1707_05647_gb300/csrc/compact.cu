@@ -1,0 +1,185 @@
+// Compaction of the candidate bitmask into the ascending list of surviving
+// candidates (Sec. 5, Algorithm 1: R <- R u {P} for every patch that passes).
+//
+// The list order is the mask order (scale, row, column), so an exclusive scan
+// of per-word popcounts gives every set bit its final slot; ties cannot occur
+// and the list is identical to any correct compaction.  Three launches, no
+// inter-CTA waiting: per-chunk counts, one scan of the chunk counts, and a
+// per-chunk scan + scatter.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace scr {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWordsPerThread = 16;
+constexpr int kChunk = kThreads * kWordsPerThread;   // 4096 words per block
+
+__device__ __forceinline__ void load_words(const uint32_t *mask, uint64_t total, uint64_t first,
+                                           uint32_t (&w)[kWordsPerThread]) {
+    if (first + kWordsPerThread <= total) {
+        const uint4 *p = reinterpret_cast<const uint4 *>(mask + first);
+#pragma unroll
+        for (int q = 0; q < kWordsPerThread / 4; ++q) {
+            const uint4 v = __ldg(p + q);
+            w[4 * q] = v.x;
+            w[4 * q + 1] = v.y;
+            w[4 * q + 2] = v.z;
+            w[4 * q + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kWordsPerThread; ++k)
+            w[k] = (first + k < total) ? mask[first + k] : 0u;
+    }
+}
+
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *sh, uint32_t &total) {
+    const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o)
+            inc += u;
+    }
+    if (lane == 31)
+        sh[wp] = inc;
+    __syncthreads();
+    if (wp == 0) {
+        const uint32_t s = lane < kThreads / 32 ? sh[lane] : 0u;
+        uint32_t si = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, si, o);
+            if (lane >= o)
+                si += u;
+        }
+        if (lane < kThreads / 32)
+            sh[32 + lane] = si - s;
+        if (lane == 31)
+            sh[64] = si;
+    }
+    __syncthreads();
+    total = sh[64];
+    return sh[32 + wp] + inc - v;
+}
+
+__global__ void __launch_bounds__(kThreads) k_count(const uint32_t *mask, uint64_t total, uint32_t *counts) {
+    __shared__ uint32_t sh[72];
+    const uint64_t first = (uint64_t)blockIdx.x * kChunk + (uint64_t)threadIdx.x * kWordsPerThread;
+    uint32_t w[kWordsPerThread];
+    load_words(mask, total, first, w);
+    uint32_t c = 0;
+#pragma unroll
+    for (int k = 0; k < kWordsPerThread; ++k)
+        c += __popc(w[k]);
+    uint32_t tot;
+    block_excl_scan(c, sh, tot);
+    if (threadIdx.x == 0)
+        counts[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_counts(const uint32_t *counts, uint64_t *offsets, int nchunks,
+                                                      uint64_t *count_out) {
+    __shared__ uint64_t sh[72];
+    const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
+    uint64_t carry = 0;
+    for (int base = 0; base < nchunks; base += 1024) {
+        const int k = base + t;
+        const uint64_t v = k < nchunks ? counts[k] : 0;
+        uint64_t inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t u = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o)
+                inc += u;
+        }
+        if (lane == 31)
+            sh[wp] = inc;
+        __syncthreads();
+        if (wp == 0) {
+            const uint64_t s = sh[lane];
+            uint64_t si = s;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint64_t u = __shfl_up_sync(0xffffffffu, si, o);
+                if (lane >= o)
+                    si += u;
+            }
+            sh[32 + lane] = si - s;
+            if (lane == 31)
+                sh[64] = si;
+        }
+        __syncthreads();
+        if (k < nchunks)
+            offsets[k] = carry + sh[32 + wp] + inc - v;
+        carry += sh[64];
+        __syncthreads();
+    }
+    if (t == 0)
+        *count_out = carry;
+}
+
+__global__ void __launch_bounds__(kThreads) k_scatter(const uint32_t *mask, uint64_t total, int H, int Wwords,
+                                                      const uint64_t *offsets, uint64_t *list, uint64_t cap) {
+    __shared__ uint32_t sh[72];
+    const uint64_t first = (uint64_t)blockIdx.x * kChunk + (uint64_t)threadIdx.x * kWordsPerThread;
+    uint32_t w[kWordsPerThread];
+    load_words(mask, total, first, w);
+    uint32_t c = 0;
+#pragma unroll
+    for (int k = 0; k < kWordsPerThread; ++k)
+        c += __popc(w[k]);
+    uint32_t tot;
+    uint64_t pos = offsets[blockIdx.x] + block_excl_scan(c, sh, tot);
+    if (c == 0 || pos >= cap)
+        return;
+    const uint64_t rowWords = (uint64_t)Wwords;
+    const uint64_t planeWords = (uint64_t)H * rowWords;
+#pragma unroll 1
+    for (int k = 0; k < kWordsPerThread; ++k) {
+        uint32_t bits = w[k];
+        if (!bits)
+            continue;
+        const uint64_t wi = first + k;
+        const uint64_t s = wi / planeWords;
+        const uint64_t rem = wi - s * planeWords;
+        const uint64_t y = rem / rowWords;
+        const uint64_t x0 = (rem - y * rowWords) * 32;
+        const uint64_t keyb = (s << 48) | (y << 24);
+        while (bits) {
+            const int b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            if (pos < cap)
+                list[pos] = keyb | (x0 + b);
+            ++pos;
+        }
+    }
+}
+
+}  // namespace
+
+size_t compact_scratch_bytes(uint64_t total_words) {
+    const uint64_t nchunks = (total_words + kChunk - 1) / kChunk;
+    return ((nchunks * 4 + 255) & ~uint64_t(255)) + nchunks * 8 + 256;
+}
+
+cudaError_t launch_compact(const uint32_t *mask, uint64_t total_words, int H, int Wwords,
+                           uint64_t *list, uint64_t cap, uint64_t *count, void *scratch,
+                           cudaStream_t st, uint64_t *launches) {
+    const uint64_t nchunks = (total_words + kChunk - 1) / kChunk;
+    uint32_t *counts = (uint32_t *)scratch;
+    uint64_t *offsets = (uint64_t *)((char *)scratch + ((nchunks * 4 + 255) & ~uint64_t(255)));
+    k_count<<<(unsigned)nchunks, kThreads, 0, st>>>(mask, total_words, counts);
+    k_scan_counts<<<1, 1024, 0, st>>>(counts, offsets, (int)nchunks, count);
+    k_scatter<<<(unsigned)nchunks, kThreads, 0, st>>>(mask, total_words, H, Wwords, offsets, list, cap);
+    if (launches)
+        *launches += 3;
+    return cudaGetLastError();
+}
+
+}  // namespace scr

@@ -1,0 +1,93 @@
+// Internal declarations shared by the library's translation units.
+// Nothing here is part of the C ABI (include/screen.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "screen.h"
+
+namespace scr {
+
+// ---------------------------------------------------------------------------
+// Table storage.
+//
+// A table of R rows x C columns is stored as 32-bit words: element (a, b)
+// lives at word a*pitch + b + kColOffset of the low plane; a 64-bit table
+// has a second (high) plane plane_stride words after the low one.  The column
+// offset of 3 puts column b = 1 on a 16-byte boundary, so the kernels store
+// eight consecutive columns b = 8k+1 .. 8k+8 with two aligned 16-byte stores
+// per plane.  pitch is a multiple of 32 words (128 bytes).
+// ---------------------------------------------------------------------------
+constexpr int kColOffset = 3;
+
+struct TableDesc {
+    uint32_t *lo = nullptr;   // low 32 bits (the whole value for 32-bit tables)
+    uint32_t *hi = nullptr;   // high 32 bits, nullptr for 32-bit tables
+    int64_t pitch = 0;        // words per row
+    int64_t rows = 0, cols = 0;
+    int bits = 32;
+};
+
+// Build geometry of the table kernels (see tables.cu).
+constexpr int kBand = 32;                  // rows per band
+constexpr int kTabThreads = 128;           // threads per tile
+constexpr int kSlotsPerThread = 8;         // columns per thread
+constexpr int kHalo = kBand;               // halo columns on each side of a tile
+constexpr int kTileCols = kTabThreads * kSlotsPerThread - 2 * kHalo;   // 960 core columns
+constexpr int kWinLo = -34;                // first carry column kept per band
+
+inline int64_t table_pitch_words(int64_t W) { return ((W + 16 + 31) / 32) * 32; }
+
+// ---------------------------------------------------------------------------
+// Screening parameters handed to the feature kernel (one record per scale).
+// ---------------------------------------------------------------------------
+constexpr int kMaxScales = 32;
+
+struct ScaleParam {
+    int32_t R, n, h, ni, hi;          // star radius, square half-side, diamond
+                                      // half-diagonal, and the inner star's n, h
+    int32_t y_lo, y_hi, x_lo, x_hi;   // valid candidate rectangle (inclusive)
+    int32_t pad;
+    int64_t A, Ain, Aring;            // pooled areas
+    int64_t S_lo, S_hi, V_lo, V_hi, N_lo, N_hi;   // inclusive bounds
+};
+
+struct ScreenArgs {
+    const uint32_t *L1, *L2, *T1, *T2;   // low planes (window sums read mod 2^32)
+    int64_t pitchL, pitchT;              // words per row
+    int32_t H, W, Wwords, n_scales;
+    uint32_t features;
+    uint32_t *mask;
+    ScaleParam sp[kMaxScales];
+};
+
+// ---------------------------------------------------------------------------
+// Launchers (return cudaError_t of the launch).  `launches` is incremented by
+// the number of kernels enqueued.
+// ---------------------------------------------------------------------------
+struct TableScratch {
+    // sizes in bytes of the scratch regions the table build needs
+    static size_t bytes(int H, int W, int sum_bits, int sq_bits);
+};
+
+cudaError_t launch_build_tables(const uint8_t *img, int H, int W, int64_t pitch,
+                                const TableDesc &L1, const TableDesc &L2, const TableDesc &T1,
+                                const TableDesc &T2, void *scratch, cudaStream_t st,
+                                uint64_t *launches);
+
+cudaError_t launch_template_sums(const TableDesc &L1, const TableDesc &L2, const TableDesc &T1,
+                                 const TableDesc &T2, int r, int t_min, int64_t *out_dev,
+                                 cudaStream_t st, uint64_t *launches);
+
+cudaError_t launch_screen(const ScreenArgs &args, cudaStream_t st, uint64_t *launches);
+
+size_t compact_scratch_bytes(uint64_t total_words);
+cudaError_t launch_compact(const uint32_t *mask, uint64_t total_words, int H, int Wwords,
+                           uint64_t *list, uint64_t cap, uint64_t *count, void *scratch,
+                           cudaStream_t st, uint64_t *launches);
+
+// Square half-side n of star radius R: (2n-1)^2 < 2R^2 < (2n+1)^2.
+int square_half(int R);
+
+}  // namespace scr

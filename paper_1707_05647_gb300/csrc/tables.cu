@@ -1,0 +1,746 @@
+// Summed-area tables of I and I^2: upright (Sec. 3, Eq. T_1) and 45-degree
+// "cone" tables (Sec. 4, triangular summed-area map), built together.
+//
+// Definitions (row y, column x; P(y, x) = sum_{x' <= x} I(y, x') is the row
+// prefix, zero for x < 0 and the row total for x >= W):
+//   L(a, b)   = sum_{y < a, x < b} I(y, x)          = sum_{y < a} P(y, b-1)
+//   cone(r,c) = sum of I over y <= r, |x - c| <= r - y
+//             = D1(r, c) - D2(r, c), with
+//   D1(r, c)  = sum_{y <= r} P(y, c + (r - y))      (anti-diagonal prefix)
+//   D2(r, c)  = sum_{y <= r} P(y, c - 1 - (r - y))  (diagonal prefix)
+// because row y's part of the cone is P(y, c + r - y) - P(y, c - r + y - 1).
+// The paper builds its rotated table with "two diagonal passes of cumulative
+// sum" (Sec. 4); D1 and D2 are those two passes.
+//
+// Work decomposition.  The image is cut into bands of kBand rows and each band
+// into tiles of kTileCols columns.  A tile needs, for its first row, the values
+// of L, D1 and D2 on the row just above its band -- "carries" that depend on
+// every pixel above.  They are linear in the pixels, so they are assembled from
+// per-band partial sums in three stages, with no inter-CTA waiting:
+//   k_tab_reduce  per tile: column sums, anti-diagonal and diagonal sums of the
+//                 band (each restricted to the band), row sums.
+//   k_tab_carry   per column / diagonal index: exclusive prefix over bands.
+//   k_tab_prefix  per band: prefix along the row of those sums -> the carry
+//                 rows L(r0, .), D1(r0-1, .), D2(r0-1, .) and per-tile row carries.
+//   k_tab_write   per tile: walk the band's rows; each thread owns 8 adjacent
+//                 columns, keeps L, D1, D2 for them in registers; per row it
+//                 scans the pixels into P (warp shuffles + one block step), adds
+//                 P to L, moves D1 one column left and D2 one column right
+//                 (register moves plus one neighbour shuffle), and stores L and
+//                 T = D1 - D2 with 16-byte stores.
+// A tile carries kHalo extra columns on each side so its D1 (which flows in
+// from the right) and D2 (from the left) stay exact over its core columns for
+// the kBand rows of a band.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace scr {
+namespace {
+
+constexpr int B = kBand;
+constexpr int NT = kTabThreads;
+constexpr int CW = kTileCols;
+constexpr int HALO = kHalo;
+constexpr int SLOTS = NT * kSlotsPerThread;  // 1024 accumulator columns per tile
+constexpr int CL = kWinLo;                   // first carry column
+
+struct Geometry {
+    int H, W, n, m;          // bands, tiles
+    int XW;                  // carry columns c in [CL, W+1]
+    int DMIN, DN;            // anti-diagonal lanes d in [DMIN, DMIN+DN)
+    int FMIN, FN;            // diagonal lanes f in [FMIN, FMIN+FN)
+    Geometry(int H_, int W_) : H(H_), W(W_) {
+        n = (H + B - 1) / B;
+        m = (W + CW - 1) / CW;
+        XW = W + 1 - CL + 1;
+        DMIN = CL - 1;
+        DN = (n - 1) * B + W + 2 - DMIN;
+        FMIN = CL - (n - 1) * B;
+        FN = (W + 1) - FMIN + 1;
+    }
+};
+
+// Scratch layout (32-bit words unless noted), carved from one buffer.
+struct Scratch {
+    uint32_t *cs1, *cs2;     // [n][W]        column sums of the band
+    uint32_t *ad1, *ad2;     // [n][W+B-1]    anti-diagonal sums, x' + B-1
+    uint32_t *md1, *md2;     // [n][W+B-1]    diagonal sums, x''
+    uint32_t *rs1, *rs2;     // [n][m][B]     row sums over the tile's shifted chunk
+    uint32_t *csx1, *csx2;   // [n][W]        exclusive band prefix of cs
+    uint32_t *adx1, *adx2;   // [n][XW]       AD_i(r0-1+c)
+    uint32_t *mdx1, *mdx2;   // [n][XW]       MD_i(c-r0)
+    uint32_t *adf1, *adf2;   // [DN]          full anti-diagonal sums, index d - DMIN
+    uint32_t *rc1, *rc2;     // [n][m][B]     row carries P(r, c0-HALO-1)
+    void *xl1, *xl2, *x11, *x12, *x21, *x22;   // [n][XW] carry rows, table width
+};
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+size_t carve(const Geometry &g, int sb, int qb, Scratch *s, char *base) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char * {
+        char *p = base ? base + off : nullptr;
+        off += align256(bytes);
+        return p;
+    };
+    const size_t n = g.n, W = g.W, m = g.m, XW = g.XW;
+    s->cs1 = (uint32_t *)take(n * W * 4);
+    s->cs2 = (uint32_t *)take(n * W * 4);
+    s->ad1 = (uint32_t *)take(n * (W + B - 1) * 4);
+    s->ad2 = (uint32_t *)take(n * (W + B - 1) * 4);
+    s->md1 = (uint32_t *)take(n * (W + B - 1) * 4);
+    s->md2 = (uint32_t *)take(n * (W + B - 1) * 4);
+    s->rs1 = (uint32_t *)take(n * m * B * 4);
+    s->rs2 = (uint32_t *)take(n * m * B * 4);
+    s->csx1 = (uint32_t *)take(n * W * 4);
+    s->csx2 = (uint32_t *)take(n * W * 4);
+    s->adx1 = (uint32_t *)take(n * XW * 4);
+    s->adx2 = (uint32_t *)take(n * XW * 4);
+    s->mdx1 = (uint32_t *)take(n * XW * 4);
+    s->mdx2 = (uint32_t *)take(n * XW * 4);
+    s->adf1 = (uint32_t *)take((size_t)g.DN * 4);
+    s->adf2 = (uint32_t *)take((size_t)g.DN * 4);
+    s->rc1 = (uint32_t *)take(n * m * B * 4);
+    s->rc2 = (uint32_t *)take(n * m * B * 4);
+    const size_t es = sb / 8, eq = qb / 8;
+    s->xl1 = take(n * XW * es);
+    s->xl2 = take(n * XW * eq);
+    s->x11 = take(n * XW * es);
+    s->x12 = take(n * XW * eq);
+    s->x21 = take(n * XW * es);
+    s->x22 = take(n * XW * eq);
+    return off;
+}
+
+// ----------------------------------------------------------------------------
+// Stage 1: per-tile band sums.
+// ----------------------------------------------------------------------------
+struct ReduceArgs {
+    const uint8_t *img;
+    int64_t pitch;
+    Geometry g;
+    Scratch s;
+    int aligned8;
+};
+
+__global__ void __launch_bounds__(NT) k_tab_reduce(const ReduceArgs a) {
+    __shared__ __align__(16) uint8_t tile[B][SLOTS];
+    __shared__ uint32_t part1[B][NT / 32], part2[B][NT / 32];
+    const Geometry &g = a.g;
+    const int j = blockIdx.x, i = blockIdx.y, t = threadIdx.x;
+    const int r0 = i * B;
+    const int c0 = j * CW;
+    const int c1 = min(c0 + CW, g.W);
+    const int base = c0 - HALO;          // smem column 0
+    const int cs = base + 8 * t;         // this thread's 8 columns
+    // load the band (zero outside the image)
+    for (int rr = 0; rr < B; ++rr) {
+        const int y = r0 + rr;
+        uint2 w;
+        if (y < g.H && a.aligned8 && cs >= 0 && cs + 8 <= g.W) {
+            w = *reinterpret_cast<const uint2 *>(a.img + (int64_t)y * a.pitch + cs);
+        } else {
+            uint32_t lo = 0, hi = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int x = cs + k;
+                const uint32_t b = (y < g.H && x >= 0 && x < g.W) ? a.img[(int64_t)y * a.pitch + x] : 0u;
+                if (k < 4)
+                    lo |= b << (8 * k);
+                else
+                    hi |= b << (8 * (k - 4));
+            }
+            w = make_uint2(lo, hi);
+        }
+        *reinterpret_cast<uint2 *>(&tile[rr][8 * t]) = w;
+        uint32_t v[8];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = (w.x >> (8 * k)) & 0xffu;
+            v[k + 4] = (w.y >> (8 * k)) & 0xffu;
+        }
+        // row sum over the shifted chunk [c0-HALO, c0-HALO+CW) (threads 0..CW/8-1)
+        uint32_t s1 = 0, s2 = 0;
+        if (t < CW / 8) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                s1 += v[k];
+                s2 += v[k] * v[k];
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+        if ((t & 31) == 0) {
+            part1[rr][t >> 5] = s1;
+            part2[rr][t >> 5] = s2;
+        }
+    }
+    __syncthreads();
+    const size_t rsb = ((size_t)i * g.m + j) * B;
+    if (t < B) {
+        uint32_t s1 = 0, s2 = 0;
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) {
+            s1 += part1[t][w];
+            s2 += part2[t][w];
+        }
+        a.s.rs1[rsb + t] = s1;
+        a.s.rs2[rsb + t] = s2;
+    }
+    const size_t W = g.W, WD = g.W + B - 1;
+    // column sums
+    for (int x = c0 + t; x < c1; x += NT) {
+        uint32_t s1 = 0, s2 = 0;
+#pragma unroll 8
+        for (int rr = 0; rr < B; ++rr) {
+            const uint32_t v = tile[rr][x - base];
+            s1 += v;
+            s2 += v * v;
+        }
+        a.s.cs1[(size_t)i * W + x] = s1;
+        a.s.cs2[(size_t)i * W + x] = s2;
+    }
+    // anti-diagonal sums through (r_end, x'): sum_k I(r_end-k, x'+k)
+    const int xa0 = (j == 0) ? -(B - 1) : c0;
+    for (int xp = xa0 + t; xp < c1; xp += NT) {
+        uint32_t s1 = 0, s2 = 0;
+#pragma unroll 8
+        for (int k = 0; k < B; ++k) {
+            const uint32_t v = tile[B - 1 - k][xp + k - base];
+            s1 += v;
+            s2 += v * v;
+        }
+        a.s.ad1[(size_t)i * WD + xp + B - 1] = s1;
+        a.s.ad2[(size_t)i * WD + xp + B - 1] = s2;
+    }
+    // diagonal sums through (r_end, x''): sum_k I(r_end-k, x''-k)
+    const int xm1 = (j == g.m - 1) ? g.W + B - 1 : c1;
+    for (int xpp = c0 + t; xpp < xm1; xpp += NT) {
+        uint32_t s1 = 0, s2 = 0;
+#pragma unroll 8
+        for (int k = 0; k < B; ++k) {
+            const uint32_t v = tile[B - 1 - k][xpp - k - base];
+            s1 += v;
+            s2 += v * v;
+        }
+        a.s.md1[(size_t)i * WD + xpp] = s1;
+        a.s.md2[(size_t)i * WD + xpp] = s2;
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Stage 2: exclusive prefix over bands, per column (cs), anti-diagonal (ad)
+// and diagonal (md) index.  Block = 32 lanes x 32 band groups.
+// ----------------------------------------------------------------------------
+struct CarryArgs {
+    Geometry g;
+    Scratch s;
+    int chunksCS, chunksAD;   // 32-lane chunks of the first two parts
+};
+
+__device__ __forceinline__ void carry_contrib(const CarryArgs &a, int part, int lane_idx, int band,
+                                              uint32_t &v1, uint32_t &v2) {
+    const Geometry &g = a.g;
+    const size_t WD = g.W + B - 1;
+    v1 = v2 = 0;
+    if (part == 0) {
+        const size_t o = (size_t)band * g.W + lane_idx;
+        v1 = a.s.cs1[o];
+        v2 = a.s.cs2[o];
+    } else if (part == 1) {
+        const int xp = g.DMIN + lane_idx - (band * B + B - 1);     // d - r_end
+        if (xp >= -(B - 1) && xp <= g.W - 1) {
+            const size_t o = (size_t)band * WD + xp + B - 1;
+            v1 = a.s.ad1[o];
+            v2 = a.s.ad2[o];
+        }
+    } else {
+        const int f = g.FMIN + lane_idx;
+        const int xpp = f + band * B + B - 1;             // f + r_end
+        if (xpp >= 0 && xpp <= g.W + B - 2) {
+            const size_t o = (size_t)band * WD + xpp;
+            v1 = a.s.md1[o];
+            v2 = a.s.md2[o];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_tab_carry(const CarryArgs a) {
+    __shared__ uint32_t sum1[32][33], sum2[32][33];
+    const Geometry &g = a.g;
+    const int lane = threadIdx.x, grp = threadIdx.y;
+    int chunk = blockIdx.x, part, nlanes;
+    if (chunk < a.chunksCS) {
+        part = 0;
+        nlanes = g.W;
+    } else if (chunk < a.chunksCS + a.chunksAD) {
+        part = 1;
+        chunk -= a.chunksCS;
+        nlanes = g.DN;
+    } else {
+        part = 2;
+        chunk -= a.chunksCS + a.chunksAD;
+        nlanes = g.FN;
+    }
+    const int idx = chunk * 32 + lane;
+    const bool live = idx < nlanes;
+    const int q = (g.n + 31) / 32;
+    const int b0 = grp * q, b1 = min(g.n, b0 + q);
+    uint32_t t1 = 0, t2 = 0;
+    if (live)
+        for (int b = b0; b < b1; ++b) {
+            uint32_t v1, v2;
+            carry_contrib(a, part, idx, b, v1, v2);
+            t1 += v1;
+            t2 += v2;
+        }
+    sum1[grp][lane] = t1;
+    sum2[grp][lane] = t2;
+    __syncthreads();
+    if (grp == 0) {
+        uint32_t r1 = 0, r2 = 0;
+        for (int k = 0; k < 32; ++k) {
+            const uint32_t u1 = sum1[k][lane], u2 = sum2[k][lane];
+            sum1[k][lane] = r1;
+            sum2[k][lane] = r2;
+            r1 += u1;
+            r2 += u2;
+        }
+        if (part == 1 && live) {
+            a.s.adf1[idx] = r1;
+            a.s.adf2[idx] = r2;
+        }
+    }
+    __syncthreads();
+    if (!live)
+        return;
+    uint32_t run1 = sum1[grp][lane], run2 = sum2[grp][lane];
+    const size_t XW = g.XW;
+    for (int b = b0; b < b1; ++b) {
+        if (part == 0) {
+            const size_t o = (size_t)b * g.W + idx;
+            a.s.csx1[o] = run1;
+            a.s.csx2[o] = run2;
+        } else if (part == 1) {
+            const int c = g.DMIN + idx - (b * B - 1);     // d = r0 - 1 + c
+            if (c >= CL && c <= g.W + 1) {
+                a.s.adx1[(size_t)b * XW + (size_t)(c - CL)] = run1;
+                a.s.adx2[(size_t)b * XW + (size_t)(c - CL)] = run2;
+            }
+        } else {
+            const int c = g.FMIN + idx + b * B;           // f = c - r0
+            if (c >= CL && c <= g.W + 1) {
+                a.s.mdx1[(size_t)b * XW + (size_t)(c - CL)] = run1;
+                a.s.mdx2[(size_t)b * XW + (size_t)(c - CL)] = run2;
+            }
+        }
+        uint32_t v1, v2;
+        carry_contrib(a, part, idx, b, v1, v2);
+        run1 += v1;
+        run2 += v2;
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Stage 3: per band, prefix along the row -> carry rows in table width.
+// ----------------------------------------------------------------------------
+struct PrefixArgs {
+    Geometry g;
+    Scratch s;
+};
+
+__device__ __forceinline__ uint64_t block_excl_scan_1024(uint64_t v, uint64_t *sh, uint64_t &total) {
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    uint64_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o)
+            inc += u;
+    }
+    if (lane == 31)
+        sh[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        uint64_t s = sh[lane];
+        uint64_t si = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t u = __shfl_up_sync(0xffffffffu, si, o);
+            if (lane >= o)
+                si += u;
+        }
+        sh[32 + lane] = si - s;
+        if (lane == 31)
+            sh[64] = si;
+    }
+    __syncthreads();
+    const uint64_t res = sh[32 + w] + inc - v;
+    total = sh[64];
+    __syncthreads();
+    return res;
+}
+
+template <typename TS, typename TQ>
+__global__ void __launch_bounds__(1024) k_tab_prefix(const PrefixArgs a) {
+    __shared__ uint64_t sh[80];
+    const Geometry &g = a.g;
+    const int i = blockIdx.x, t = threadIdx.x;
+    const int r0 = i * B;
+    const size_t XW = g.XW;
+    // triangle: sum of full anti-diagonals d < r0 - 1 + CL (all inside rows < r0)
+    uint64_t tr1 = 0, tr2 = 0;
+    {
+        const int dend = r0 - 1 + CL;
+        uint64_t p1 = 0, p2 = 0;
+        for (int d = t; d < dend; d += 1024) {
+            p1 += a.s.adf1[d - g.DMIN];
+            p2 += a.s.adf2[d - g.DMIN];
+        }
+        uint64_t tot;
+        block_excl_scan_1024(p1, sh, tot);
+        tr1 = tot;
+        block_excl_scan_1024(p2, sh, tot);
+        tr2 = tot;
+    }
+    // six inclusive scans along c in [CL, W+1]
+    const int per = (int)((XW + 1023) / 1024);
+    const int k0 = t * per, k1 = min((int)XW, k0 + per);
+    uint64_t loc[6] = {0, 0, 0, 0, 0, 0};
+    for (int k = k0; k < k1; ++k) {
+        const int c = k + CL;
+        if (c >= 0 && c < g.W) {
+            loc[0] += a.s.csx1[(size_t)i * g.W + c];
+            loc[1] += a.s.csx2[(size_t)i * g.W + c];
+        }
+        loc[2] += a.s.adx1[(size_t)i * XW + k];
+        loc[3] += a.s.adx2[(size_t)i * XW + k];
+        loc[4] += a.s.mdx1[(size_t)i * XW + k];
+        loc[5] += a.s.mdx2[(size_t)i * XW + k];
+    }
+    uint64_t run[6];
+    for (int q = 0; q < 6; ++q) {
+        uint64_t tot;
+        run[q] = block_excl_scan_1024(loc[q], sh, tot);
+    }
+    run[2] += tr1;
+    run[3] += tr2;
+    TS *xl1 = (TS *)a.s.xl1, *x11 = (TS *)a.s.x11, *x21 = (TS *)a.s.x21;
+    TQ *xl2 = (TQ *)a.s.xl2, *x12 = (TQ *)a.s.x12, *x22 = (TQ *)a.s.x22;
+    for (int k = k0; k < k1; ++k) {
+        const int c = k + CL;
+        if (c >= 0 && c < g.W) {
+            run[0] += a.s.csx1[(size_t)i * g.W + c];
+            run[1] += a.s.csx2[(size_t)i * g.W + c];
+        }
+        run[2] += a.s.adx1[(size_t)i * XW + k];
+        run[3] += a.s.adx2[(size_t)i * XW + k];
+        run[4] += a.s.mdx1[(size_t)i * XW + k];
+        run[5] += a.s.mdx2[(size_t)i * XW + k];
+        const size_t o = (size_t)i * XW + k;
+        xl1[o] = (TS)run[0];
+        xl2[o] = (TQ)run[1];
+        x11[o] = (TS)run[2];
+        x12[o] = (TQ)run[3];
+        x21[o] = (TS)run[4];
+        x22[o] = (TQ)run[5];
+    }
+    // row carries per tile: sum of row sums of the tiles to the left
+    if (t < B) {
+        uint32_t c1 = 0, c2 = 0;
+        for (int j = 0; j < g.m; ++j) {
+            const size_t o = ((size_t)i * g.m + j) * B + t;
+            a.s.rc1[o] = c1;
+            a.s.rc2[o] = c2;
+            c1 += a.s.rs1[o];
+            c2 += a.s.rs2[o];
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Stage 4: per tile, walk the band's rows and write L1, L2, T1, T2.
+// ----------------------------------------------------------------------------
+struct WriteArgs {
+    const uint8_t *img;
+    int64_t pitch;
+    Geometry g;
+    Scratch s;
+    uint32_t *L1lo, *L1hi, *L2lo, *L2hi, *T1lo, *T1hi, *T2lo, *T2hi;
+    int64_t pL, pT;
+    int aligned8;
+};
+
+template <typename T>
+__device__ __forceinline__ void store8(uint32_t *lo, uint32_t *hi, int64_t word, const T (&v)[8]) {
+    if (sizeof(T) == 4) {
+        uint4 a = make_uint4((uint32_t)v[0], (uint32_t)v[1], (uint32_t)v[2], (uint32_t)v[3]);
+        uint4 b = make_uint4((uint32_t)v[4], (uint32_t)v[5], (uint32_t)v[6], (uint32_t)v[7]);
+        *reinterpret_cast<uint4 *>(lo + word) = a;
+        *reinterpret_cast<uint4 *>(lo + word + 4) = b;
+    } else {
+        uint4 a = make_uint4((uint32_t)v[0], (uint32_t)v[1], (uint32_t)v[2], (uint32_t)v[3]);
+        uint4 b = make_uint4((uint32_t)v[4], (uint32_t)v[5], (uint32_t)v[6], (uint32_t)v[7]);
+        uint4 c = make_uint4((uint32_t)((uint64_t)v[0] >> 32), (uint32_t)((uint64_t)v[1] >> 32),
+                             (uint32_t)((uint64_t)v[2] >> 32), (uint32_t)((uint64_t)v[3] >> 32));
+        uint4 d = make_uint4((uint32_t)((uint64_t)v[4] >> 32), (uint32_t)((uint64_t)v[5] >> 32),
+                             (uint32_t)((uint64_t)v[6] >> 32), (uint32_t)((uint64_t)v[7] >> 32));
+        *reinterpret_cast<uint4 *>(lo + word) = a;
+        *reinterpret_cast<uint4 *>(lo + word + 4) = b;
+        *reinterpret_cast<uint4 *>(hi + word) = c;
+        *reinterpret_cast<uint4 *>(hi + word + 4) = d;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void store1(uint32_t *lo, uint32_t *hi, int64_t word, T v) {
+    lo[word] = (uint32_t)v;
+    if (sizeof(T) == 8)
+        hi[word] = (uint32_t)((uint64_t)v >> 32);
+}
+
+template <typename TS, typename TQ>
+__global__ void __launch_bounds__(NT) k_tab_write(const WriteArgs a) {
+    __shared__ uint32_t wt1[2][NT / 32], wt2[2][NT / 32];      // warp totals
+    __shared__ TS nb_d1a[2][NT / 32], nb_d2a[2][NT / 32];      // warp-edge neighbours
+    __shared__ TQ nb_d1b[2][NT / 32], nb_d2b[2][NT / 32];
+    const Geometry &g = a.g;
+    const int j = blockIdx.x, i = blockIdx.y, t = threadIdx.x;
+    const int lane = t & 31, w = t >> 5;
+    const int r0 = i * B;
+    const int rows = min(B, g.H - r0);
+    const int c0 = j * CW;
+    const bool last = (j == g.m - 1);
+    const int cs = c0 - HALO + 8 * t;
+    const int cTmax = last ? g.W : c0 + CW - 1;     // last T column this tile writes
+    const int cLmax = last ? g.W - 1 : c0 + CW - 1; // last L column (b = c+1 <= W)
+    const bool wT = cs >= c0 && cs <= cTmax;
+    const bool wL = cs >= c0 && cs <= cLmax;
+    const bool wEdge = (j == 0) && (cs == -8);      // column c = -1 (b = 0)
+
+    // carries from the row above the band
+    TS L1a[8], D1a[8], D2a[8];
+    TQ L2a[8], D1b[8], D2b[8];
+    {
+        const size_t XW = g.XW;
+        const TS *xl1 = (const TS *)a.s.xl1, *x11 = (const TS *)a.s.x11, *x21 = (const TS *)a.s.x21;
+        const TQ *xl2 = (const TQ *)a.s.xl2, *x12 = (const TQ *)a.s.x12, *x22 = (const TQ *)a.s.x22;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            int c = cs + k;
+            c = c < CL ? CL : (c > g.W + 1 ? g.W + 1 : c);
+            const size_t o = (size_t)i * XW + (c - CL);
+            L1a[k] = xl1[o];
+            L2a[k] = xl2[o];
+            D1a[k] = x11[o];
+            D1b[k] = x12[o];
+            D2a[k] = x21[o];
+            D2b[k] = x22[o];
+        }
+    }
+    // row 0 of every table is zero
+    if (i == 0) {
+        TS z1[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        TQ z2[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (wL) {
+            store8(a.L1lo, a.L1hi, cs + 1 + kColOffset, z1);
+            store8(a.L2lo, a.L2hi, cs + 1 + kColOffset, z2);
+        }
+        if (wT) {
+            store8(a.T1lo, a.T1hi, cs + 1 + kColOffset, z1);
+            store8(a.T2lo, a.T2hi, cs + 1 + kColOffset, z2);
+        }
+        if (wEdge) {
+            store1(a.L1lo, a.L1hi, kColOffset, (TS)0);
+            store1(a.L2lo, a.L2hi, kColOffset, (TQ)0);
+            store1(a.T1lo, a.T1hi, kColOffset, (TS)0);
+            store1(a.T2lo, a.T2hi, kColOffset, (TQ)0);
+        }
+    }
+    const uint32_t *rc1 = a.s.rc1 + ((size_t)i * g.m + j) * B;
+    const uint32_t *rc2 = a.s.rc2 + ((size_t)i * g.m + j) * B;
+
+    for (int rr = 0; rr < rows; ++rr) {
+        const int y = r0 + rr;
+        const int par = rr & 1;
+        uint32_t v[8];
+        if (a.aligned8 && cs >= 0 && cs + 8 <= g.W) {
+            const uint2 q = __ldg(reinterpret_cast<const uint2 *>(a.img + (int64_t)y * a.pitch + cs));
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                v[k] = (q.x >> (8 * k)) & 0xffu;
+                v[k + 4] = (q.y >> (8 * k)) & 0xffu;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int x = cs + k;
+                v[k] = (x >= 0 && x < g.W) ? (uint32_t)__ldg(a.img + (int64_t)y * a.pitch + x) : 0u;
+            }
+        }
+        uint32_t p1[8], p2[8];
+        p1[0] = v[0];
+        p2[0] = v[0] * v[0];
+#pragma unroll
+        for (int k = 1; k < 8; ++k) {
+            p1[k] = p1[k - 1] + v[k];
+            p2[k] = p2[k - 1] + v[k] * v[k];
+        }
+        // warp inclusive scan of the thread totals
+        uint32_t s1 = p1[7], s2 = p2[7];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u1 = __shfl_up_sync(0xffffffffu, s1, o);
+            const uint32_t u2 = __shfl_up_sync(0xffffffffu, s2, o);
+            if (lane >= o) {
+                s1 += u1;
+                s2 += u2;
+            }
+        }
+        if (lane == 31) {
+            wt1[par][w] = s1;
+            wt2[par][w] = s2;
+        }
+        // old D1[0] and D2[7] of warp-edge threads for the neighbouring warps
+        if (lane == 0) {
+            nb_d1a[par][w] = D1a[0];
+            nb_d1b[par][w] = D1b[0];
+        }
+        if (lane == 31) {
+            nb_d2a[par][w] = D2a[7];
+            nb_d2b[par][w] = D2b[7];
+        }
+        // in-warp neighbours (before the update)
+        TS n1a = __shfl_down_sync(0xffffffffu, D1a[0], 1);
+        TQ n1b = __shfl_down_sync(0xffffffffu, D1b[0], 1);
+        TS n2a = __shfl_up_sync(0xffffffffu, D2a[7], 1);
+        TQ n2b = __shfl_up_sync(0xffffffffu, D2b[7], 1);
+        __syncthreads();
+        uint32_t e1 = rc1[rr] + s1 - p1[7], e2 = rc2[rr] + s2 - p2[7];
+        for (int q = 0; q < w; ++q) {
+            e1 += wt1[par][q];
+            e2 += wt2[par][q];
+        }
+        if (lane == 31) {
+            if (w + 1 < NT / 32) {
+                n1a = nb_d1a[par][w + 1];
+                n1b = nb_d1b[par][w + 1];
+            } else {            // rightmost column of the tile: D1 is constant there
+                n1a = D1a[7];   // (exact for the last tile, whose right end is past W)
+                n1b = D1b[7];
+            }
+        }
+        if (lane == 0) {
+            if (w > 0) {
+                n2a = nb_d2a[par][w - 1];
+                n2b = nb_d2b[par][w - 1];
+            } else {            // leftmost column: D2 = 0 left of the image (tile 0)
+                n2a = 0;
+                n2b = 0;
+            }
+        }
+        // P(y, c) for this thread's columns; e = P(y, cs-1)
+        uint32_t P1[8], P2[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            P1[k] = e1 + p1[k];
+            P2[k] = e2 + p2[k];
+        }
+        TS T1v[8];
+        TQ T2v[8];
+        // D2 moves one column right: D2(y, c) = P(y, c-1) + D2(y-1, c-1)
+#pragma unroll
+        for (int k = 7; k >= 1; --k) {
+            D2a[k] = (TS)P1[k - 1] + D2a[k - 1];
+            D2b[k] = (TQ)P2[k - 1] + D2b[k - 1];
+        }
+        D2a[0] = (TS)e1 + n2a;
+        D2b[0] = (TQ)e2 + n2b;
+        // D1 moves one column left: D1(y, c) = P(y, c) + D1(y-1, c+1)
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+            D1a[k] = (TS)P1[k] + D1a[k + 1];
+            D1b[k] = (TQ)P2[k] + D1b[k + 1];
+        }
+        D1a[7] = (TS)P1[7] + n1a;
+        D1b[7] = (TQ)P2[7] + n1b;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            L1a[k] += (TS)P1[k];
+            L2a[k] += (TQ)P2[k];
+            T1v[k] = D1a[k] - D2a[k];
+            T2v[k] = D1b[k] - D2b[k];
+        }
+        const int64_t rowL = (int64_t)(y + 1) * a.pL + kColOffset;
+        const int64_t rowT = (int64_t)(y + 1) * a.pT + kColOffset;
+        if (wL) {
+            store8(a.L1lo, a.L1hi, rowL + cs + 1, L1a);
+            store8(a.L2lo, a.L2hi, rowL + cs + 1, L2a);
+        }
+        if (wT) {
+            store8(a.T1lo, a.T1hi, rowT + cs + 1, T1v);
+            store8(a.T2lo, a.T2hi, rowT + cs + 1, T2v);
+        }
+        if (wEdge) {   // b = 0: L is zero, T is cone(y, -1) = D1(y, -1)
+            store1(a.L1lo, a.L1hi, rowL, (TS)0);
+            store1(a.L2lo, a.L2hi, rowL, (TQ)0);
+            store1(a.T1lo, a.T1hi, rowT, T1v[7]);
+            store1(a.T2lo, a.T2hi, rowT, T2v[7]);
+        }
+    }
+}
+
+template <typename TS, typename TQ>
+cudaError_t launch_all(const Geometry &g, const Scratch &s, const uint8_t *img, int64_t pitch,
+                       int aligned8, const TableDesc &L1, const TableDesc &L2,
+                       const TableDesc &T1, const TableDesc &T2, cudaStream_t st) {
+    ReduceArgs ra{img, pitch, g, s, aligned8};
+    k_tab_reduce<<<dim3(g.m, g.n), NT, 0, st>>>(ra);
+    CarryArgs ca{g, s, (g.W + 31) / 32, (g.DN + 31) / 32};
+    const int chunks = ca.chunksCS + ca.chunksAD + (g.FN + 31) / 32;
+    k_tab_carry<<<chunks, dim3(32, 32), 0, st>>>(ca);
+    PrefixArgs pa{g, s};
+    k_tab_prefix<TS, TQ><<<g.n, 1024, 0, st>>>(pa);
+    WriteArgs wa{img, pitch, g, s, L1.lo, L1.hi, L2.lo, L2.hi, T1.lo, T1.hi, T2.lo, T2.hi,
+                 L1.pitch, T1.pitch, aligned8};
+    k_tab_write<TS, TQ><<<dim3(g.m, g.n), NT, 0, st>>>(wa);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t TableScratch::bytes(int H, int W, int sum_bits, int sq_bits) {
+    Geometry g(H, W);
+    Scratch s;
+    return carve(g, sum_bits, sq_bits, &s, nullptr);
+}
+
+cudaError_t launch_build_tables(const uint8_t *img, int H, int W, int64_t pitch,
+                                const TableDesc &L1, const TableDesc &L2, const TableDesc &T1,
+                                const TableDesc &T2, void *scratch, cudaStream_t st,
+                                uint64_t *launches) {
+    Geometry g(H, W);
+    Scratch s;
+    carve(g, L1.bits, L2.bits, &s, (char *)scratch);
+    const int aligned8 = ((uintptr_t)img % 8 == 0) && (pitch % 8 == 0);
+    cudaError_t e;
+    const bool s64 = L1.bits == 64, q64 = L2.bits == 64;
+    if (!s64 && !q64)
+        e = launch_all<uint32_t, uint32_t>(g, s, img, pitch, aligned8, L1, L2, T1, T2, st);
+    else if (!s64 && q64)
+        e = launch_all<uint32_t, uint64_t>(g, s, img, pitch, aligned8, L1, L2, T1, T2, st);
+    else if (s64 && !q64)
+        e = launch_all<uint64_t, uint32_t>(g, s, img, pitch, aligned8, L1, L2, T1, T2, st);
+    else
+        e = launch_all<uint64_t, uint64_t>(g, s, img, pitch, aligned8, L1, L2, T1, T2, st);
+    if (launches)
+        *launches += 4;
+    return e;
+}
+
+}  // namespace scr
