@@ -71,7 +71,7 @@ class Clocks:
     def __enter__(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.p = None
@@ -152,7 +152,8 @@ def run_reference(args):
 
 
 def config_dict(wl):
-    return {"workload": "single large image: 4096x4096 u8, planted r=48 template, 8 scales 0.5-2, "
+    H, W = wl.image.shape
+    return {"workload": f"single large image: {H}x{W} u8, planted r=48 template, 8 scales 0.5-2, "
                         "mean+variance+contrast, u32 sum / u64 sum^2 tables",
             "image": f"{wl.image.shape[0]}x{wl.image.shape[1]}", "radii": wl.radii, "t_min": wl.t_min,
             "features": "mean+var+contrast", "tables": f"u{wl.sum_bits} sum / u{wl.sq_bits} sum^2",
@@ -174,6 +175,8 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     wl = synth.config2(synth.BASE_SEED + 1 + 1000 * rank)
+    if args.size != 4096:      # smaller case of the same recipe (profiling captures)
+        wl.image = np.ascontiguousarray(wl.image[:args.size, :args.size])
     H, W = wl.image.shape
     S = len(wl.radii)
     ncand = candidates(H, W, wl.radii)
@@ -228,6 +231,19 @@ def run_ours(args):
     n_surv = int(count.item())
 
     # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(scr, torch, ctx, wl, tm, p, cap, ncand, args)
+    if rank == 0:
+        emit(args, wl, world, total_s, value, k3_ms, step_ms, launches, clk, n_surv, e2e)
+    scr.template_release(ctx, tm)
+    scr.screen_shutdown(ctx)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_e2e(scr, torch, ctx, wl, tm, p, cap, ncand, args):
+    H, W = wl.image.shape
     img_host = torch.from_numpy(wl.image).pin_memory()
     lst_host = torch.empty(cap, dtype=torch.int64).pin_memory()
     for _ in range(2):
@@ -238,53 +254,55 @@ def run_ours(args):
     for _ in range(e2e_steps):
         n_e2e, _ = scr.screen_host(ctx, img_host.numpy(), wl.sum_bits, wl.sq_bits, tm, p, lst_host.numpy())
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    e2e = {"value": ncand / e2e_s, "unit": UNIT, "h2d_bytes_per_step": H * W,
-           "d2h_bytes_per_step": 8 + 8 * min(n_e2e, cap)}
+    return {"value": ncand / e2e_s, "unit": UNIT, "h2d_bytes_per_step": H * W,
+            "d2h_bytes_per_step": 8 + 8 * min(n_e2e, cap), "steps": e2e_steps}
 
-    if rank == 0:
-        peak, src = measured_peak_gbs()
-        k3 = statistics.mean(k3_ms) / 1e3
-        alg = per_scale_bytes(H, W, S, wl.sum_bits, wl.sq_bits)
-        achieved = alg / k3 / 1e9
-        prof = os.path.join(ROOT, "profiles", "traffic_screen_4096.json")
-        traffic = None
-        if os.path.exists(prof):
-            try:
-                traffic = json.load(open(prof)).get("dram_bytes_per_launch")
-            except Exception:
-                traffic = None
-        cpu = None
-        if not args.no_cpu_baseline:
-            v, sample, cores, dt = oracle_baseline(wl)
-            cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
-                   "seconds": round(dt, 2)}
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32+u64", "data": "synthetic",
-            "config": config_dict(wl),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "peak_source": src,
-                         "kernel": "k_screen", "model": "Algorithm 1 per-scale: 4 tables read once per "
-                         "scale + mask written", "kernel_ms": 1e3 * k3},
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk.summary(), "survivors": n_surv,
-            "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
-        }
-        print(json.dumps(line), flush=True)
-    scr.template_release(ctx, tm)
-    scr.screen_shutdown(ctx)
-    if dist:
-        dist.destroy_process_group()
+
+def emit(args, wl, world, total_s, value, k3_ms, step_ms, launches, clk, n_surv, e2e):
+    H, W = wl.image.shape
+    S = len(wl.radii)
+    peak, src = measured_peak_gbs()
+    k3 = statistics.mean(k3_ms) / 1e3
+    alg = per_scale_bytes(H, W, S, wl.sum_bits, wl.sq_bits)
+    achieved = alg / k3 / 1e9
+    prof = os.path.join(ROOT, "profiles", "traffic_screen_4096.json")
+    traffic = None
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+    cpu = None
+    if not args.no_cpu_baseline:
+        v, sample, cores, dt = oracle_baseline(wl)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+               "seconds": round(dt, 2)}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32+u64", "data": "synthetic",
+        "config": config_dict(wl),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": src,
+                     "kernel": "k_screen", "model": "Algorithm 1 per-scale: 4 tables read once per "
+                     "scale + mask written", "kernel_ms": 1e3 * k3},
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clk.summary(), "survivors": n_surv,
+        "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
+    }
+    print(json.dumps(line), flush=True)
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--size", type=int, default=4096,
+                    help="crop the 4096x4096 image to size x size (smaller ncu captures)")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

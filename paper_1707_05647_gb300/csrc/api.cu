@@ -320,8 +320,8 @@ int fill_screen_args(const scr_tables *t, const scr_tmpl *tm, const scr_params *
     a->L2 = t->t[1].lo;
     a->T1 = t->t[2].lo;
     a->T2 = t->t[3].lo;
-    a->pitchL = t->t[0].pitch;
-    a->pitchT = t->t[2].pitch;
+    const int64_t P = t->t[0].pitch;   // all four tables share the pitch
+    a->pitch = P;
     a->H = t->H;
     a->W = t->W;
     a->Wwords = (t->W + 31) / 32;
@@ -331,26 +331,52 @@ int fill_screen_args(const scr_tables *t, const scr_tmpl *tm, const scr_params *
         const int R = p->radii[s];
         const Geo g = geometry(R);
         ScaleParam &sp = a->sp[s];
-        sp.R = R;
-        sp.n = g.n;
-        sp.h = g.h;
-        sp.ni = g.ni;
-        sp.hi = g.hi;
+        const int64_t n = g.n, h = g.h, ni = g.ni, hi = g.hi;
+        const int64_t oL[4] = {(n + 1) * P + (n + 1), (1 - n) * P + (n + 1), (n + 1) * P + (1 - n), (1 - n) * P + (1 - n)};
+        const int64_t oT[4] = {(h + 1) * P + 1, P + (1 - h), P + (h + 1), (1 - h) * P + 1};
+        const int64_t oLi[4] = {(ni + 1) * P + (ni + 1), (1 - ni) * P + (ni + 1), (ni + 1) * P + (1 - ni),
+                                (1 - ni) * P + (1 - ni)};
+        const int64_t oTi[4] = {(hi + 1) * P + 1, P + (1 - hi), P + (hi + 1), (1 - hi) * P + 1};
+        for (int k = 0; k < 4; ++k) {
+            sp.oL[k] = (int32_t)oL[k];
+            sp.oT[k] = (int32_t)oT[k];
+            sp.oLi[k] = (int32_t)oLi[k];
+            sp.oTi[k] = (int32_t)oTi[k];
+        }
         sp.y_lo = std::max(g.n, g.h) - 1;
         sp.y_hi = t->H - 1 - std::max(g.n, g.h);
         sp.x_lo = std::max(g.n, g.h) - 1;
         sp.x_hi = std::min(t->W - 1 - g.n, t->W - g.h);
-        sp.A = g.A;
-        sp.Ain = g.Ain;
-        sp.Aring = g.Aring;
+        sp.A = (uint32_t)g.A;
+        sp.Ain = (uint32_t)g.Ain;
+        sp.Aring = (uint32_t)g.Aring;
         scr_bounds b;
         bounds_for(tm, p, R, &b);
-        sp.S_lo = b.S_lo;
-        sp.S_hi = b.S_hi;
-        sp.V_lo = b.V_lo;
-        sp.V_hi = b.V_hi;
-        sp.N_lo = b.N_lo;
-        sp.N_hi = b.N_hi;
+        // no valid position at this scale (the star does not fit in the image)
+        sp.empty = (sp.x_hi < sp.x_lo || sp.y_hi < sp.y_lo) ? 1u : 0u;
+        sp.S_lo = 0;
+        sp.S_rng = UINT32_MAX;
+        if (p->features & SCR_F_MEAN) {
+            const int64_t lo = std::max<int64_t>(b.S_lo, 0), hi2 = std::min<int64_t>(b.S_hi, UINT32_MAX);
+            if (lo > hi2)
+                sp.empty = 1;
+            else {
+                sp.S_lo = (uint32_t)lo;
+                sp.S_rng = (uint32_t)(hi2 - lo);
+            }
+        }
+        if (p->features & SCR_F_VAR) {
+            if (b.V_lo > b.V_hi)
+                sp.empty = 1;
+            sp.V_lo = b.V_lo;
+            sp.V_rng = (uint64_t)((i128)b.V_hi - (i128)b.V_lo);
+        }
+        if (p->features & SCR_F_GRAD) {
+            if (b.N_lo > b.N_hi)
+                sp.empty = 1;
+            sp.N_lo = b.N_lo;
+            sp.N_rng = (uint64_t)((i128)b.N_hi - (i128)b.N_lo);
+        }
     }
     return SCR_OK;
 }

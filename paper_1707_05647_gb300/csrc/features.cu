@@ -18,7 +18,12 @@
 //
 // Mapping: one warp evaluates one mask word -- 32 consecutive x of one row --
 // for every scale, so each corner read is a coalesced 128-byte row segment and
-// the word is formed with one warp ballot.
+// the word is formed with one warp ballot.  The tests run in order mean,
+// variance, contrast and each later test's corner reads are issued only for
+// lanes still alive, so a warp whose candidates all fail the mean test reads
+// 8 of the 24 corners.  The kernel is bound by instruction issue; corner
+// offsets are precomputed per scale so each read costs one multiply-add and
+// one load.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -31,49 +36,127 @@ constexpr int kWarpsPerBlock = 8;
 
 __device__ __forceinline__ uint32_t ld(const uint32_t *p) { return __ldg(p); }
 
-__device__ __forceinline__ uint32_t square_sum(const uint32_t *L, int64_t pitch, int y, int x, int n) {
-    const uint32_t *r1 = L + (int64_t)(y + n + 1) * pitch + kColOffset;
-    const uint32_t *r0 = L + (int64_t)(y - n + 1) * pitch + kColOffset;
-    return ld(r1 + x + n + 1) - ld(r0 + x + n + 1) - ld(r1 + x - n + 1) + ld(r0 + x - n + 1);
+// Sum over a window from its four corner values: c0 - c1 - c2 + c3 (mod 2^32).
+__device__ __forceinline__ uint32_t corners(const uint32_t *base, const int32_t (&o)[4]) {
+    return ld(base + o[0]) - ld(base + o[1]) - ld(base + o[2]) + ld(base + o[3]);
 }
 
-__device__ __forceinline__ uint32_t diamond_sum(const uint32_t *T, int64_t pitch, int y, int x, int h) {
-    const uint32_t *rc = T + (int64_t)(y + 1) * pitch + kColOffset;
-    return ld(T + (int64_t)(y + h + 1) * pitch + kColOffset + x + 1) - ld(rc + x - h + 1) -
-           ld(rc + x + h + 1) + ld(T + (int64_t)(y - h + 1) * pitch + kColOffset + x + 1);
-}
+// Eight corner pointers of one star shape pair (square + diamond) for the
+// first word of a warp; word j reads 32*j elements further (immediate offset).
+struct Corners {
+    const uint32_t *p[8];
+    __device__ __forceinline__ Corners(const uint32_t *L, const uint32_t *T, const int32_t (&oL)[4],
+                                       const int32_t (&oT)[4]) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            p[k] = L + oL[k];
+            p[4 + k] = T + oT[k];
+        }
+    }
+    // square + diamond sum of word j (mod 2^32; exact since the sum is < 2^32)
+    __device__ __forceinline__ uint32_t sum(int j) const {
+        const int d = 32 * j;
+        return ld(p[0] + d) - ld(p[1] + d) - ld(p[2] + d) + ld(p[3] + d) + ld(p[4] + d) - ld(p[5] + d) -
+               ld(p[6] + d) + ld(p[7] + d);
+    }
+};
+
+// WPW: mask words per warp.  The warp covers 32*WPW consecutive x; corner
+// pointers are formed once per scale and every word reads at an immediate
+// offset from them, and the per-scale bookkeeping is shared by all words.
+// Warps whose whole span lies inside the valid range take a branch-free path.
+// The star-sum reads of all words of a scale are issued back to back; the
+// survivors of each test are kept as a per-lane bitmask (bit j = word j); the
+// variance and contrast reads are issued only when some lane of the warp is
+// still alive (a warp-uniform vote), and only for the live words.
+constexpr int WPW = 8;
 
 __global__ void __launch_bounds__(32 * kWarpsPerBlock)
 k_screen(const __grid_constant__ ScreenArgs a) {
     const int lane = threadIdx.x & 31;
-    const int word = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const int w0 = (blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5)) * WPW;   // first word
     const int y = blockIdx.y;
-    if (word >= a.Wwords)
+    if (w0 >= a.Wwords)
         return;
-    const int x = word * 32 + lane;
+    const int x0 = w0 * 32 + lane;
+    // this candidate's element in every table; corners are fixed offsets from it
+    const int64_t e = (int64_t)y * a.pitch + x0 + kColOffset;
+    const uint32_t *L1 = a.L1 + e, *L2 = a.L2 + e, *T1 = a.T1 + e, *T2 = a.T2 + e;
+    uint32_t *out = a.mask + (int64_t)y * a.Wwords + w0;
+    const int64_t plane = (int64_t)a.H * a.Wwords;
+    const bool fm = a.features & SCR_F_MEAN, fv = a.features & SCR_F_VAR, fg = a.features & SCR_F_GRAD;
+    const bool store_word = lane < WPW && w0 + lane < a.Wwords;
+    const int xw_lo = w0 * 32, xw_hi = (w0 + WPW) * 32 - 1;   // span of this warp
+#pragma unroll 1
     for (int s = 0; s < a.n_scales; ++s) {
         const ScaleParam &p = a.sp[s];
-        bool keep = false;
-        if (y >= p.y_lo && y <= p.y_hi && x >= p.x_lo && x <= p.x_hi) {
-            const uint32_t S = square_sum(a.L1, a.pitchL, y, x, p.n) + diamond_sum(a.T1, a.pitchT, y, x, p.h);
-            keep = true;
-            if (a.features & SCR_F_MEAN)
-                keep = (int64_t)S >= p.S_lo && (int64_t)S <= p.S_hi;
-            if (keep && (a.features & SCR_F_VAR)) {
-                const uint64_t Q = (uint64_t)square_sum(a.L2, a.pitchL, y, x, p.n) +
-                                   (uint64_t)diamond_sum(a.T2, a.pitchT, y, x, p.h);
-                const int64_t V = (int64_t)((uint64_t)p.A * Q - (uint64_t)S * S);
-                keep = V >= p.V_lo && V <= p.V_hi;
+        uint32_t keep = 0;   // bit j: the candidate of word j is still alive
+        if (!p.empty && y >= p.y_lo && y <= p.y_hi) {   // block-uniform
+            uint32_t S[WPW];
+            // star sum: square (upright table) + diamond (cone table), Sec. 4
+            const Corners c(L1, T1, p.oL, p.oT);
+            if (xw_lo >= p.x_lo && xw_hi <= p.x_hi) {   // warp-uniform: every word valid
+#pragma unroll
+                for (int j = 0; j < WPW; ++j)
+                    S[j] = c.sum(j);
+                keep = (1u << WPW) - 1;
+            } else {
+                const uint32_t span = (uint32_t)(p.x_hi - p.x_lo);
+#pragma unroll
+                for (int j = 0; j < WPW; ++j) {
+                    S[j] = 0;
+                    if ((uint32_t)(x0 + 32 * j - p.x_lo) <= span) {
+                        S[j] = c.sum(j);
+                        keep |= 1u << j;
+                    }
+                }
             }
-            if (keep && (a.features & SCR_F_GRAD)) {
-                const uint32_t Si = square_sum(a.L1, a.pitchL, y, x, p.ni) + diamond_sum(a.T1, a.pitchT, y, x, p.hi);
-                const int64_t N = (int64_t)Si * p.Aring - ((int64_t)S - (int64_t)Si) * p.Ain;
-                keep = N >= p.N_lo && N <= p.N_hi;
+            if (fm) {
+                uint32_t k2 = 0;
+#pragma unroll
+                for (int j = 0; j < WPW; ++j)
+                    k2 |= ((S[j] - p.S_lo) <= p.S_rng ? 1u : 0u) << j;
+                keep &= k2;
+            }
+            if (fv && __any_sync(0xffffffffu, keep != 0)) {
+                // the square and diamond sums of I^2 are each below 2^32 but
+                // their sum may not be: add them in 64 bits
+                const Corners cq(L2, T2, p.oL, p.oT);
+#pragma unroll
+                for (int j = 0; j < WPW; ++j) {
+                    if (!((keep >> j) & 1u))
+                        continue;
+                    const int d = 32 * j;
+                    const uint32_t qs = ld(cq.p[0] + d) - ld(cq.p[1] + d) - ld(cq.p[2] + d) + ld(cq.p[3] + d);
+                    const uint32_t qd = ld(cq.p[4] + d) - ld(cq.p[5] + d) - ld(cq.p[6] + d) + ld(cq.p[7] + d);
+                    const uint64_t Q = (uint64_t)qs + qd;
+                    const uint64_t V = (uint64_t)p.A * Q - (uint64_t)S[j] * S[j];   // A^2 * variance
+                    if ((V - (uint64_t)p.V_lo) > p.V_rng)
+                        keep &= ~(1u << j);
+                }
+            }
+            if (fg && __any_sync(0xffffffffu, keep != 0)) {
+                const Corners ci(L1, T1, p.oLi, p.oTi);   // inner star
+#pragma unroll
+                for (int j = 0; j < WPW; ++j) {
+                    if (!((keep >> j) & 1u))
+                        continue;
+                    const uint32_t Si = ci.sum(j);
+                    const int64_t N = (int64_t)((uint64_t)Si * p.Aring) -
+                                      (int64_t)((uint64_t)(S[j] - Si) * p.Ain);
+                    if (((uint64_t)N - (uint64_t)p.N_lo) > p.N_rng)
+                        keep &= ~(1u << j);
+                }
             }
         }
-        const uint32_t bits = __ballot_sync(0xffffffffu, keep);
-        if (lane == 0)
-            a.mask[((int64_t)s * a.H + y) * a.Wwords + word] = bits;
+        uint32_t mine = 0;
+#pragma unroll
+        for (int j = 0; j < WPW; ++j) {
+            const uint32_t bits = __ballot_sync(0xffffffffu, (keep >> j) & 1u);
+            mine = lane == j ? bits : mine;
+        }
+        if (store_word)
+            out[s * plane + lane] = mine;
     }
 }
 
@@ -131,7 +214,8 @@ __global__ void k_template_sums(const TmplArgs a) {
 }  // namespace
 
 cudaError_t launch_screen(const ScreenArgs &args, cudaStream_t st, uint64_t *launches) {
-    dim3 grid((args.Wwords + kWarpsPerBlock - 1) / kWarpsPerBlock, args.H);
+    const int warps = (args.Wwords + WPW - 1) / WPW;
+    dim3 grid((warps + kWarpsPerBlock - 1) / kWarpsPerBlock, args.H);
     k_screen<<<grid, 32 * kWarpsPerBlock, 0, st>>>(args);
     if (launches)
         *launches += 1;

@@ -31,10 +31,9 @@ struct TableDesc {
 
 // Build geometry of the table kernels (see tables.cu).
 constexpr int kBand = 32;                  // rows per band
-constexpr int kTabThreads = 128;           // threads per tile
-constexpr int kSlotsPerThread = 8;         // columns per thread
+constexpr int kTileSlots = 1024;           // accumulator columns per tile
 constexpr int kHalo = kBand;               // halo columns on each side of a tile
-constexpr int kTileCols = kTabThreads * kSlotsPerThread - 2 * kHalo;   // 960 core columns
+constexpr int kTileCols = kTileSlots - 2 * kHalo;   // 960 core columns
 constexpr int kWinLo = -34;                // first carry column kept per band
 
 inline int64_t table_pitch_words(int64_t W) { return ((W + 16 + 31) / 32) * 32; }
@@ -44,18 +43,28 @@ inline int64_t table_pitch_words(int64_t W) { return ((W + 16 + 31) / 32) * 32; 
 // ---------------------------------------------------------------------------
 constexpr int kMaxScales = 32;
 
+// Per-scale record, precomputed on the host.  Corner offsets are element
+// offsets relative to the candidate's own element (y, x) of the table (both
+// table kinds share one pitch), so the kernel forms each corner address with
+// one multiply-add from a per-thread base pointer.  Interval tests use the
+// unsigned-range form (v - lo) <= (hi - lo).
 struct ScaleParam {
-    int32_t R, n, h, ni, hi;          // star radius, square half-side, diamond
-                                      // half-diagonal, and the inner star's n, h
     int32_t y_lo, y_hi, x_lo, x_hi;   // valid candidate rectangle (inclusive)
-    int32_t pad;
-    int64_t A, Ain, Aring;            // pooled areas
-    int64_t S_lo, S_hi, V_lo, V_hi, N_lo, N_hi;   // inclusive bounds
+    int32_t oL[4];                    // square corners: (+n+1,+n+1) (-n+1,+n+1) (+n+1,-n+1) (-n+1,-n+1)
+    int32_t oT[4];                    // diamond corners: (h+1, 1) (1, 1-h) (1, h+1) (1-h, 1)
+    int32_t oLi[4], oTi[4];           // the same for the inner star (radius floor(R/2))
+    uint32_t S_lo, S_rng;             // mean:     (S - S_lo) <= S_rng        (32-bit)
+    uint32_t A, Ain, Aring;           // pooled areas
+    uint32_t empty;                   // 1: an interval is empty, nothing survives
+    int64_t V_lo;
+    uint64_t V_rng;                   // variance: (V - V_lo) <= V_rng       (64-bit)
+    int64_t N_lo;
+    uint64_t N_rng;                   // contrast: (N - N_lo) <= N_rng       (64-bit)
 };
 
 struct ScreenArgs {
     const uint32_t *L1, *L2, *T1, *T2;   // low planes (window sums read mod 2^32)
-    int64_t pitchL, pitchT;              // words per row
+    int64_t pitch;                       // words per row (all four tables)
     int32_t H, W, Wwords, n_scales;
     uint32_t features;
     uint32_t *mask;

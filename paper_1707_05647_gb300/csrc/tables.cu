@@ -22,7 +22,7 @@
 //   k_tab_carry   per column / diagonal index: exclusive prefix over bands.
 //   k_tab_prefix  per band: prefix along the row of those sums -> the carry
 //                 rows L(r0, .), D1(r0-1, .), D2(r0-1, .) and per-tile row carries.
-//   k_tab_write   per tile: walk the band's rows; each thread owns 8 adjacent
+//   k_tab_write   per tile: walk the band's rows; each thread owns 4 adjacent
 //                 columns, keeps L, D1, D2 for them in registers; per row it
 //                 scans the pixels into P (warp shuffles + one block step), adds
 //                 P to L, moves D1 one column left and D2 one column right
@@ -40,10 +40,12 @@ namespace scr {
 namespace {
 
 constexpr int B = kBand;
-constexpr int NT = kTabThreads;
 constexpr int CW = kTileCols;
 constexpr int HALO = kHalo;
-constexpr int SLOTS = NT * kSlotsPerThread;  // 1024 accumulator columns per tile
+constexpr int SLOTS = kTileSlots;            // 1024 accumulator columns per tile
+constexpr int NT = 512;                      // threads of k_tab_reduce
+constexpr int WT = 256;                      // threads of k_tab_write (4 columns each)
+constexpr int K = SLOTS / WT;                // columns per k_tab_write thread
 constexpr int CL = kWinLo;                   // first carry column
 
 struct Geometry {
@@ -125,72 +127,73 @@ struct ReduceArgs {
     int aligned8;
 };
 
+__device__ __forceinline__ uint2 load8(const uint8_t *img, int64_t pitch, int H, int W, int aligned8, int y,
+                                       int cs) {
+    if (y < H && aligned8 && cs >= 0 && cs + 8 <= W)
+        return __ldg(reinterpret_cast<const uint2 *>(img + (int64_t)y * pitch + cs));
+    uint32_t lo = 0, hi = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int x = cs + k;
+        const uint32_t b = (y < H && x >= 0 && x < W) ? (uint32_t)__ldg(img + (int64_t)y * pitch + x) : 0u;
+        if (k < 4)
+            lo |= b << (8 * k);
+        else
+            hi |= b << (8 * (k - 4));
+    }
+    return make_uint2(lo, hi);
+}
+
 __global__ void __launch_bounds__(NT) k_tab_reduce(const ReduceArgs a) {
     __shared__ __align__(16) uint8_t tile[B][SLOTS];
-    __shared__ uint32_t part1[B][NT / 32], part2[B][NT / 32];
     const Geometry &g = a.g;
     const int j = blockIdx.x, i = blockIdx.y, t = threadIdx.x;
     const int r0 = i * B;
     const int c0 = j * CW;
     const int c1 = min(c0 + CW, g.W);
-    const int base = c0 - HALO;          // smem column 0
-    const int cs = base + 8 * t;         // this thread's 8 columns
-    // load the band (zero outside the image)
-    for (int rr = 0; rr < B; ++rr) {
-        const int y = r0 + rr;
-        uint2 w;
-        if (y < g.H && a.aligned8 && cs >= 0 && cs + 8 <= g.W) {
-            w = *reinterpret_cast<const uint2 *>(a.img + (int64_t)y * a.pitch + cs);
-        } else {
-            uint32_t lo = 0, hi = 0;
+    const int base = c0 - HALO;                  // smem column 0
+    // load the band (zero outside the image): thread t covers 8 columns of
+    // B / (NT / 128) rows, all loads in flight
+    {
+        constexpr int RPT = B / (NT / 128);      // rows per thread
+        const int cs = base + 8 * (t & 127);
+        const int rb = (t >> 7) * RPT;
+        uint2 w[RPT];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int x = cs + k;
-                const uint32_t b = (y < g.H && x >= 0 && x < g.W) ? a.img[(int64_t)y * a.pitch + x] : 0u;
-                if (k < 4)
-                    lo |= b << (8 * k);
-                else
-                    hi |= b << (8 * (k - 4));
-            }
-            w = make_uint2(lo, hi);
-        }
-        *reinterpret_cast<uint2 *>(&tile[rr][8 * t]) = w;
-        uint32_t v[8];
+        for (int k = 0; k < RPT; ++k)
+            w[k] = load8(a.img, a.pitch, g.H, g.W, a.aligned8, r0 + rb + k, cs);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            v[k] = (w.x >> (8 * k)) & 0xffu;
-            v[k + 4] = (w.y >> (8 * k)) & 0xffu;
-        }
-        // row sum over the shifted chunk [c0-HALO, c0-HALO+CW) (threads 0..CW/8-1)
+        for (int k = 0; k < RPT; ++k)
+            *reinterpret_cast<uint2 *>(&tile[rb + k][8 * (t & 127)]) = w[k];
+    }
+    __syncthreads();
+    // row sums over the shifted chunk [c0-HALO, c0-HALO+CW): NT/B threads per row
+    {
+        constexpr int TPR = NT / B;                  // threads per row (16)
+        constexpr int WPT = CW / 4 / TPR;            // 32-bit words per thread (15)
+        const int rr = t / TPR, part = t % TPR;
+        const uint32_t *row = reinterpret_cast<const uint32_t *>(&tile[rr][0]) + part * WPT;
         uint32_t s1 = 0, s2 = 0;
-        if (t < CW / 8) {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                s1 += v[k];
-                s2 += v[k] * v[k];
+        for (int q = 0; q < WPT; ++q) {
+            const uint32_t w4 = row[q];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t v = (w4 >> (8 * k)) & 0xffu;
+                s1 += v;
+                s2 += v * v;
             }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
+        for (int o = 1; o < TPR; o <<= 1) {
             s1 += __shfl_xor_sync(0xffffffffu, s1, o);
             s2 += __shfl_xor_sync(0xffffffffu, s2, o);
         }
-        if ((t & 31) == 0) {
-            part1[rr][t >> 5] = s1;
-            part2[rr][t >> 5] = s2;
+        if (part == 0) {
+            const size_t o = ((size_t)i * g.m + j) * B + rr;
+            a.s.rs1[o] = s1;
+            a.s.rs2[o] = s2;
         }
-    }
-    __syncthreads();
-    const size_t rsb = ((size_t)i * g.m + j) * B;
-    if (t < B) {
-        uint32_t s1 = 0, s2 = 0;
-#pragma unroll
-        for (int w = 0; w < NT / 32; ++w) {
-            s1 += part1[t][w];
-            s2 += part2[t][w];
-        }
-        a.s.rs1[rsb + t] = s1;
-        a.s.rs2[rsb + t] = s2;
     }
     const size_t W = g.W, WD = g.W + B - 1;
     // column sums
@@ -270,8 +273,10 @@ __device__ __forceinline__ void carry_contrib(const CarryArgs &a, int part, int 
     }
 }
 
-__global__ void __launch_bounds__(1024) k_tab_carry(const CarryArgs a) {
-    __shared__ uint32_t sum1[32][33], sum2[32][33];
+constexpr int CG = 8;   // band groups per carry block
+
+__global__ void __launch_bounds__(32 * CG) k_tab_carry(const CarryArgs a) {
+    __shared__ uint32_t sum1[CG][33], sum2[CG][33];
     const Geometry &g = a.g;
     const int lane = threadIdx.x, grp = threadIdx.y;
     int chunk = blockIdx.x, part, nlanes;
@@ -289,10 +294,11 @@ __global__ void __launch_bounds__(1024) k_tab_carry(const CarryArgs a) {
     }
     const int idx = chunk * 32 + lane;
     const bool live = idx < nlanes;
-    const int q = (g.n + 31) / 32;
+    const int q = (g.n + CG - 1) / CG;
     const int b0 = grp * q, b1 = min(g.n, b0 + q);
     uint32_t t1 = 0, t2 = 0;
     if (live)
+#pragma unroll 8
         for (int b = b0; b < b1; ++b) {
             uint32_t v1, v2;
             carry_contrib(a, part, idx, b, v1, v2);
@@ -304,7 +310,7 @@ __global__ void __launch_bounds__(1024) k_tab_carry(const CarryArgs a) {
     __syncthreads();
     if (grp == 0) {
         uint32_t r1 = 0, r2 = 0;
-        for (int k = 0; k < 32; ++k) {
+        for (int k = 0; k < CG; ++k) {
             const uint32_t u1 = sum1[k][lane], u2 = sum2[k][lane];
             sum1[k][lane] = r1;
             sum2[k][lane] = r2;
@@ -354,112 +360,103 @@ struct PrefixArgs {
     Scratch s;
 };
 
-__device__ __forceinline__ uint64_t block_excl_scan_1024(uint64_t v, uint64_t *sh, uint64_t &total) {
-    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    uint64_t inc = v;
+__device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v, int lane) {
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const uint64_t u = __shfl_up_sync(0xffffffffu, inc, o);
+        const uint64_t u = __shfl_up_sync(0xffffffffu, v, o);
         if (lane >= o)
-            inc += u;
+            v += u;
     }
-    if (lane == 31)
-        sh[w] = inc;
-    __syncthreads();
-    if (w == 0) {
-        uint64_t s = sh[lane];
-        uint64_t si = s;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint64_t u = __shfl_up_sync(0xffffffffu, si, o);
-            if (lane >= o)
-                si += u;
-        }
-        sh[32 + lane] = si - s;
-        if (lane == 31)
-            sh[64] = si;
-    }
-    __syncthreads();
-    const uint64_t res = sh[32 + w] + inc - v;
-    total = sh[64];
-    __syncthreads();
-    return res;
+    return v;
 }
 
+// One CTA per (band, sequence).  Each warp scans a contiguous segment of the
+// row 32 entries at a time (coalesced), after one pass that sums the segment.
+constexpr int PT = 256;
+
 template <typename TS, typename TQ>
-__global__ void __launch_bounds__(1024) k_tab_prefix(const PrefixArgs a) {
-    __shared__ uint64_t sh[80];
+__global__ void __launch_bounds__(PT) k_tab_prefix(const PrefixArgs a) {
+    __shared__ uint64_t wsum[PT / 32], red[PT / 32];
     const Geometry &g = a.g;
-    const int i = blockIdx.x, t = threadIdx.x;
+    const int i = blockIdx.x, q = blockIdx.y, t = threadIdx.x, lane = t & 31, w = t >> 5;
     const int r0 = i * B;
-    const size_t XW = g.XW;
-    // triangle: sum of full anti-diagonals d < r0 - 1 + CL (all inside rows < r0)
-    uint64_t tr1 = 0, tr2 = 0;
-    {
+    const int XW = g.XW;
+    if (q == 6) {   // row carries per tile: sum of the row sums of the tiles to the left
+        if (t < B) {
+            uint32_t c1 = 0, c2 = 0;
+            for (int j = 0; j < g.m; ++j) {
+                const size_t o = ((size_t)i * g.m + j) * B + t;
+                a.s.rc1[o] = c1;
+                a.s.rc2[o] = c2;
+                c1 += a.s.rs1[o];
+                c2 += a.s.rs2[o];
+            }
+        }
+        return;
+    }
+    // q: 0,1 = L (column prefix), 2,3 = D1 (anti-diagonal), 4,5 = D2 (diagonal);
+    // even = sum table, odd = sum-of-squares table
+    const uint32_t *src;
+    void *dst;
+    switch (q) {
+        case 0: src = a.s.csx1; dst = a.s.xl1; break;
+        case 1: src = a.s.csx2; dst = a.s.xl2; break;
+        case 2: src = a.s.adx1; dst = a.s.x11; break;
+        case 3: src = a.s.adx2; dst = a.s.x12; break;
+        case 4: src = a.s.mdx1; dst = a.s.x21; break;
+        default: src = a.s.mdx2; dst = a.s.x22; break;
+    }
+    auto value = [&](int k) -> uint64_t {
+        if (k >= XW)
+            return 0;
+        if (q < 2) {
+            const int c = k + CL;
+            return (c >= 0 && c < g.W) ? src[(size_t)i * g.W + c] : 0u;
+        }
+        return src[(size_t)i * XW + k];
+    };
+    const int seg = ((XW + PT / 32 - 1) / (PT / 32) + 31) / 32 * 32;   // entries per warp
+    const int k0 = w * seg, k1 = min(XW, k0 + seg);
+    // pass 1: segment sums (+ the anti-diagonals above the band for D1)
+    uint64_t part = 0;
+    for (int k = k0 + lane; k < k1; k += 32)
+        part += value(k);
+    uint64_t tri = 0;
+    if (q == 2 || q == 3) {
+        const uint32_t *adf = q == 2 ? a.s.adf1 : a.s.adf2;
         const int dend = r0 - 1 + CL;
-        uint64_t p1 = 0, p2 = 0;
-        for (int d = t; d < dend; d += 1024) {
-            p1 += a.s.adf1[d - g.DMIN];
-            p2 += a.s.adf2[d - g.DMIN];
-        }
-        uint64_t tot;
-        block_excl_scan_1024(p1, sh, tot);
-        tr1 = tot;
-        block_excl_scan_1024(p2, sh, tot);
-        tr2 = tot;
+        for (int d = t; d < dend; d += PT)
+            tri += adf[d - g.DMIN];
     }
-    // six inclusive scans along c in [CL, W+1]
-    const int per = (int)((XW + 1023) / 1024);
-    const int k0 = t * per, k1 = min((int)XW, k0 + per);
-    uint64_t loc[6] = {0, 0, 0, 0, 0, 0};
-    for (int k = k0; k < k1; ++k) {
-        const int c = k + CL;
-        if (c >= 0 && c < g.W) {
-            loc[0] += a.s.csx1[(size_t)i * g.W + c];
-            loc[1] += a.s.csx2[(size_t)i * g.W + c];
-        }
-        loc[2] += a.s.adx1[(size_t)i * XW + k];
-        loc[3] += a.s.adx2[(size_t)i * XW + k];
-        loc[4] += a.s.mdx1[(size_t)i * XW + k];
-        loc[5] += a.s.mdx2[(size_t)i * XW + k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        part += __shfl_xor_sync(0xffffffffu, part, o);
+        tri += __shfl_xor_sync(0xffffffffu, tri, o);
     }
-    uint64_t run[6];
-    for (int q = 0; q < 6; ++q) {
-        uint64_t tot;
-        run[q] = block_excl_scan_1024(loc[q], sh, tot);
+    if (lane == 0) {
+        wsum[w] = part;
+        red[w] = tri;
     }
-    run[2] += tr1;
-    run[3] += tr2;
-    TS *xl1 = (TS *)a.s.xl1, *x11 = (TS *)a.s.x11, *x21 = (TS *)a.s.x21;
-    TQ *xl2 = (TQ *)a.s.xl2, *x12 = (TQ *)a.s.x12, *x22 = (TQ *)a.s.x22;
-    for (int k = k0; k < k1; ++k) {
-        const int c = k + CL;
-        if (c >= 0 && c < g.W) {
-            run[0] += a.s.csx1[(size_t)i * g.W + c];
-            run[1] += a.s.csx2[(size_t)i * g.W + c];
-        }
-        run[2] += a.s.adx1[(size_t)i * XW + k];
-        run[3] += a.s.adx2[(size_t)i * XW + k];
-        run[4] += a.s.mdx1[(size_t)i * XW + k];
-        run[5] += a.s.mdx2[(size_t)i * XW + k];
-        const size_t o = (size_t)i * XW + k;
-        xl1[o] = (TS)run[0];
-        xl2[o] = (TQ)run[1];
-        x11[o] = (TS)run[2];
-        x12[o] = (TQ)run[3];
-        x21[o] = (TS)run[4];
-        x22[o] = (TQ)run[5];
+    __syncthreads();
+    uint64_t carry = 0;
+    for (int u = 0; u < PT / 32; ++u) {
+        carry += red[u];
+        if (u < w)
+            carry += wsum[u];
     }
-    // row carries per tile: sum of row sums of the tiles to the left
-    if (t < B) {
-        uint32_t c1 = 0, c2 = 0;
-        for (int j = 0; j < g.m; ++j) {
-            const size_t o = ((size_t)i * g.m + j) * B + t;
-            a.s.rc1[o] = c1;
-            a.s.rc2[o] = c2;
-            c1 += a.s.rs1[o];
-            c2 += a.s.rs2[o];
+    // pass 2: scan and store in table width
+    for (int kb = k0; kb < k1; kb += 32) {
+        const int k = kb + lane;
+        const uint64_t v = value(k);
+        const uint64_t incl = warp_incl_scan(v, lane);
+        if (k < k1) {
+            const uint64_t out = carry + incl;
+            if (q & 1)
+                ((TQ *)dst)[(size_t)i * XW + k] = (TQ)out;
+            else
+                ((TS *)dst)[(size_t)i * XW + k] = (TS)out;
         }
+        carry += __shfl_sync(0xffffffffu, incl, 31);
     }
 }
 
@@ -477,24 +474,13 @@ struct WriteArgs {
 };
 
 template <typename T>
-__device__ __forceinline__ void store8(uint32_t *lo, uint32_t *hi, int64_t word, const T (&v)[8]) {
-    if (sizeof(T) == 4) {
-        uint4 a = make_uint4((uint32_t)v[0], (uint32_t)v[1], (uint32_t)v[2], (uint32_t)v[3]);
-        uint4 b = make_uint4((uint32_t)v[4], (uint32_t)v[5], (uint32_t)v[6], (uint32_t)v[7]);
-        *reinterpret_cast<uint4 *>(lo + word) = a;
-        *reinterpret_cast<uint4 *>(lo + word + 4) = b;
-    } else {
-        uint4 a = make_uint4((uint32_t)v[0], (uint32_t)v[1], (uint32_t)v[2], (uint32_t)v[3]);
-        uint4 b = make_uint4((uint32_t)v[4], (uint32_t)v[5], (uint32_t)v[6], (uint32_t)v[7]);
-        uint4 c = make_uint4((uint32_t)((uint64_t)v[0] >> 32), (uint32_t)((uint64_t)v[1] >> 32),
-                             (uint32_t)((uint64_t)v[2] >> 32), (uint32_t)((uint64_t)v[3] >> 32));
-        uint4 d = make_uint4((uint32_t)((uint64_t)v[4] >> 32), (uint32_t)((uint64_t)v[5] >> 32),
-                             (uint32_t)((uint64_t)v[6] >> 32), (uint32_t)((uint64_t)v[7] >> 32));
-        *reinterpret_cast<uint4 *>(lo + word) = a;
-        *reinterpret_cast<uint4 *>(lo + word + 4) = b;
-        *reinterpret_cast<uint4 *>(hi + word) = c;
-        *reinterpret_cast<uint4 *>(hi + word + 4) = d;
-    }
+__device__ __forceinline__ void store4(uint32_t *lo, uint32_t *hi, int64_t word, const T (&v)[K]) {
+    *reinterpret_cast<uint4 *>(lo + word) =
+        make_uint4((uint32_t)v[0], (uint32_t)v[1], (uint32_t)v[2], (uint32_t)v[3]);
+    if (sizeof(T) == 8)
+        *reinterpret_cast<uint4 *>(hi + word) =
+            make_uint4((uint32_t)((uint64_t)v[0] >> 32), (uint32_t)((uint64_t)v[1] >> 32),
+                       (uint32_t)((uint64_t)v[2] >> 32), (uint32_t)((uint64_t)v[3] >> 32));
 }
 
 template <typename T>
@@ -504,11 +490,29 @@ __device__ __forceinline__ void store1(uint32_t *lo, uint32_t *hi, int64_t word,
         hi[word] = (uint32_t)((uint64_t)v >> 32);
 }
 
+__device__ __forceinline__ uint32_t load4(const uint8_t *img, int64_t pitch, int H, int W, int aligned4, int y,
+                                          int cs) {
+    if (y < H && aligned4 && cs >= 0 && cs + 4 <= W)
+        return __ldg(reinterpret_cast<const uint32_t *>(img + (int64_t)y * pitch + cs));
+    uint32_t w = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int x = cs + k;
+        const uint32_t b = (y < H && x >= 0 && x < W) ? (uint32_t)__ldg(img + (int64_t)y * pitch + x) : 0u;
+        w |= b << (8 * k);
+    }
+    return w;
+}
+
+// Each thread owns K = 4 adjacent columns, so every warp store writes 512
+// contiguous bytes of one plane.
 template <typename TS, typename TQ>
-__global__ void __launch_bounds__(NT) k_tab_write(const WriteArgs a) {
-    __shared__ uint32_t wt1[2][NT / 32], wt2[2][NT / 32];      // warp totals
-    __shared__ TS nb_d1a[2][NT / 32], nb_d2a[2][NT / 32];      // warp-edge neighbours
-    __shared__ TQ nb_d1b[2][NT / 32], nb_d2b[2][NT / 32];
+__global__ void __launch_bounds__(WT) k_tab_write(const WriteArgs a) {
+    constexpr int NW = WT / 32;
+    __shared__ uint32_t wt1[2][NW], wt2[2][NW];                // warp totals
+    __shared__ TS nb_d1a[2][NW], nb_d2a[2][NW];                // warp-edge neighbours
+    __shared__ TQ nb_d1b[2][NW], nb_d2b[2][NW];
+    __shared__ uint32_t rc1[B], rc2[B];
     const Geometry &g = a.g;
     const int j = blockIdx.x, i = blockIdx.y, t = threadIdx.x;
     const int lane = t & 31, w = t >> 5;
@@ -516,25 +520,25 @@ __global__ void __launch_bounds__(NT) k_tab_write(const WriteArgs a) {
     const int rows = min(B, g.H - r0);
     const int c0 = j * CW;
     const bool last = (j == g.m - 1);
-    const int cs = c0 - HALO + 8 * t;
+    const int cs = c0 - HALO + K * t;
     const int cTmax = last ? g.W : c0 + CW - 1;     // last T column this tile writes
     const int cLmax = last ? g.W - 1 : c0 + CW - 1; // last L column (b = c+1 <= W)
     const bool wT = cs >= c0 && cs <= cTmax;
     const bool wL = cs >= c0 && cs <= cLmax;
-    const bool wEdge = (j == 0) && (cs == -8);      // column c = -1 (b = 0)
+    const bool wEdge = (j == 0) && (cs == -K);      // holds column c = -1 (b = 0)
 
     // carries from the row above the band
-    TS L1a[8], D1a[8], D2a[8];
-    TQ L2a[8], D1b[8], D2b[8];
+    TS L1a[K], D1a[K], D2a[K];
+    TQ L2a[K], D1b[K], D2b[K];
     {
         const size_t XW = g.XW;
         const TS *xl1 = (const TS *)a.s.xl1, *x11 = (const TS *)a.s.x11, *x21 = (const TS *)a.s.x21;
         const TQ *xl2 = (const TQ *)a.s.xl2, *x12 = (const TQ *)a.s.x12, *x22 = (const TQ *)a.s.x22;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < K; ++k) {
             int c = cs + k;
             c = c < CL ? CL : (c > g.W + 1 ? g.W + 1 : c);
-            const size_t o = (size_t)i * XW + (c - CL);
+            const size_t o = (size_t)i * XW + (size_t)(c - CL);
             L1a[k] = xl1[o];
             L2a[k] = xl2[o];
             D1a[k] = x11[o];
@@ -545,15 +549,15 @@ __global__ void __launch_bounds__(NT) k_tab_write(const WriteArgs a) {
     }
     // row 0 of every table is zero
     if (i == 0) {
-        TS z1[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        TQ z2[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        TS z1[K] = {0, 0, 0, 0};
+        TQ z2[K] = {0, 0, 0, 0};
         if (wL) {
-            store8(a.L1lo, a.L1hi, cs + 1 + kColOffset, z1);
-            store8(a.L2lo, a.L2hi, cs + 1 + kColOffset, z2);
+            store4(a.L1lo, a.L1hi, cs + 1 + kColOffset, z1);
+            store4(a.L2lo, a.L2hi, cs + 1 + kColOffset, z2);
         }
         if (wT) {
-            store8(a.T1lo, a.T1hi, cs + 1 + kColOffset, z1);
-            store8(a.T2lo, a.T2hi, cs + 1 + kColOffset, z2);
+            store4(a.T1lo, a.T1hi, cs + 1 + kColOffset, z1);
+            store4(a.T2lo, a.T2hi, cs + 1 + kColOffset, z2);
         }
         if (wEdge) {
             store1(a.L1lo, a.L1hi, kColOffset, (TS)0);
@@ -562,37 +566,32 @@ __global__ void __launch_bounds__(NT) k_tab_write(const WriteArgs a) {
             store1(a.T2lo, a.T2hi, kColOffset, (TQ)0);
         }
     }
-    const uint32_t *rc1 = a.s.rc1 + ((size_t)i * g.m + j) * B;
-    const uint32_t *rc2 = a.s.rc2 + ((size_t)i * g.m + j) * B;
+    if (t < B) {
+        rc1[t] = a.s.rc1[((size_t)i * g.m + j) * B + t];
+        rc2[t] = a.s.rc2[((size_t)i * g.m + j) * B + t];
+    }
+    __syncthreads();
+    const int aligned4 = a.aligned8;
+    // pixel rows are prefetched two rows ahead
+    uint32_t nxt0 = load4(a.img, a.pitch, g.H, g.W, aligned4, r0, cs);
+    uint32_t nxt1 = load4(a.img, a.pitch, g.H, g.W, aligned4, r0 + 1, cs);
 
     for (int rr = 0; rr < rows; ++rr) {
         const int y = r0 + rr;
         const int par = rr & 1;
-        uint32_t v[8];
-        if (a.aligned8 && cs >= 0 && cs + 8 <= g.W) {
-            const uint2 q = __ldg(reinterpret_cast<const uint2 *>(a.img + (int64_t)y * a.pitch + cs));
+        const uint32_t q = nxt0;
+        nxt0 = nxt1;
+        if (rr + 2 < rows)
+            nxt1 = load4(a.img, a.pitch, g.H, g.W, aligned4, y + 2, cs);
+        uint32_t p1[K], p2[K];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                v[k] = (q.x >> (8 * k)) & 0xffu;
-                v[k + 4] = (q.y >> (8 * k)) & 0xffu;
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int x = cs + k;
-                v[k] = (x >= 0 && x < g.W) ? (uint32_t)__ldg(a.img + (int64_t)y * a.pitch + x) : 0u;
-            }
-        }
-        uint32_t p1[8], p2[8];
-        p1[0] = v[0];
-        p2[0] = v[0] * v[0];
-#pragma unroll
-        for (int k = 1; k < 8; ++k) {
-            p1[k] = p1[k - 1] + v[k];
-            p2[k] = p2[k - 1] + v[k] * v[k];
+        for (int k = 0; k < K; ++k) {
+            const uint32_t v = (q >> (8 * k)) & 0xffu;
+            p1[k] = (k ? p1[k - 1] : 0u) + v;
+            p2[k] = (k ? p2[k - 1] : 0u) + v * v;
         }
         // warp inclusive scan of the thread totals
-        uint32_t s1 = p1[7], s2 = p2[7];
+        uint32_t s1 = p1[K - 1], s2 = p2[K - 1];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t u1 = __shfl_up_sync(0xffffffffu, s1, o);
@@ -606,33 +605,36 @@ __global__ void __launch_bounds__(NT) k_tab_write(const WriteArgs a) {
             wt1[par][w] = s1;
             wt2[par][w] = s2;
         }
-        // old D1[0] and D2[7] of warp-edge threads for the neighbouring warps
+        // old D1[0] and D2[K-1] of warp-edge threads for the neighbouring warps
         if (lane == 0) {
             nb_d1a[par][w] = D1a[0];
             nb_d1b[par][w] = D1b[0];
         }
         if (lane == 31) {
-            nb_d2a[par][w] = D2a[7];
-            nb_d2b[par][w] = D2b[7];
+            nb_d2a[par][w] = D2a[K - 1];
+            nb_d2b[par][w] = D2b[K - 1];
         }
         // in-warp neighbours (before the update)
         TS n1a = __shfl_down_sync(0xffffffffu, D1a[0], 1);
         TQ n1b = __shfl_down_sync(0xffffffffu, D1b[0], 1);
-        TS n2a = __shfl_up_sync(0xffffffffu, D2a[7], 1);
-        TQ n2b = __shfl_up_sync(0xffffffffu, D2b[7], 1);
+        TS n2a = __shfl_up_sync(0xffffffffu, D2a[K - 1], 1);
+        TQ n2b = __shfl_up_sync(0xffffffffu, D2b[K - 1], 1);
         __syncthreads();
-        uint32_t e1 = rc1[rr] + s1 - p1[7], e2 = rc2[rr] + s2 - p2[7];
-        for (int q = 0; q < w; ++q) {
-            e1 += wt1[par][q];
-            e2 += wt2[par][q];
+        uint32_t e1 = rc1[rr] + s1 - p1[K - 1], e2 = rc2[rr] + s2 - p2[K - 1];
+#pragma unroll
+        for (int qq = 0; qq < NW; ++qq) {
+            if (qq < w) {
+                e1 += wt1[par][qq];
+                e2 += wt2[par][qq];
+            }
         }
         if (lane == 31) {
-            if (w + 1 < NT / 32) {
+            if (w + 1 < NW) {
                 n1a = nb_d1a[par][w + 1];
                 n1b = nb_d1b[par][w + 1];
             } else {            // rightmost column of the tile: D1 is constant there
-                n1a = D1a[7];   // (exact for the last tile, whose right end is past W)
-                n1b = D1b[7];
+                n1a = D1a[K - 1];   // (exact for the last tile, whose right end is past W)
+                n1b = D1b[K - 1];
             }
         }
         if (lane == 0) {
@@ -645,17 +647,15 @@ __global__ void __launch_bounds__(NT) k_tab_write(const WriteArgs a) {
             }
         }
         // P(y, c) for this thread's columns; e = P(y, cs-1)
-        uint32_t P1[8], P2[8];
+        uint32_t P1[K], P2[K];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < K; ++k) {
             P1[k] = e1 + p1[k];
             P2[k] = e2 + p2[k];
         }
-        TS T1v[8];
-        TQ T2v[8];
         // D2 moves one column right: D2(y, c) = P(y, c-1) + D2(y-1, c-1)
 #pragma unroll
-        for (int k = 7; k >= 1; --k) {
+        for (int k = K - 1; k >= 1; --k) {
             D2a[k] = (TS)P1[k - 1] + D2a[k - 1];
             D2b[k] = (TQ)P2[k - 1] + D2b[k - 1];
         }
@@ -663,14 +663,16 @@ __global__ void __launch_bounds__(NT) k_tab_write(const WriteArgs a) {
         D2b[0] = (TQ)e2 + n2b;
         // D1 moves one column left: D1(y, c) = P(y, c) + D1(y-1, c+1)
 #pragma unroll
-        for (int k = 0; k < 7; ++k) {
+        for (int k = 0; k < K - 1; ++k) {
             D1a[k] = (TS)P1[k] + D1a[k + 1];
             D1b[k] = (TQ)P2[k] + D1b[k + 1];
         }
-        D1a[7] = (TS)P1[7] + n1a;
-        D1b[7] = (TQ)P2[7] + n1b;
+        D1a[K - 1] = (TS)P1[K - 1] + n1a;
+        D1b[K - 1] = (TQ)P2[K - 1] + n1b;
+        TS T1v[K];
+        TQ T2v[K];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < K; ++k) {
             L1a[k] += (TS)P1[k];
             L2a[k] += (TQ)P2[k];
             T1v[k] = D1a[k] - D2a[k];
@@ -679,18 +681,18 @@ __global__ void __launch_bounds__(NT) k_tab_write(const WriteArgs a) {
         const int64_t rowL = (int64_t)(y + 1) * a.pL + kColOffset;
         const int64_t rowT = (int64_t)(y + 1) * a.pT + kColOffset;
         if (wL) {
-            store8(a.L1lo, a.L1hi, rowL + cs + 1, L1a);
-            store8(a.L2lo, a.L2hi, rowL + cs + 1, L2a);
+            store4(a.L1lo, a.L1hi, rowL + cs + 1, L1a);
+            store4(a.L2lo, a.L2hi, rowL + cs + 1, L2a);
         }
         if (wT) {
-            store8(a.T1lo, a.T1hi, rowT + cs + 1, T1v);
-            store8(a.T2lo, a.T2hi, rowT + cs + 1, T2v);
+            store4(a.T1lo, a.T1hi, rowT + cs + 1, T1v);
+            store4(a.T2lo, a.T2hi, rowT + cs + 1, T2v);
         }
         if (wEdge) {   // b = 0: L is zero, T is cone(y, -1) = D1(y, -1)
             store1(a.L1lo, a.L1hi, rowL, (TS)0);
             store1(a.L2lo, a.L2hi, rowL, (TQ)0);
-            store1(a.T1lo, a.T1hi, rowT, T1v[7]);
-            store1(a.T2lo, a.T2hi, rowT, T2v[7]);
+            store1(a.T1lo, a.T1hi, rowT, T1v[K - 1]);
+            store1(a.T2lo, a.T2hi, rowT, T2v[K - 1]);
         }
     }
 }
@@ -703,12 +705,12 @@ cudaError_t launch_all(const Geometry &g, const Scratch &s, const uint8_t *img, 
     k_tab_reduce<<<dim3(g.m, g.n), NT, 0, st>>>(ra);
     CarryArgs ca{g, s, (g.W + 31) / 32, (g.DN + 31) / 32};
     const int chunks = ca.chunksCS + ca.chunksAD + (g.FN + 31) / 32;
-    k_tab_carry<<<chunks, dim3(32, 32), 0, st>>>(ca);
+    k_tab_carry<<<chunks, dim3(32, CG), 0, st>>>(ca);
     PrefixArgs pa{g, s};
-    k_tab_prefix<TS, TQ><<<g.n, 1024, 0, st>>>(pa);
+    k_tab_prefix<TS, TQ><<<dim3(g.n, 7), PT, 0, st>>>(pa);
     WriteArgs wa{img, pitch, g, s, L1.lo, L1.hi, L2.lo, L2.hi, T1.lo, T1.hi, T2.lo, T2.hi,
                  L1.pitch, T1.pitch, aligned8};
-    k_tab_write<TS, TQ><<<dim3(g.m, g.n), NT, 0, st>>>(wa);
+    k_tab_write<TS, TQ><<<dim3(g.m, g.n), WT, 0, st>>>(wa);
     return cudaGetLastError();
 }
 
@@ -727,7 +729,7 @@ cudaError_t launch_build_tables(const uint8_t *img, int H, int W, int64_t pitch,
     Geometry g(H, W);
     Scratch s;
     carve(g, L1.bits, L2.bits, &s, (char *)scratch);
-    const int aligned8 = ((uintptr_t)img % 8 == 0) && (pitch % 8 == 0);
+    const int aligned8 = ((uintptr_t)img % 8 == 0) && (pitch % 8 == 0);   // also 4-byte aligned
     cudaError_t e;
     const bool s64 = L1.bits == 64, q64 = L2.bits == 64;
     if (!s64 && !q64)
