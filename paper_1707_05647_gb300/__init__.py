@@ -80,6 +80,8 @@ def load(build_if_missing: bool = True):
         "screen_bounds": ([vp, ctypes.POINTER(_Params), ctypes.POINTER(_Bounds)], ctypes.c_int),
         "screen_features": ([vp, vp, vp, ctypes.POINTER(_Params), vp, u64, vp], ctypes.c_int),
         "compact_mask": ([vp, vp, i32, i32, i32, vp, u64, vp, vp], ctypes.c_int),
+        "compact_mask_noalloc": ([vp, i32, i32, i32, vp, u64, vp, vp], ctypes.c_int),
+        "compact_mask_noalloc_error": ([], ctypes.c_char_p),
         "screen_positions": ([vp, vp, vp, ctypes.POINTER(_Params), vp, u64, vp, u64, ctypes.POINTER(u64), vp],
                              ctypes.c_int),
         "screen_positions_async": ([vp, vp, vp, ctypes.POINTER(_Params), vp, u64, vp, u64, vp, vp], ctypes.c_int),
@@ -97,7 +99,8 @@ def load(build_if_missing: bool = True):
 def exported_symbols():
     return ["screen_init", "screen_shutdown", "screen_last_error", "screen_stats", "build_tables",
             "tables_view", "tables_copy_to_host", "tables_release", "template_features", "template_sums",
-            "template_release", "screen_bounds", "screen_features", "compact_mask", "screen_positions",
+            "template_release", "screen_bounds", "screen_features", "compact_mask", "compact_mask_noalloc",
+            "compact_mask_noalloc_error", "screen_positions",
             "screen_positions_async", "screen_host"]
 
 
@@ -237,6 +240,19 @@ def screen_features(ctx, tables, tm, params: Params, mask, stream=None) -> None:
 def compact_mask(ctx, mask, n_scales, H, W, lst, count, stream=None) -> None:
     cap = 0 if lst is None else lst.numel()
     _check(load().compact_mask(ctx, _ptr(mask), n_scales, H, W, _ptr(lst), cap, _ptr(count), _stream(stream)))
+
+
+def compact_mask_noalloc(mask, n_scales, H, W, lst, count, stream=None) -> None:
+    """compact_mask without device allocation: scratch is a fixed array in the
+    library (callers inside stream capture or without an allocator)."""
+    cap = 0 if lst is None else lst.numel()
+    rc = load().compact_mask_noalloc(_ptr(mask), n_scales, H, W, _ptr(lst), cap, _ptr(count), _stream(stream))
+    if rc != SCR_OK:
+        raise ScreenError(rc, compact_mask_noalloc_error())
+
+
+def compact_mask_noalloc_error() -> str:
+    return load().compact_mask_noalloc_error().decode()
 
 
 def screen_positions(ctx, tables, tm, params: Params, mask, lst, stream=None) -> tuple[int, bool]:

@@ -8,6 +8,9 @@
 // per-chunk scan + scatter.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
+
+#include <mutex>
 
 #include "internal.h"
 
@@ -183,3 +186,84 @@ cudaError_t launch_compact(const uint32_t *mask, uint64_t total_words, int H, in
 }
 
 }  // namespace scr
+
+// ---------------------------------------------------------------------------
+// Allocation-free compaction.
+//
+// Some callers cannot allocate device memory at the point where they compact
+// a mask: code running while a stream is being captured into a CUDA graph
+// (where cudaMalloc is not allowed), real-time loops that must not enter the
+// allocator, and hosts whose device memory is owned by another framework's
+// allocator with no hook for a foreign library.  compact_mask_noalloc serves
+// them: its scratch (per-chunk bit counts and their prefix offsets) lives in
+// the fixed device array below instead of coming from an allocation.
+//
+// The array is a file-scope __device__ variable, so every GPU that loads this
+// library holds it (kStaticCompactBytes) until the process exits.  In host
+// code its name is only a host-side stand-in; the device address is looked up
+// once per device with cudaGetSymbolAddress, with that device current.
+// ---------------------------------------------------------------------------
+namespace scr {
+namespace {
+
+constexpr uint64_t kStaticChunks = 65536;   // chunks of 4096 mask words
+constexpr size_t kStaticCompactBytes = 256 * 3 + kStaticChunks * 4 + kStaticChunks * 8;
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_compact_scratch[kStaticCompactBytes];
+
+std::mutex g_static_mu;
+void *g_static_ptr[kMaxDevices] = {nullptr};
+thread_local char g_noalloc_err[256];
+
+int noalloc_fail(int code, const char *msg) {
+    snprintf(g_noalloc_err, sizeof g_noalloc_err, "%s", msg);
+    return code;
+}
+
+}  // namespace
+}  // namespace scr
+
+extern "C" const char *compact_mask_noalloc_error(void) { return scr::g_noalloc_err; }
+
+extern "C" int compact_mask_noalloc(const uint32_t *mask_dev, int32_t n_scales, int32_t H, int32_t W,
+                                    uint64_t *list_dev, uint64_t list_cap, uint64_t *count_dev,
+                                    scr_stream stream) {
+    using namespace scr;
+    if (!mask_dev || !count_dev || (list_cap && !list_dev))
+        return noalloc_fail(SCR_EINVAL, "null mask, count or list");
+    if (((uintptr_t)mask_dev & 15) || ((uintptr_t)count_dev & 7) || ((uintptr_t)list_dev & 7))
+        return noalloc_fail(SCR_EINVAL, "mask must be 16-byte aligned, list and count 8-byte aligned");
+    if (n_scales < 1 || n_scales > 65535 || H < 1 || W < 1 || H > 65535 || W > 65535)
+        return noalloc_fail(SCR_EINVAL, "bad mask geometry");
+    const int Ww = (W + 31) / 32;
+    const uint64_t total = (uint64_t)n_scales * H * Ww;
+    const uint64_t nchunks = (total + 4095) / 4096;
+    if (nchunks > kStaticChunks)
+        return noalloc_fail(SCR_EINVAL, "mask larger than the fixed scratch allows "
+                                        "(at most 65536 * 4096 = 268435456 words)");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return noalloc_fail(SCR_ECUDA, "no usable current CUDA device");
+    void *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_static_mu);
+        if (!g_static_ptr[dev]) {
+            // one-time set-up for this device (the current device)
+            void *p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_compact_scratch);
+            if (e != cudaSuccess || !p) {
+                cudaGetLastError();
+                return noalloc_fail(SCR_ECUDA, "cudaGetSymbolAddress of the fixed compaction scratch failed");
+            }
+            g_static_ptr[dev] = p;
+        }
+        scratch = g_static_ptr[dev];
+    }
+    // counts and offsets are fully rewritten by every call: nothing to clear
+    const cudaError_t e = launch_compact(mask_dev, total, H, Ww, list_dev, list_cap, count_dev, scratch,
+                                         (cudaStream_t)stream, nullptr);
+    if (e != cudaSuccess)
+        return noalloc_fail(SCR_ECUDA, cudaGetErrorString(e));
+    return SCR_OK;
+}
