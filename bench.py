@@ -112,6 +112,24 @@ class Clocks:
                 if any(r[2].replace(".", "").isdigit() for r in rows) else None}
 
 
+def recorded_traffic(H, W):
+    """DRAM bytes per k_screen launch from the committed ncu capture of the
+    4096x4096 workload, or None if the kernel source changed since."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_screen_4096_traffic.txt")
+    if (H, W) != (4096, 4096) or not os.path.exists(path):
+        return None
+    rec = {}
+    for line in open(path):
+        if ":" in line and not line.startswith(("#", " ", "`")):
+            k, v = line.split(":", 1)
+            rec[k.strip()] = v.strip()
+    src = os.path.join(ROOT, "paper_1707_05647_gb300", "csrc", "features.cu")
+    if rec.get("kernel_source_sha256") != hashlib.sha256(open(src, "rb").read()).hexdigest():
+        return None
+    return int(rec["dram_bytes_per_launch"])
+
+
 def measured_peak_gbs():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -273,13 +291,7 @@ def emit(args, wl, world, total_s, value, k3_ms, step_ms, launches, clk, n_surv,
     alg = compulsory_bytes(H, W, S)
     achieved = alg / k3 / 1e9
     alg1 = per_scale_bytes(H, W, S, wl.sum_bits, wl.sq_bits) / k3 / 1e9
-    prof = os.path.join(ROOT, "profiles", "traffic_screen_4096.json")
-    traffic = None
-    if os.path.exists(prof):
-        try:
-            traffic = json.load(open(prof)).get("dram_bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = recorded_traffic(H, W)
     cpu = None
     if not args.no_cpu_baseline:
         v, sample, cores, dt = oracle_baseline(wl)
