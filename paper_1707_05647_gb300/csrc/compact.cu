@@ -10,6 +10,7 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "internal.h"
@@ -71,23 +72,29 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *sh, ui
     return sh[32 + wp] + inc - v;
 }
 
-__global__ void __launch_bounds__(kThreads) k_count(const uint32_t *mask, uint64_t total, uint32_t *counts) {
+__global__ void __launch_bounds__(kThreads) k_count(const uint32_t *mask, uint64_t total, uint32_t *counts,
+                                                    uint32_t nchunks) {
+    pdl_begin();
     __shared__ uint32_t sh[72];
-    const uint64_t first = (uint64_t)blockIdx.x * kChunk + (uint64_t)threadIdx.x * kWordsPerThread;
-    uint32_t w[kWordsPerThread];
-    load_words(mask, total, first, w);
-    uint32_t c = 0;
+    for (uint32_t b = blockIdx.x; b < nchunks; b += gridDim.x) {   // grid-stride over chunks
+        const uint64_t first = (uint64_t)b * kChunk + (uint64_t)threadIdx.x * kWordsPerThread;
+        uint32_t w[kWordsPerThread];
+        load_words(mask, total, first, w);
+        uint32_t c = 0;
 #pragma unroll
-    for (int k = 0; k < kWordsPerThread; ++k)
-        c += __popc(w[k]);
-    uint32_t tot;
-    block_excl_scan(c, sh, tot);
-    if (threadIdx.x == 0)
-        counts[blockIdx.x] = tot;
+        for (int k = 0; k < kWordsPerThread; ++k)
+            c += __popc(w[k]);
+        uint32_t tot;
+        block_excl_scan(c, sh, tot);
+        if (threadIdx.x == 0)
+            counts[b] = tot;
+        __syncthreads();
+    }
 }
 
 __global__ void __launch_bounds__(1024) k_scan_counts(const uint32_t *counts, uint64_t *offsets, int nchunks,
                                                       uint64_t *count_out) {
+    pdl_begin();
     __shared__ uint64_t sh[72];
     const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
     uint64_t carry = 0;
@@ -128,38 +135,45 @@ __global__ void __launch_bounds__(1024) k_scan_counts(const uint32_t *counts, ui
 }
 
 __global__ void __launch_bounds__(kThreads) k_scatter(const uint32_t *mask, uint64_t total, int H, int Wwords,
-                                                      const uint64_t *offsets, uint64_t *list, uint64_t cap) {
+                                                      const uint32_t *counts, const uint64_t *offsets,
+                                                      uint64_t *list, uint64_t cap, uint32_t nchunks) {
+    pdl_begin();
     __shared__ uint32_t sh[72];
-    const uint64_t first = (uint64_t)blockIdx.x * kChunk + (uint64_t)threadIdx.x * kWordsPerThread;
-    uint32_t w[kWordsPerThread];
-    load_words(mask, total, first, w);
-    uint32_t c = 0;
-#pragma unroll
-    for (int k = 0; k < kWordsPerThread; ++k)
-        c += __popc(w[k]);
-    uint32_t tot;
-    uint64_t pos = offsets[blockIdx.x] + block_excl_scan(c, sh, tot);
-    if (c == 0 || pos >= cap)
-        return;
     const uint64_t rowWords = (uint64_t)Wwords;
     const uint64_t planeWords = (uint64_t)H * rowWords;
-#pragma unroll 1
-    for (int k = 0; k < kWordsPerThread; ++k) {
-        uint32_t bits = w[k];
-        if (!bits)
+    for (uint32_t b = blockIdx.x; b < nchunks; b += gridDim.x) {   // grid-stride over chunks
+        if (counts[b] == 0 || offsets[b] >= cap)   // block-uniform: nothing to write here
             continue;
-        const uint64_t wi = first + k;
-        const uint64_t s = wi / planeWords;
-        const uint64_t rem = wi - s * planeWords;
-        const uint64_t y = rem / rowWords;
-        const uint64_t x0 = (rem - y * rowWords) * 32;
-        const uint64_t keyb = (s << 48) | (y << 24);
-        while (bits) {
-            const int b = __ffs(bits) - 1;
-            bits &= bits - 1;
-            if (pos < cap)
-                list[pos] = keyb | (x0 + b);
-            ++pos;
+        const uint64_t first = (uint64_t)b * kChunk + (uint64_t)threadIdx.x * kWordsPerThread;
+        uint32_t w[kWordsPerThread];
+        load_words(mask, total, first, w);
+        uint32_t c = 0;
+#pragma unroll
+        for (int k = 0; k < kWordsPerThread; ++k)
+            c += __popc(w[k]);
+        uint32_t tot;
+        uint64_t pos = offsets[b] + block_excl_scan(c, sh, tot);
+        __syncthreads();
+        if (c == 0 || pos >= cap)
+            continue;
+#pragma unroll
+        for (int k = 0; k < kWordsPerThread; ++k) {
+            uint32_t bits = w[k];
+            if (!bits)
+                continue;
+            const uint64_t wi = first + k;
+            const uint64_t s = wi / planeWords;
+            const uint64_t rem = wi - s * planeWords;
+            const uint64_t y = rem / rowWords;
+            const uint64_t x0 = (rem - y * rowWords) * 32;
+            const uint64_t keyb = (s << 48) | (y << 24);
+            while (bits) {
+                const int bit = __ffs(bits) - 1;
+                bits &= bits - 1;
+                if (pos < cap)
+                    list[pos] = keyb | (x0 + bit);
+                ++pos;
+            }
         }
     }
 }
@@ -177,12 +191,19 @@ cudaError_t launch_compact(const uint32_t *mask, uint64_t total_words, int H, in
     const uint64_t nchunks = (total_words + kChunk - 1) / kChunk;
     uint32_t *counts = (uint32_t *)scratch;
     uint64_t *offsets = (uint64_t *)((char *)scratch + ((nchunks * 4 + 255) & ~uint64_t(255)));
-    k_count<<<(unsigned)nchunks, kThreads, 0, st>>>(mask, total_words, counts);
-    k_scan_counts<<<1, 1024, 0, st>>>(counts, offsets, (int)nchunks, count);
-    k_scatter<<<(unsigned)nchunks, kThreads, 0, st>>>(mask, total_words, H, Wwords, offsets, list, cap);
+    cudaError_t e;
     if (launches)
         *launches += 3;
-    return cudaGetLastError();
+    // grid-stride kernels: a few blocks per SM, each walking many chunks
+    const unsigned grid = (unsigned)std::min<uint64_t>(nchunks, 152 * 4);
+    if ((e = launch_pdl(k_count, dim3(grid), dim3(kThreads), st, mask, total_words, counts, (uint32_t)nchunks)) !=
+        cudaSuccess)
+        return e;
+    if ((e = launch_pdl(k_scan_counts, dim3(1), dim3(1024), st, (const uint32_t *)counts, offsets, (int)nchunks,
+                        count)) != cudaSuccess)
+        return e;
+    return launch_pdl(k_scatter, dim3(grid), dim3(kThreads), st, mask, total_words, H, Wwords,
+                      (const uint32_t *)counts, (const uint64_t *)offsets, list, cap, (uint32_t)nchunks);
 }
 
 }  // namespace scr

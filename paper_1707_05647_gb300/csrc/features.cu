@@ -73,6 +73,7 @@ constexpr int WPW = 8;
 
 __global__ void __launch_bounds__(32 * kWarpsPerBlock)
 k_screen(const __grid_constant__ ScreenArgs a) {
+    pdl_begin();
     const int lane = threadIdx.x & 31;
     const int w0 = (blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5)) * WPW;   // first word
     const int y = blockIdx.y;
@@ -195,6 +196,7 @@ __device__ __forceinline__ int square_half_dev(int R) {
 }
 
 __global__ void k_template_sums(const TmplArgs a) {
+    pdl_begin();
     const int t = a.t_min + blockIdx.x * blockDim.x + threadIdx.x;
     if (t > a.r)
         return;
@@ -216,10 +218,10 @@ __global__ void k_template_sums(const TmplArgs a) {
 cudaError_t launch_screen(const ScreenArgs &args, cudaStream_t st, uint64_t *launches) {
     const int warps = (args.Wwords + WPW - 1) / WPW;
     dim3 grid((warps + kWarpsPerBlock - 1) / kWarpsPerBlock, args.H);
-    k_screen<<<grid, 32 * kWarpsPerBlock, 0, st>>>(args);
+    const cudaError_t e = launch_pdl(k_screen, grid, dim3(32 * kWarpsPerBlock), st, args);
     if (launches)
         *launches += 1;
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t launch_template_sums(const TableDesc &L1, const TableDesc &L2, const TableDesc &T1,
@@ -227,10 +229,10 @@ cudaError_t launch_template_sums(const TableDesc &L1, const TableDesc &L2, const
                                  cudaStream_t st, uint64_t *launches) {
     TmplArgs a{L1.lo, L1.hi, L2.lo, L2.hi, T1.lo, T1.hi, T2.lo, T2.hi, L1.pitch, T1.pitch, r, t_min, out_dev};
     const int cnt = r - t_min + 1;
-    k_template_sums<<<(cnt + 127) / 128, 128, 0, st>>>(a);
+    const cudaError_t e = launch_pdl(k_template_sums, dim3((cnt + 127) / 128), dim3(128), st, a);
     if (launches)
         *launches += 1;
-    return cudaGetLastError();
+    return e;
 }
 
 }  // namespace scr

@@ -72,6 +72,35 @@ struct ScreenArgs {
 };
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch.  Every kernel of the library begins with
+// pdl_begin(): it waits until the grids it depends on have completed and their
+// memory is visible (no memory operation of the kernel precedes the wait), then
+// lets the next kernel in the stream be scheduled.  Kernels are launched with
+// launch_pdl(), so a kernel's CTAs are placed on the GPU while its predecessor
+// drains instead of after it has fully retired.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_begin() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,
+                              Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+// ---------------------------------------------------------------------------
 // Launchers (return cudaError_t of the launch).  `launches` is incremented by
 // the number of kernels enqueued.
 // ---------------------------------------------------------------------------

@@ -43,7 +43,7 @@ constexpr int B = kBand;
 constexpr int CW = kTileCols;
 constexpr int HALO = kHalo;
 constexpr int SLOTS = kTileSlots;            // 1024 accumulator columns per tile
-constexpr int NT = 512;                      // threads of k_tab_reduce
+constexpr int NT = 256;                      // threads of k_tab_reduce
 constexpr int WT = 256;                      // threads of k_tab_write (4 columns each)
 constexpr int K = SLOTS / WT;                // columns per k_tab_write thread
 constexpr int CL = kWinLo;                   // first carry column
@@ -51,12 +51,14 @@ constexpr int CL = kWinLo;                   // first carry column
 struct Geometry {
     int H, W, n, m;          // bands, tiles
     int XW;                  // carry columns c in [CL, W+1]
+    int XWp;                 // row pitch of the carry arrays (XW rounded up to 4)
     int DMIN, DN;            // anti-diagonal lanes d in [DMIN, DMIN+DN)
     int FMIN, FN;            // diagonal lanes f in [FMIN, FMIN+FN)
     Geometry(int H_, int W_) : H(H_), W(W_) {
         n = (H + B - 1) / B;
         m = (W + CW - 1) / CW;
         XW = W + 1 - CL + 1;
+        XWp = (XW + 3) & ~3;
         DMIN = CL - 1;
         DN = (n - 1) * B + W + 2 - DMIN;
         FMIN = CL - (n - 1) * B;
@@ -70,12 +72,12 @@ struct Scratch {
     uint32_t *ad1, *ad2;     // [n][W+B-1]    anti-diagonal sums, x' + B-1
     uint32_t *md1, *md2;     // [n][W+B-1]    diagonal sums, x''
     uint32_t *rs1, *rs2;     // [n][m][B]     row sums over the tile's shifted chunk
-    uint32_t *csx1, *csx2;   // [n][W]        exclusive band prefix of cs
-    uint32_t *adx1, *adx2;   // [n][XW]       AD_i(r0-1+c)
-    uint32_t *mdx1, *mdx2;   // [n][XW]       MD_i(c-r0)
+    uint32_t *csx1, *csx2;   // [n][XWp]      exclusive band prefix of cs at x = c (0 outside the image)
+    uint32_t *adx1, *adx2;   // [n][XWp]      AD_i(r0-1+c)
+    uint32_t *mdx1, *mdx2;   // [n][XWp]      MD_i(c-r0)
     uint32_t *adf1, *adf2;   // [DN]          full anti-diagonal sums, index d - DMIN
     uint32_t *rc1, *rc2;     // [n][m][B]     row carries P(r, c0-HALO-1)
-    void *xl1, *xl2, *x11, *x12, *x21, *x22;   // [n][XW] carry rows, table width
+    void *xl1, *xl2, *x11, *x12, *x21, *x22;   // [n][XWp] carry rows, table width
 };
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
@@ -87,7 +89,7 @@ size_t carve(const Geometry &g, int sb, int qb, Scratch *s, char *base) {
         off += align256(bytes);
         return p;
     };
-    const size_t n = g.n, W = g.W, m = g.m, XW = g.XW;
+    const size_t n = g.n, W = g.W, m = g.m, XW = g.XWp;
     s->cs1 = (uint32_t *)take(n * W * 4);
     s->cs2 = (uint32_t *)take(n * W * 4);
     s->ad1 = (uint32_t *)take(n * (W + B - 1) * 4);
@@ -96,8 +98,8 @@ size_t carve(const Geometry &g, int sb, int qb, Scratch *s, char *base) {
     s->md2 = (uint32_t *)take(n * (W + B - 1) * 4);
     s->rs1 = (uint32_t *)take(n * m * B * 4);
     s->rs2 = (uint32_t *)take(n * m * B * 4);
-    s->csx1 = (uint32_t *)take(n * W * 4);
-    s->csx2 = (uint32_t *)take(n * W * 4);
+    s->csx1 = (uint32_t *)take(n * XW * 4);
+    s->csx2 = (uint32_t *)take(n * XW * 4);
     s->adx1 = (uint32_t *)take(n * XW * 4);
     s->adx2 = (uint32_t *)take(n * XW * 4);
     s->mdx1 = (uint32_t *)take(n * XW * 4);
@@ -145,6 +147,7 @@ __device__ __forceinline__ uint2 load8(const uint8_t *img, int64_t pitch, int H,
 }
 
 __global__ void __launch_bounds__(NT) k_tab_reduce(const ReduceArgs a) {
+    pdl_begin();
     __shared__ __align__(16) uint8_t tile[B][SLOTS];
     const Geometry &g = a.g;
     const int j = blockIdx.x, i = blockIdx.y, t = threadIdx.x;
@@ -252,9 +255,12 @@ __device__ __forceinline__ void carry_contrib(const CarryArgs &a, int part, int 
     const size_t WD = g.W + B - 1;
     v1 = v2 = 0;
     if (part == 0) {
-        const size_t o = (size_t)band * g.W + lane_idx;
-        v1 = a.s.cs1[o];
-        v2 = a.s.cs2[o];
+        const int x = lane_idx + CL;                        // column c of the carry window
+        if (x >= 0 && x < g.W) {
+            const size_t o = (size_t)band * g.W + x;
+            v1 = a.s.cs1[o];
+            v2 = a.s.cs2[o];
+        }
     } else if (part == 1) {
         const int xp = g.DMIN + lane_idx - (band * B + B - 1);     // d - r_end
         if (xp >= -(B - 1) && xp <= g.W - 1) {
@@ -274,15 +280,17 @@ __device__ __forceinline__ void carry_contrib(const CarryArgs &a, int part, int 
 }
 
 constexpr int CG = 8;   // band groups per carry block
+constexpr int CQ = 16;  // bands per group kept in registers (more bands: reloaded)
 
 __global__ void __launch_bounds__(32 * CG) k_tab_carry(const CarryArgs a) {
+    pdl_begin();
     __shared__ uint32_t sum1[CG][33], sum2[CG][33];
     const Geometry &g = a.g;
     const int lane = threadIdx.x, grp = threadIdx.y;
     int chunk = blockIdx.x, part, nlanes;
     if (chunk < a.chunksCS) {
         part = 0;
-        nlanes = g.W;
+        nlanes = g.XW;
     } else if (chunk < a.chunksCS + a.chunksAD) {
         part = 1;
         chunk -= a.chunksCS;
@@ -296,10 +304,18 @@ __global__ void __launch_bounds__(32 * CG) k_tab_carry(const CarryArgs a) {
     const bool live = idx < nlanes;
     const int q = (g.n + CG - 1) / CG;
     const int b0 = grp * q, b1 = min(g.n, b0 + q);
+    uint32_t c1[CQ], c2[CQ];
     uint32_t t1 = 0, t2 = 0;
+#pragma unroll
+    for (int k = 0; k < CQ; ++k) {
+        c1[k] = c2[k] = 0;
+        if (live && b0 + k < b1)
+            carry_contrib(a, part, idx, b0 + k, c1[k], c2[k]);
+        t1 += c1[k];
+        t2 += c2[k];
+    }
     if (live)
-#pragma unroll 8
-        for (int b = b0; b < b1; ++b) {
+        for (int b = b0 + CQ; b < b1; ++b) {
             uint32_t v1, v2;
             carry_contrib(a, part, idx, b, v1, v2);
             t1 += v1;
@@ -326,10 +342,10 @@ __global__ void __launch_bounds__(32 * CG) k_tab_carry(const CarryArgs a) {
     if (!live)
         return;
     uint32_t run1 = sum1[grp][lane], run2 = sum2[grp][lane];
-    const size_t XW = g.XW;
-    for (int b = b0; b < b1; ++b) {
+    const size_t XW = g.XWp;
+    auto put = [&](int b) {
         if (part == 0) {
-            const size_t o = (size_t)b * g.W + idx;
+            const size_t o = (size_t)b * XW + idx;
             a.s.csx1[o] = run1;
             a.s.csx2[o] = run2;
         } else if (part == 1) {
@@ -345,6 +361,17 @@ __global__ void __launch_bounds__(32 * CG) k_tab_carry(const CarryArgs a) {
                 a.s.mdx2[(size_t)b * XW + (size_t)(c - CL)] = run2;
             }
         }
+    };
+#pragma unroll
+    for (int k = 0; k < CQ; ++k) {
+        if (b0 + k >= b1)
+            break;
+        put(b0 + k);
+        run1 += c1[k];
+        run2 += c2[k];
+    }
+    for (int b = b0 + CQ; b < b1; ++b) {
+        put(b);
         uint32_t v1, v2;
         carry_contrib(a, part, idx, b, v1, v2);
         run1 += v1;
@@ -376,6 +403,7 @@ constexpr int PT = 256;
 
 template <typename TS, typename TQ>
 __global__ void __launch_bounds__(PT) k_tab_prefix(const PrefixArgs a) {
+    pdl_begin();
     __shared__ uint64_t wsum[PT / 32], red[PT / 32];
     const Geometry &g = a.g;
     const int i = blockIdx.x, q = blockIdx.y, t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -406,27 +434,40 @@ __global__ void __launch_bounds__(PT) k_tab_prefix(const PrefixArgs a) {
         case 4: src = a.s.mdx1; dst = a.s.x21; break;
         default: src = a.s.mdx2; dst = a.s.x22; break;
     }
-    auto value = [&](int k) -> uint64_t {
-        if (k >= XW)
-            return 0;
-        if (q < 2) {
-            const int c = k + CL;
-            return (c >= 0 && c < g.W) ? src[(size_t)i * g.W + c] : 0u;
-        }
-        return src[(size_t)i * XW + k];
-    };
-    const int seg = ((XW + PT / 32 - 1) / (PT / 32) + 31) / 32 * 32;   // entries per warp
+    // every sequence is a row of XWp words (16-byte aligned); each lane takes 4
+    // consecutive entries per step, each warp a contiguous segment
+    const uint32_t *row = src + (size_t)i * g.XWp;
+    constexpr int MAXIT = 5;                                   // 128-entry steps kept in registers
+    const int seg = ((XW + PT / 32 - 1) / (PT / 32) + 127) / 128 * 128;   // entries per warp
     const int k0 = w * seg, k1 = min(XW, k0 + seg);
-    // pass 1: segment sums (+ the anti-diagonals above the band for D1)
-    uint64_t part = 0;
-    for (int k = k0 + lane; k < k1; k += 32)
-        part += value(k);
+    auto load4 = [&](int k) -> uint4 {                         // k multiple of 4
+        if (k + 4 <= k1)
+            return *reinterpret_cast<const uint4 *>(row + k);
+        uint32_t v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            v[u] = (k + u < k1) ? row[k + u] : 0u;
+        return make_uint4(v[0], v[1], v[2], v[3]);
+    };
     uint64_t tri = 0;
     if (q == 2 || q == 3) {
+        // anti-diagonals d < r0 - 1 + CL lie entirely above the band
         const uint32_t *adf = q == 2 ? a.s.adf1 : a.s.adf2;
         const int dend = r0 - 1 + CL;
         for (int d = t; d < dend; d += PT)
             tri += adf[d - g.DMIN];
+    }
+    uint4 v[MAXIT];
+    uint64_t part = 0;
+#pragma unroll
+    for (int it = 0; it < MAXIT; ++it) {
+        const int k = k0 + 128 * it + 4 * lane;
+        v[it] = (k < k1) ? load4(k) : make_uint4(0, 0, 0, 0);
+        part += (uint64_t)v[it].x + v[it].y + v[it].z + v[it].w;
+    }
+    for (int k = k0 + 128 * MAXIT + 4 * lane; k < k1; k += 128) {   // very wide images only
+        const uint4 u = load4(k);
+        part += (uint64_t)u.x + u.y + u.z + u.w;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -444,19 +485,40 @@ __global__ void __launch_bounds__(PT) k_tab_prefix(const PrefixArgs a) {
         if (u < w)
             carry += wsum[u];
     }
-    // pass 2: scan and store in table width
-    for (int kb = k0; kb < k1; kb += 32) {
-        const int k = kb + lane;
-        const uint64_t v = value(k);
-        const uint64_t incl = warp_incl_scan(v, lane);
+    auto step = [&](int k, uint4 u) {
+        const uint64_t p0 = u.x, p1 = p0 + u.y, p2 = p1 + u.z, p3 = p2 + u.w;
+        const uint64_t incl = warp_incl_scan(p3, lane);
+        const uint64_t base = carry + incl - p3;
         if (k < k1) {
-            const uint64_t out = carry + incl;
-            if (q & 1)
-                ((TQ *)dst)[(size_t)i * XW + k] = (TQ)out;
-            else
-                ((TS *)dst)[(size_t)i * XW + k] = (TS)out;
+            const uint64_t o[4] = {base + p0, base + p1, base + p2, base + p3};
+            if (q & 1) {
+                TQ *d = (TQ *)dst + (size_t)i * g.XWp + k;
+                if (k + 4 <= k1 && sizeof(TQ) == 4)
+                    *reinterpret_cast<uint4 *>(d) = make_uint4((uint32_t)o[0], (uint32_t)o[1], (uint32_t)o[2], (uint32_t)o[3]);
+                else
+                    for (int e = 0; e < 4; ++e)
+                        if (k + e < k1) d[e] = (TQ)o[e];
+            } else {
+                TS *d = (TS *)dst + (size_t)i * g.XWp + k;
+                if (k + 4 <= k1 && sizeof(TS) == 4)
+                    *reinterpret_cast<uint4 *>(d) = make_uint4((uint32_t)o[0], (uint32_t)o[1], (uint32_t)o[2], (uint32_t)o[3]);
+                else
+                    for (int e = 0; e < 4; ++e)
+                        if (k + e < k1) d[e] = (TS)o[e];
+            }
         }
         carry += __shfl_sync(0xffffffffu, incl, 31);
+    };
+#pragma unroll
+    for (int it = 0; it < MAXIT; ++it) {
+        const int kb = k0 + 128 * it;
+        if (kb >= k1)
+            break;
+        step(kb + 4 * lane, v[it]);
+    }
+    for (int kb = k0 + 128 * MAXIT; kb < k1; kb += 128) {
+        const int k = kb + 4 * lane;
+        step(k, k < k1 ? load4(k) : make_uint4(0, 0, 0, 0));
     }
 }
 
@@ -508,6 +570,7 @@ __device__ __forceinline__ uint32_t load4(const uint8_t *img, int64_t pitch, int
 // contiguous bytes of one plane.
 template <typename TS, typename TQ>
 __global__ void __launch_bounds__(WT) k_tab_write(const WriteArgs a) {
+    pdl_begin();
     constexpr int NW = WT / 32;
     __shared__ uint32_t wt1[2][NW], wt2[2][NW];                // warp totals
     __shared__ TS nb_d1a[2][NW], nb_d2a[2][NW];                // warp-edge neighbours
@@ -531,7 +594,7 @@ __global__ void __launch_bounds__(WT) k_tab_write(const WriteArgs a) {
     TS L1a[K], D1a[K], D2a[K];
     TQ L2a[K], D1b[K], D2b[K];
     {
-        const size_t XW = g.XW;
+        const size_t XW = g.XWp;
         const TS *xl1 = (const TS *)a.s.xl1, *x11 = (const TS *)a.s.x11, *x21 = (const TS *)a.s.x21;
         const TQ *xl2 = (const TQ *)a.s.xl2, *x12 = (const TQ *)a.s.x12, *x22 = (const TQ *)a.s.x22;
 #pragma unroll
@@ -701,17 +764,20 @@ template <typename TS, typename TQ>
 cudaError_t launch_all(const Geometry &g, const Scratch &s, const uint8_t *img, int64_t pitch,
                        int aligned8, const TableDesc &L1, const TableDesc &L2,
                        const TableDesc &T1, const TableDesc &T2, cudaStream_t st) {
+    cudaError_t e;
     ReduceArgs ra{img, pitch, g, s, aligned8};
-    k_tab_reduce<<<dim3(g.m, g.n), NT, 0, st>>>(ra);
-    CarryArgs ca{g, s, (g.W + 31) / 32, (g.DN + 31) / 32};
+    if ((e = launch_pdl(k_tab_reduce, dim3(g.m, g.n), dim3(NT), st, ra)) != cudaSuccess)
+        return e;
+    CarryArgs ca{g, s, (g.XW + 31) / 32, (g.DN + 31) / 32};
     const int chunks = ca.chunksCS + ca.chunksAD + (g.FN + 31) / 32;
-    k_tab_carry<<<chunks, dim3(32, CG), 0, st>>>(ca);
+    if ((e = launch_pdl(k_tab_carry, dim3(chunks), dim3(32, CG), st, ca)) != cudaSuccess)
+        return e;
     PrefixArgs pa{g, s};
-    k_tab_prefix<TS, TQ><<<dim3(g.n, 7), PT, 0, st>>>(pa);
+    if ((e = launch_pdl(k_tab_prefix<TS, TQ>, dim3(g.n, 7), dim3(PT), st, pa)) != cudaSuccess)
+        return e;
     WriteArgs wa{img, pitch, g, s, L1.lo, L1.hi, L2.lo, L2.hi, T1.lo, T1.hi, T2.lo, T2.hi,
                  L1.pitch, T1.pitch, aligned8};
-    k_tab_write<TS, TQ><<<dim3(g.m, g.n), WT, 0, st>>>(wa);
-    return cudaGetLastError();
+    return launch_pdl(k_tab_write<TS, TQ>, dim3(g.m, g.n), dim3(WT), st, wa);
 }
 
 }  // namespace
