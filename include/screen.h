@@ -229,6 +229,66 @@ int screen_positions_async(scr_ctx *ctx, const scr_tables *t, const scr_tmpl *tm
                            uint64_t *list_dev, uint64_t list_cap, uint64_t *count_dev,
                            scr_stream stream);
 
+/* ---- batched screening (many images x many templates) -------------------- */
+
+/* One unit of batched work: screen image `image` with template `tmpl`. */
+typedef struct {
+    int32_t image, tmpl;
+} scr_pair;
+
+/* Launch shape of the batched kernel; words_per_warp 0 = autotune. */
+typedef struct {
+    int32_t words_per_warp; /* 2, 4 or 8 mask words (x 32 positions) per warp */
+    int32_t blocks_per_sm;  /* persistent blocks per SM */
+} scr_batch_tuning;
+
+typedef struct {
+    int64_t n_groups;       /* (image, star radius) groups */
+    int64_t n_records;      /* (pair, scale) tests */
+    int64_t n_units;        /* units of work (one row x one block of mask words) */
+    uint64_t candidates;    /* (pair, scale, valid position) candidates per run */
+    int32_t words_per_warp, blocks_per_sm;
+    uint64_t union_words;   /* words of the union mask */
+} scr_batch_info;
+
+typedef struct scr_batch scr_batch;
+
+/* Plan a batched screen of n_pairs (image, template) pairs over n_images
+ * tables handles and n_tmpls templates (params[t] gives template t's radii,
+ * features and tolerances).  Every (pair, scale) becomes one test; tests are
+ * grouped per image by star radius so each (position, radius) feature vector
+ * is computed once and compared with every test of that radius (Sec. 5,
+ * Algorithm 1, applied to many templates at once).  One run screens every
+ * candidate (pair, scale, valid position) and writes, all caller-owned:
+ *   counts_dev[n_pairs]   survivors per pair (exact);
+ *   offsets_dev[n_pairs]  exclusive prefix of counts_dev (may be NULL);
+ *   union_mask_dev        per image, in image order, H x ceil(W/32) words:
+ *                         bit set when some template survives there at some
+ *                         scale (may be NULL);
+ *   keys_dev[keys_cap]    survivor keys (pair << 37) | (scale << 32) | (y << 16) | x
+ *                         in ascending order, i.e. per pair in the (scale, row,
+ *                         column) order of compact_mask; *n_keys_dev = the exact
+ *                         total.  If the total exceeds keys_cap the keys are
+ *                         unspecified (counts and mask stay exact).
+ * Images up to 65535 x 65535, n_pairs < 2^26.  tuning NULL (or words_per_warp
+ * 0) autotunes the launch shape on this batch and caches the choice in the
+ * context.  The run (zeroing, screening kernel, radix sort, offsets) is
+ * captured once into a CUDA graph; the tables, templates and output buffers
+ * must stay valid while the plan exists.  Synchronous. */
+int screen_batch_create(scr_ctx *ctx, const scr_tables *const *tables, int32_t n_images,
+                        const scr_tmpl *const *tmpls, const scr_params *params, int32_t n_tmpls,
+                        const scr_pair *pairs, int32_t n_pairs, uint64_t *counts_dev,
+                        uint64_t *offsets_dev, uint32_t *union_mask_dev, uint64_t *keys_dev,
+                        uint64_t keys_cap, uint64_t *n_keys_dev, const scr_batch_tuning *tuning,
+                        scr_stream stream, scr_batch **out);
+
+/* Replay the plan's graph on `stream` (stream-ordered, no host sync). */
+int screen_batch_run(scr_batch *b, scr_stream stream);
+
+int screen_batch_info(const scr_batch *b, scr_batch_info *out);
+
+void screen_batch_release(scr_ctx *ctx, scr_batch *b);
+
 /* ---- whole path from host memory ----------------------------------------- */
 
 /* End-to-end call for host-resident data: copy the image (host, pitch bytes per

@@ -46,6 +46,20 @@ class _Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("kernel_launches", "bytes_in_use", "bytes_peak", "budget")]
 
 
+class _Pair(ctypes.Structure):
+    _fields_ = [("image", ctypes.c_int32), ("tmpl", ctypes.c_int32)]
+
+
+class _Tuning(ctypes.Structure):
+    _fields_ = [("words_per_warp", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+
+
+class _BatchInfo(ctypes.Structure):
+    _fields_ = [("n_groups", ctypes.c_int64), ("n_records", ctypes.c_int64), ("n_units", ctypes.c_int64),
+                ("candidates", ctypes.c_uint64), ("words_per_warp", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("union_words", ctypes.c_uint64)]
+
+
 _lib = None
 
 
@@ -87,6 +101,11 @@ def load(build_if_missing: bool = True):
         "screen_positions_async": ([vp, vp, vp, ctypes.POINTER(_Params), vp, u64, vp, u64, vp, vp], ctypes.c_int),
         "screen_host": ([vp, vp, i32, i32, i64, i32, i32, vp, ctypes.POINTER(_Params), vp, u64,
                          ctypes.POINTER(u64), vp], ctypes.c_int),
+        "screen_batch_create": ([vp, vp, i32, vp, ctypes.POINTER(_Params), i32, ctypes.POINTER(_Pair), i32,
+                                 vp, vp, vp, vp, u64, vp, ctypes.POINTER(_Tuning), vp, pp], ctypes.c_int),
+        "screen_batch_run": ([vp, vp], ctypes.c_int),
+        "screen_batch_info": ([vp, ctypes.POINTER(_BatchInfo)], ctypes.c_int),
+        "screen_batch_release": ([vp, vp], None),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -101,7 +120,8 @@ def exported_symbols():
             "tables_view", "tables_copy_to_host", "tables_release", "template_features", "template_sums",
             "template_release", "screen_bounds", "screen_features", "compact_mask", "compact_mask_noalloc",
             "compact_mask_noalloc_error", "screen_positions",
-            "screen_positions_async", "screen_host"]
+            "screen_positions_async", "screen_host", "screen_batch_create", "screen_batch_run",
+            "screen_batch_info", "screen_batch_release"]
 
 
 def _check(rc: int, allow=()):
@@ -279,6 +299,40 @@ def screen_host(ctx, img: np.ndarray, sum_bits: int, sq_bits: int, tm, params: P
                                    ctypes.byref(params.c), _ptr(lst), 0 if lst is None else lst.size,
                                    ctypes.byref(n), _stream(stream)), allow=(SCR_EOVERFLOW,))
     return int(n.value), rc == SCR_EOVERFLOW
+
+
+# ---- batched screening ------------------------------------------------------
+
+def screen_batch_create(ctx, tables, tmpls, params, pairs, counts, keys, n_keys, offsets=None, union_mask=None,
+                        tuning=None, stream=None):
+    """tables, tmpls, params: lists (one params per template); pairs: list of
+    (image, template) indices.  Output tensors are caller-owned CUDA tensors."""
+    nt = len(tmpls)
+    tab_arr = (ctypes.c_void_p * len(tables))(*[t.value if hasattr(t, "value") else t for t in tables])
+    tm_arr = (ctypes.c_void_p * nt)(*[t.value if hasattr(t, "value") else t for t in tmpls])
+    par_arr = (_Params * nt)(*[p.c for p in params])
+    pr_arr = (_Pair * len(pairs))(*[_Pair(int(i), int(t)) for (i, t) in pairs])
+    tun = None if tuning is None else ctypes.byref(_Tuning(int(tuning[0]), int(tuning[1])))
+    out = ctypes.c_void_p()
+    _check(load().screen_batch_create(ctx, tab_arr, len(tables), tm_arr, par_arr, nt, pr_arr, len(pairs),
+                                      _ptr(counts), _ptr(offsets), _ptr(union_mask), _ptr(keys),
+                                      0 if keys is None else keys.numel(), _ptr(n_keys), tun, _stream(stream),
+                                      ctypes.byref(out)))
+    return out
+
+
+def screen_batch_run(b, stream=None) -> None:
+    _check(load().screen_batch_run(b, _stream(stream)))
+
+
+def screen_batch_info(b) -> dict:
+    info = _BatchInfo()
+    _check(load().screen_batch_info(b, ctypes.byref(info)))
+    return {n: int(getattr(info, n)) for n, _ in _BatchInfo._fields_}
+
+
+def screen_batch_release(ctx, b) -> None:
+    load().screen_batch_release(ctx, b)
 
 
 __all__ = [n for n in dir() if not n.startswith("_")]

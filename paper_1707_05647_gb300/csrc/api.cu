@@ -15,8 +15,12 @@
 #include <string>
 #include <vector>
 
+#include "batch.h"
 #include "internal.h"
 #include "screen.h"
+
+#include <chrono>
+#include <map>
 
 using namespace scr;
 
@@ -66,6 +70,8 @@ struct scr_tmpl {
     int64_t g_lo_n = 0, g_lo_d = 1, g_hi_n = 0, g_hi_d = 1;
 };
 
+struct scr_batch;
+
 struct scr_ctx {
     int device = 0;
     uint64_t budget = 0;
@@ -74,10 +80,37 @@ struct scr_ctx {
     std::mutex mu;
     std::set<scr_tables *> tables;
     std::set<scr_tmpl *> tmpls;
+    std::set<scr_batch *> batches;
+    std::map<std::string, std::pair<int, int>> tuned;   // batch shape -> (words per warp, blocks per SM)
     uint64_t *pinned = nullptr;      // 8-byte pinned slot for counts
 };
 
+struct scr_batch {
+    scr_ctx *ctx = nullptr;
+    int n_images = 0, n_pairs = 0;
+    std::vector<scr::BImage> images;
+    std::vector<scr::BGroup> groups;
+    std::vector<scr::BRecord> records;
+    void *desc = nullptr;            // device copy of images, groups, records
+    size_t desc_bytes = 0;
+    void *sort_buf = nullptr;        // radix-sort histogram + ping-pong keys
+    size_t sort_bytes = 0;
+    scr::BatchArgs args = {};
+    scr::SortArgs sargs = {};
+    int key_bits = 0;
+    int wpw = 8, blocks_per_sm = 4, grid = 0;
+    int64_t n_units = 0;
+    uint64_t candidates = 0;         // (record, valid position) pairs screened per run
+    uint64_t *offsets = nullptr;
+    uint64_t union_words = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
 namespace {
+
+void free_batch(scr_ctx *c, scr_batch *b);
 
 struct DeviceGuard {
     int prev = -1;
@@ -465,6 +498,9 @@ void screen_shutdown(scr_ctx *c) {
         for (auto *tm : c->tmpls)
             delete tm;
         c->tmpls.clear();
+        for (auto *b : c->batches)
+            free_batch(c, b);
+        c->batches.clear();
     }
     cudaDeviceSynchronize();
     if (c->pinned)
@@ -801,6 +837,413 @@ int screen_host(scr_ctx *c, const uint8_t *img_host, int32_t H, int32_t W, int64
         return fail(SCR_EOVERFLOW, "%llu survivors exceed list capacity %llu", (unsigned long long)*n_survivors,
                     (unsigned long long)list_cap);
     return rc;
+}
+
+
+// ---------------------------------------------------------------------------
+// Batched screening (many images x many templates, one persistent launch)
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+// Group the (pair, scale) records of every image by star radius and cut the
+// groups into units of one row x (8 * wpw) mask words.
+void plan_layout(scr_batch *b, int wpw) {
+    const int words_per_unit = 8 * wpw;
+    int64_t u = 0;
+    for (auto &g : b->groups) {
+        g.unit0 = u;
+        const int words = g.w_hi - g.w_lo + 1;
+        g.blocks_per_row = (words + words_per_unit - 1) / words_per_unit;
+        u += (int64_t)(g.y_hi - g.y_lo + 1) * g.blocks_per_row;
+    }
+    b->n_units = u;
+}
+
+int build_plan(scr_ctx *c, scr_batch *b, const scr_tables *const *tables, int n_images, const scr_tmpl *const *tmpls,
+               const scr_params *params, int n_tmpls, const scr_pair *pairs, int n_pairs) {
+    b->images.resize(n_images);
+    uint64_t moff = 0;
+    for (int i = 0; i < n_images; ++i) {
+        const scr_tables *t = tables[i];
+        BImage &im = b->images[i];
+        im.L1 = t->t[0].lo;
+        im.L2 = t->t[1].lo;
+        im.T1 = t->t[2].lo;
+        im.T2 = t->t[3].lo;
+        im.pitch = t->t[0].pitch;
+        im.H = t->H;
+        im.W = t->W;
+        im.Wwords = (t->W + 31) / 32;
+        im.mask_offset = (int64_t)moff;
+        moff += (uint64_t)t->H * im.Wwords;
+    }
+    b->union_words = moff;
+    // records per (image, R), in (pair, scale) order
+    std::vector<std::map<int, std::vector<BRecord>>> byR(n_images);
+    b->candidates = 0;
+    for (int p = 0; p < n_pairs; ++p) {
+        const int i = pairs[p].image, t = pairs[p].tmpl;
+        const scr_params *pp = &params[t];
+        for (int s = 0; s < pp->n_scales; ++s) {
+            const int R = pp->radii[s];
+            scr_bounds bd;
+            bounds_for(tmpls[t], pp, R, &bd);
+            BRecord rc = {};
+            rc.pair = (uint32_t)p;
+            rc.s = (uint32_t)s;
+            rc.features = pp->features;
+            rc.S_lo = 0;
+            rc.S_rng = UINT32_MAX;
+            bool empty = false;
+            if (pp->features & SCR_F_MEAN) {
+                const int64_t lo = std::max<int64_t>(bd.S_lo, 0), hi = std::min<int64_t>(bd.S_hi, UINT32_MAX);
+                if (lo > hi)
+                    empty = true;
+                else {
+                    rc.S_lo = (uint32_t)lo;
+                    rc.S_rng = (uint32_t)(hi - lo);
+                }
+            }
+            if (pp->features & SCR_F_VAR) {
+                empty = empty || bd.V_lo > bd.V_hi;
+                rc.V_lo = bd.V_lo;
+                rc.V_rng = (uint64_t)((i128)bd.V_hi - (i128)bd.V_lo);
+            }
+            if (pp->features & SCR_F_GRAD) {
+                empty = empty || bd.N_lo > bd.N_hi;
+                rc.N_lo = bd.N_lo;
+                rc.N_rng = (uint64_t)((i128)bd.N_hi - (i128)bd.N_lo);
+            }
+            const Geo g = geometry(R);
+            const int H = b->images[i].H, W = b->images[i].W;
+            const int ylo = std::max(g.n, g.h) - 1, yhi = H - 1 - std::max(g.n, g.h);
+            const int xlo = std::max(g.n, g.h) - 1, xhi = std::min(W - 1 - g.n, W - g.h);
+            if (yhi < ylo || xhi < xlo)
+                continue;   // no valid position at this scale
+            b->candidates += (uint64_t)(yhi - ylo + 1) * (uint64_t)(xhi - xlo + 1);
+            if (!empty)
+                byR[i][R].push_back(rc);
+        }
+    }
+    b->groups.clear();
+    b->records.clear();
+    for (int i = 0; i < n_images; ++i) {
+        const BImage &im = b->images[i];
+        const int64_t P = im.pitch;
+        for (auto &kv : byR[i]) {
+            const int R = kv.first;
+            const Geo g = geometry(R);
+            BGroup gr = {};
+            gr.image = i;
+            gr.R = R;
+            gr.y_lo = std::max(g.n, g.h) - 1;
+            gr.y_hi = im.H - 1 - std::max(g.n, g.h);
+            gr.x_lo = std::max(g.n, g.h) - 1;
+            gr.x_hi = std::min(im.W - 1 - g.n, im.W - g.h);
+            gr.w_lo = gr.x_lo / 32;
+            gr.w_hi = gr.x_hi / 32;
+            const int64_t n = g.n, h = g.h, ni = g.ni, hi = g.hi;
+            const int64_t oL[4] = {(n + 1) * P + (n + 1), (1 - n) * P + (n + 1), (n + 1) * P + (1 - n), (1 - n) * P + (1 - n)};
+            const int64_t oT[4] = {(h + 1) * P + 1, P + (1 - h), P + (h + 1), (1 - h) * P + 1};
+            const int64_t oLi[4] = {(ni + 1) * P + (ni + 1), (1 - ni) * P + (ni + 1), (ni + 1) * P + (1 - ni),
+                                    (1 - ni) * P + (1 - ni)};
+            const int64_t oTi[4] = {(hi + 1) * P + 1, P + (1 - hi), P + (hi + 1), (1 - hi) * P + 1};
+            for (int k = 0; k < 4; ++k) {
+                gr.oL[k] = (int32_t)oL[k];
+                gr.oT[k] = (int32_t)oT[k];
+                gr.oLi[k] = (int32_t)oLi[k];
+                gr.oTi[k] = (int32_t)oTi[k];
+            }
+            gr.A = (uint32_t)g.A;
+            gr.Ain = (uint32_t)g.Ain;
+            gr.Aring = (uint32_t)g.Aring;
+            uint64_t hlo = UINT32_MAX, hhi = 0;
+            gr.need = 0;
+            for (const BRecord &rc : kv.second) {
+                gr.need |= rc.features;
+                if (rc.features & SCR_F_MEAN) {
+                    hlo = std::min<uint64_t>(hlo, rc.S_lo);
+                    hhi = std::max<uint64_t>(hhi, (uint64_t)rc.S_lo + rc.S_rng);
+                } else {
+                    hlo = 0;
+                    hhi = UINT32_MAX;
+                }
+            }
+            gr.S_lo_hull = (uint32_t)hlo;
+            gr.S_rng_hull = (uint32_t)(hhi - hlo);
+            gr.rec0 = (int32_t)b->records.size();
+            b->records.insert(b->records.end(), kv.second.begin(), kv.second.end());
+            gr.rec1 = (int32_t)b->records.size();
+            b->groups.push_back(gr);
+        }
+    }
+    (void)c;
+    return SCR_OK;
+}
+
+int upload_plan(scr_batch *b, cudaStream_t st) {
+    std::vector<char> host(b->desc_bytes);
+    size_t off = 0;
+    memcpy(host.data() + off, b->images.data(), b->images.size() * sizeof(BImage));
+    off += (b->images.size() * sizeof(BImage) + 255) & ~size_t(255);
+    memcpy(host.data() + off, b->groups.data(), b->groups.size() * sizeof(BGroup));
+    off += (b->groups.size() * sizeof(BGroup) + 255) & ~size_t(255);
+    memcpy(host.data() + off, b->records.data(), b->records.size() * sizeof(BRecord));
+    CUDA_TRY(cudaMemcpyAsync(b->desc, host.data(), b->desc_bytes, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return SCR_OK;
+}
+
+size_t desc_size(const scr_batch *b) {
+    return ((b->images.size() * sizeof(BImage) + 255) & ~size_t(255)) +
+           ((b->groups.size() * sizeof(BGroup) + 255) & ~size_t(255)) +
+           ((b->records.size() * sizeof(BRecord) + 255) & ~size_t(255)) + 256;
+}
+
+void set_args(scr_batch *b) {
+    char *base = (char *)b->desc;
+    b->args.images = (const BImage *)base;
+    base += (b->images.size() * sizeof(BImage) + 255) & ~size_t(255);
+    b->args.groups = (const BGroup *)base;
+    base += (b->groups.size() * sizeof(BGroup) + 255) & ~size_t(255);
+    b->args.records = (const BRecord *)base;
+    b->args.n_groups = (int32_t)b->groups.size();
+    b->args.n_units = b->n_units;
+}
+
+int sm_count(int device) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device);
+    return n > 0 ? n : 1;
+}
+
+// One run: zero the outputs, screen, sort, offsets.
+int enqueue_run(scr_batch *b, cudaStream_t st, uint64_t *launches) {
+    if (b->union_words && b->args.union_mask)
+        CUDA_TRY(cudaMemsetAsync(b->args.union_mask, 0, b->union_words * 4, st));
+    CUDA_TRY(cudaMemsetAsync(b->args.counts, 0, (size_t)b->n_pairs * 8, st));
+    CUDA_TRY(cudaMemsetAsync(b->args.n_keys, 0, 8, st));
+    if (b->n_units > 0 && !b->groups.empty())
+        CUDA_TRY(launch_batch(b->args, b->wpw, b->grid, st, launches));
+    if (b->args.keys_cap > 0) {
+        bool in_scratch = false;
+        CUDA_TRY(launch_sort(b->sargs, b->key_bits, sm_count(b->ctx->device) * 4, st, launches, &in_scratch));
+        if (in_scratch)
+            return fail(SCR_ECUDA, "internal: radix sort ended in the scratch buffer");
+    }
+    if (b->offsets)
+        CUDA_TRY(launch_pair_offsets(b->args.counts, b->offsets, b->n_pairs, st, launches));
+    return SCR_OK;
+}
+
+void free_batch(scr_ctx *c, scr_batch *b) {
+    if (b->exec)
+        cudaGraphExecDestroy(b->exec);
+    if (b->graph)
+        cudaGraphDestroy(b->graph);
+    if (b->cap_stream) {
+        cudaStreamSynchronize(b->cap_stream);
+        cudaStreamDestroy(b->cap_stream);
+    }
+    dev_free(c, b->desc, b->desc_bytes, nullptr);
+    dev_free(c, b->sort_buf, b->sort_bytes, nullptr);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int screen_batch_create(scr_ctx *c, const scr_tables *const *tables, int32_t n_images, const scr_tmpl *const *tmpls,
+                        const scr_params *params, int32_t n_tmpls, const scr_pair *pairs, int32_t n_pairs,
+                        uint64_t *counts_dev, uint64_t *offsets_dev, uint32_t *union_mask_dev, uint64_t *keys_dev,
+                        uint64_t keys_cap, uint64_t *n_keys_dev, const scr_batch_tuning *tuning, scr_stream stream,
+                        scr_batch **out) {
+    int rc;
+    if ((rc = check_ctx(c)))
+        return rc;
+    if (!out || !tables || !tmpls || !params || !pairs || n_images < 1 || n_tmpls < 1 || n_pairs < 1)
+        return fail(SCR_EINVAL, "null or empty batch description");
+    if (n_pairs >= (1 << 26))
+        return fail(SCR_EINVAL, "at most 2^26 pairs");
+    if (!counts_dev || !n_keys_dev || (keys_cap && !keys_dev))
+        return fail(SCR_EINVAL, "null counts, key count or keys");
+    for (int i = 0; i < n_images; ++i) {
+        if (!tables[i])
+            return fail(SCR_EINVAL, "null tables for image %d", i);
+        if (tables[i]->H > 65535 || tables[i]->W > 65535)
+            return fail(SCR_EINVAL, "image %d too large for 16-bit key fields", i);
+    }
+    for (int t = 0; t < n_tmpls; ++t) {
+        if ((rc = check_screen_inputs(tables[0], tmpls[t], &params[t])))
+            return fail(rc, "template %d: %s", t, g_last_error.c_str());
+        if (params[t].n_scales > 32)
+            return fail(SCR_EINVAL, "template %d: more than 32 scales", t);
+    }
+    for (int p = 0; p < n_pairs; ++p)
+        if (pairs[p].image < 0 || pairs[p].image >= n_images || pairs[p].tmpl < 0 || pairs[p].tmpl >= n_tmpls)
+            return fail(SCR_EINVAL, "pair %d out of range", p);
+    *out = nullptr;
+    DeviceGuard dg(c->device);
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    auto *b = new (std::nothrow) scr_batch();
+    if (!b)
+        return fail(SCR_ENOMEM, "host allocation failed");
+    b->ctx = c;
+    b->n_images = n_images;
+    b->n_pairs = n_pairs;
+    build_plan(c, b, tables, n_images, tmpls, params, n_tmpls, pairs, n_pairs);
+    b->desc_bytes = desc_size(b);
+    int pbits = 1;
+    while ((1 << pbits) < n_pairs)
+        ++pbits;
+    b->key_bits = ((37 + pbits + 15) / 16) * 16;   // whole 8-bit passes, an even number of them
+    const uint64_t tiles = sort_max_tiles(keys_cap ? keys_cap : 1);
+    const size_t hist_bytes = (sort_hist_bytes(keys_cap ? keys_cap : 1) + 255) & ~size_t(255);
+    b->sort_bytes = hist_bytes + (size_t)(keys_cap ? keys_cap : 1) * 8;
+    if ((rc = dev_alloc(c, b->desc_bytes, st, &b->desc)) || (rc = dev_alloc(c, b->sort_bytes, st, &b->sort_buf))) {
+        free_batch(c, b);
+        return rc;
+    }
+    b->args.counts = counts_dev;
+    b->args.union_mask = union_mask_dev;
+    b->args.keys = keys_dev;
+    b->args.keys_cap = keys_cap;
+    b->args.n_keys = n_keys_dev;
+    b->offsets = offsets_dev;
+    b->sargs.src = keys_dev;
+    b->sargs.dst = (uint64_t *)((char *)b->sort_buf + hist_bytes);
+    b->sargs.hist = (uint32_t *)b->sort_buf;
+    b->sargs.n_keys = n_keys_dev;
+    b->sargs.cap = keys_cap;
+    b->sargs.max_tiles = tiles;
+    const int sms = sm_count(c->device);
+    // tuning: given, cached for this batch shape, or measured now
+    char key[160];
+    snprintf(key, sizeof key, "dev%d/img%d/pairs%d/groups%zu/records%zu/cand%llu", c->device, n_images, n_pairs,
+             b->groups.size(), b->records.size(), (unsigned long long)b->candidates);
+    std::vector<std::pair<int, int>> cand;
+    if (tuning && tuning->words_per_warp > 0) {
+        cand.push_back({tuning->words_per_warp, tuning->blocks_per_sm > 0 ? tuning->blocks_per_sm : 4});
+    } else if (c->tuned.count(key)) {
+        cand.push_back(c->tuned[key]);
+    } else {
+        for (int w : {2, 4, 8})
+            for (int bps : {2, 4, 8})
+                cand.push_back({w, bps});
+    }
+    for (auto &cf : cand)
+        if (cf.first != 2 && cf.first != 4 && cf.first != 8)
+            cf.first = 8;
+    float best = 1e30f;
+    std::pair<int, int> chosen = cand[0];
+    if (cand.size() > 1) {
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        for (auto cf : cand) {
+            b->wpw = cf.first;
+            b->blocks_per_sm = cf.second;
+            b->grid = sms * cf.second;
+            plan_layout(b, b->wpw);
+            if ((rc = upload_plan(b, st))) {
+                free_batch(c, b);
+                return rc;
+            }
+            set_args(b);
+            float ms = 0;
+            for (int rep = 0; rep < 2; ++rep) {   // first run warms up, second is timed
+                cudaMemsetAsync(b->args.counts, 0, (size_t)n_pairs * 8, st);
+                cudaMemsetAsync(b->args.n_keys, 0, 8, st);
+                cudaEventRecord(e0, st);
+                if (b->n_units > 0 && !b->groups.empty())
+                    launch_batch(b->args, b->wpw, b->grid, st, nullptr);
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (cudaGetLastError() != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                free_batch(c, b);
+                return fail(SCR_ECUDA, "batch kernel failed during tuning");
+            }
+            if (ms < best) {
+                best = ms;
+                chosen = cf;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        c->tuned[key] = chosen;
+    }
+    b->wpw = chosen.first;
+    b->blocks_per_sm = chosen.second;
+    b->grid = sms * chosen.second;
+    plan_layout(b, b->wpw);
+    if ((rc = upload_plan(b, st))) {
+        free_batch(c, b);
+        return rc;
+    }
+    set_args(b);
+    // capture one run into a CUDA graph on a private stream
+    cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        free_batch(c, b);
+        return fail(SCR_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    }
+    uint64_t n_launch = 0;
+    rc = enqueue_run(b, b->cap_stream, &n_launch);
+    e = cudaStreamEndCapture(b->cap_stream, &b->graph);
+    if (rc || e != cudaSuccess) {
+        free_batch(c, b);
+        return rc ? rc : fail(SCR_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) {
+        free_batch(c, b);
+        return fail(SCR_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    c->batches.insert(b);
+    *out = b;
+    return SCR_OK;
+}
+
+int screen_batch_run(scr_batch *b, scr_stream stream) {
+    if (!b)
+        return fail(SCR_EINVAL, "null batch");
+    DeviceGuard dg(b->ctx->device);
+    CUDA_TRY(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+    // the graph holds the screening kernel, the sort passes and the offsets
+    b->ctx->launches += 1 + (uint64_t)(b->key_bits / 8) * 3 + (b->offsets ? 1 : 0);
+    return SCR_OK;
+}
+
+int screen_batch_info(const scr_batch *b, scr_batch_info *out) {
+    if (!b || !out)
+        return fail(SCR_EINVAL, "null argument");
+    out->n_groups = (int64_t)b->groups.size();
+    out->n_records = (int64_t)b->records.size();
+    out->n_units = b->n_units;
+    out->candidates = b->candidates;
+    out->words_per_warp = b->wpw;
+    out->blocks_per_sm = b->blocks_per_sm;
+    out->union_words = b->union_words;
+    return SCR_OK;
+}
+
+void screen_batch_release(scr_ctx *c, scr_batch *b) {
+    if (!c || !b)
+        return;
+    DeviceGuard dg(c->device);
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (c->batches.erase(b))
+        free_batch(c, b);
 }
 
 }  // extern "C"

@@ -1,0 +1,376 @@
+// Batched screening: many images of uneven size against many templates and
+// scales in one persistent launch.
+//
+// Every (template, scale) that a pair (image, template) asks for becomes a
+// "record" (its pair, its scale index and its integer bounds).  Records are
+// grouped per image by star radius R: the features at each (position, R) --
+// star sum S, variance numerator V, contrast numerator N (Sec. 3, 4, 5) -- are
+// computed once and tested against every record of the group.  A group is cut
+// into units of one row x 64 mask words; a persistent grid walks the units.
+//
+// Survivors are appended as keys (pair << 37 | s << 32 | y << 16 | x) with
+// warp-aggregated atomics, counted per pair, and OR-ed into a per-image union
+// mask; a stable LSD radix sort then puts the keys in ascending order, so the
+// per-pair lists come out in the canonical (scale, row, column) order of the
+// single-image path.  No kernel waits on another CTA.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "batch.h"
+#include "internal.h"
+
+namespace scr {
+namespace {
+
+__device__ __forceinline__ uint32_t ldb(const uint32_t *p) { return __ldg(p); }
+
+template <int WPW>
+__device__ __forceinline__ void corner_sums(const uint32_t *L, const uint32_t *T, const int32_t (&oL)[4],
+                                            const int32_t (&oT)[4], uint32_t live, uint32_t (&out)[WPW]) {
+    const uint32_t *p0 = L + oL[0], *p1 = L + oL[1], *p2 = L + oL[2], *p3 = L + oL[3];
+    const uint32_t *q0 = T + oT[0], *q1 = T + oT[1], *q2 = T + oT[2], *q3 = T + oT[3];
+#pragma unroll
+    for (int j = 0; j < WPW; ++j) {
+        out[j] = 0;
+        if ((live >> j) & 1u) {
+            const int d = 32 * j;
+            out[j] = ldb(p0 + d) - ldb(p1 + d) - ldb(p2 + d) + ldb(p3 + d) + ldb(q0 + d) - ldb(q1 + d) -
+                     ldb(q2 + d) + ldb(q3 + d);
+        }
+    }
+}
+
+// Two window sums (square, diamond) of one table pair, each exact mod 2^32,
+// added in 64 bits (for the sums of squares).
+template <int WPW>
+__device__ __forceinline__ void corner_sums64(const uint32_t *L, const uint32_t *T, const int32_t (&oL)[4],
+                                              const int32_t (&oT)[4], uint32_t live, uint64_t (&out)[WPW]) {
+#pragma unroll
+    for (int j = 0; j < WPW; ++j) {
+        out[j] = 0;
+        if ((live >> j) & 1u) {
+            const int d = 32 * j;
+            const uint32_t a = ldb(L + oL[0] + d) - ldb(L + oL[1] + d) - ldb(L + oL[2] + d) + ldb(L + oL[3] + d);
+            const uint32_t b = ldb(T + oT[0] + d) - ldb(T + oT[1] + d) - ldb(T + oT[2] + d) + ldb(T + oT[3] + d);
+            out[j] = (uint64_t)a + b;
+        }
+    }
+}
+
+constexpr int kBatchWarps = 8;
+
+template <int WPW>
+__global__ void __launch_bounds__(32 * kBatchWarps) k_batch(const BatchArgs a) {
+    pdl_begin();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    for (int64_t u = blockIdx.x; u < a.n_units; u += gridDim.x) {
+        // group of this unit: last g with unit0[g] <= u (block-uniform binary search)
+        int lo = 0, hi = a.n_groups - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(&a.groups[mid].unit0) <= u)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const BGroup &gr = a.groups[lo];
+        const BImage &im = a.images[gr.image];
+        const int64_t local = u - gr.unit0;
+        const int y = gr.y_lo + (int)(local / gr.blocks_per_row);
+        const int cblock = (int)(local % gr.blocks_per_row);
+        const int w0 = gr.w_lo + (cblock * kBatchWarps + warp) * WPW;   // first word of this warp
+        if (w0 > gr.w_hi)
+            continue;
+        const int x0 = w0 * 32 + lane;
+        uint32_t live = 0;
+#pragma unroll
+        for (int j = 0; j < WPW; ++j) {
+            const int x = x0 + 32 * j;
+            if (x >= gr.x_lo && x <= gr.x_hi)
+                live |= 1u << j;
+        }
+        if (!__any_sync(0xffffffffu, live))
+            continue;
+        const int64_t e = (int64_t)y * im.pitch + x0 + kColOffset;
+        uint32_t S[WPW];
+        corner_sums<WPW>(im.L1 + e, im.T1 + e, gr.oL, gr.oT, live, S);
+        // fast reject against the hull of every record's mean interval
+        uint32_t alive = 0;
+#pragma unroll
+        for (int j = 0; j < WPW; ++j)
+            if (((live >> j) & 1u) && (S[j] - gr.S_lo_hull) <= gr.S_rng_hull)
+                alive |= 1u << j;
+        if (!__any_sync(0xffffffffu, alive))
+            continue;
+        uint64_t V[WPW], N[WPW];
+#pragma unroll
+        for (int j = 0; j < WPW; ++j)
+            V[j] = N[j] = 0;
+        if (gr.need & SCR_F_VAR) {
+            uint64_t Q[WPW];
+            corner_sums64<WPW>(im.L2 + e, im.T2 + e, gr.oL, gr.oT, alive, Q);
+#pragma unroll
+            for (int j = 0; j < WPW; ++j)
+                V[j] = (uint64_t)gr.A * Q[j] - (uint64_t)S[j] * S[j];
+        }
+        if (gr.need & SCR_F_GRAD) {
+            uint32_t Si[WPW];
+            corner_sums<WPW>(im.L1 + e, im.T1 + e, gr.oLi, gr.oTi, alive, Si);
+#pragma unroll
+            for (int j = 0; j < WPW; ++j)
+                N[j] = (uint64_t)((int64_t)((uint64_t)Si[j] * gr.Aring) -
+                                  (int64_t)((uint64_t)(S[j] - Si[j]) * gr.Ain));
+        }
+        uint32_t *umask = a.union_mask ? a.union_mask + im.mask_offset + (int64_t)y * im.Wwords : nullptr;
+        for (int r = gr.rec0; r < gr.rec1; ++r) {
+            const BRecord &rc = a.records[r];
+#pragma unroll
+            for (int j = 0; j < WPW; ++j) {
+                bool keep = (alive >> j) & 1u;
+                if (rc.features & SCR_F_MEAN)
+                    keep = keep && (S[j] - rc.S_lo) <= rc.S_rng;
+                if (rc.features & SCR_F_VAR)
+                    keep = keep && (V[j] - (uint64_t)rc.V_lo) <= rc.V_rng;
+                if (rc.features & SCR_F_GRAD)
+                    keep = keep && (N[j] - (uint64_t)rc.N_lo) <= rc.N_rng;
+                const uint32_t bits = __ballot_sync(0xffffffffu, keep);
+                if (!bits)
+                    continue;
+                uint64_t base = 0;
+                if (lane == 0) {
+                    const uint32_t c = __popc(bits);
+                    base = atomicAdd((unsigned long long *)a.n_keys, (unsigned long long)c);
+                    atomicAdd((unsigned long long *)&a.counts[rc.pair], (unsigned long long)c);
+                    if (umask)
+                        atomicOr(umask + w0 + j, bits);
+                }
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (keep) {
+                    const uint64_t pos = base + __popc(bits & lt_mask);
+                    if (pos < a.keys_cap)
+                        a.keys[pos] = ((uint64_t)rc.pair << 37) | ((uint64_t)rc.s << 32) |
+                                      ((uint64_t)y << 16) | (uint64_t)(x0 + 32 * j);
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Stable LSD radix sort of the keys, 8 bits per pass.  The key count lives in
+// device memory, so every kernel walks tiles with a grid stride and the grid
+// size is fixed (the sequence can be captured in a CUDA graph).
+// ---------------------------------------------------------------------------
+constexpr int RS_T = 256;                   // threads
+constexpr int RS_R = 8;                     // rounds (keys per thread) per tile
+constexpr int RS_TILE = RS_T * RS_R;        // 2048 keys per tile
+
+__device__ __forceinline__ uint64_t sort_count(const SortArgs &a) {
+    const uint64_t n = *a.n_keys;
+    return n < a.cap ? n : a.cap;
+}
+
+__global__ void __launch_bounds__(RS_T) k_rs_hist(const SortArgs a, int shift) {
+    pdl_begin();
+    __shared__ uint32_t h[256];
+    const uint64_t n = sort_count(a);
+    const uint64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        h[threadIdx.x] = 0;
+        __syncthreads();
+        for (int k = 0; k < RS_R; ++k) {
+            const uint64_t i = t * RS_TILE + (uint64_t)k * RS_T + threadIdx.x;
+            if (i < n)
+                atomicAdd(&h[(a.src[i] >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        a.hist[(uint64_t)threadIdx.x * a.max_tiles + t] = h[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+// Exclusive scan of hist in digit-major order (digit, tile), in place.
+__global__ void __launch_bounds__(1024) k_rs_scan(const SortArgs a) {
+    pdl_begin();
+    __shared__ uint64_t sh[72];
+    const uint64_t n = sort_count(a);
+    const uint64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    uint64_t carry = 0;
+    for (int d = 0; d < 256; ++d) {
+        uint32_t *row = a.hist + (uint64_t)d * a.max_tiles;
+        for (uint64_t b0 = 0; b0 < ntiles; b0 += 1024) {
+            const uint64_t i = b0 + t;
+            const uint64_t v = i < ntiles ? row[i] : 0;
+            uint64_t inc = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint64_t x = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o)
+                    inc += x;
+            }
+            if (lane == 31)
+                sh[w] = inc;
+            __syncthreads();
+            if (w == 0) {
+                const uint64_t s = sh[lane];
+                uint64_t si = s;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint64_t x = __shfl_up_sync(0xffffffffu, si, o);
+                    if (lane >= o)
+                        si += x;
+                }
+                sh[32 + lane] = si - s;
+                if (lane == 31)
+                    sh[64] = si;
+            }
+            __syncthreads();
+            if (i < ntiles)
+                row[i] = (uint32_t)(carry + sh[32 + w] + inc - v);
+            carry += sh[64];
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(RS_T) k_rs_scatter(const SortArgs a, int shift) {
+    pdl_begin();
+    constexpr int NW = RS_T / 32;
+    __shared__ uint32_t wcnt[NW][256];
+    __shared__ uint32_t run[256];
+    const uint64_t n = sort_count(a);
+    const uint64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        run[t] = a.hist[(uint64_t)t * a.max_tiles + tile];   // global start of each digit
+        __syncthreads();
+        for (int k = 0; k < RS_R; ++k) {
+            const uint64_t i = tile * RS_TILE + (uint64_t)k * RS_T + t;
+            const bool has = i < n;
+            const uint64_t key = has ? a.src[i] : 0;
+            const uint32_t d = has ? (uint32_t)((key >> shift) & 255u) : 256u + lane;   // distinct dummy digits
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+#pragma unroll
+            for (int q = 0; q < NW; ++q)
+                wcnt[q][t] = 0;
+            __syncthreads();
+            const uint32_t rank = __popc(peers & lt_mask);
+            if (has && rank == 0)
+                wcnt[w][d] = __popc(peers);
+            __syncthreads();
+            // prefix over warps for digit t, and the round total
+            uint32_t acc = 0;
+#pragma unroll
+            for (int q = 0; q < NW; ++q) {
+                const uint32_t c = wcnt[q][t];
+                wcnt[q][t] = acc;
+                acc += c;
+            }
+            __syncthreads();
+            if (has)
+                a.dst[run[d] + wcnt[w][d] + rank] = key;
+            __syncthreads();
+            run[t] += acc;
+            __syncthreads();
+        }
+    }
+}
+
+// offsets[p] = sum of counts[q] for q < p (one block, grid-independent).
+__global__ void __launch_bounds__(1024) k_pair_offsets(const uint64_t *counts, uint64_t *offsets, int n) {
+    pdl_begin();
+    __shared__ uint64_t sh[72];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    uint64_t carry = 0;
+    for (int b0 = 0; b0 < n; b0 += 1024) {
+        const int i = b0 + t;
+        const uint64_t v = i < n ? counts[i] : 0;
+        uint64_t inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t x = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o)
+                inc += x;
+        }
+        if (lane == 31)
+            sh[w] = inc;
+        __syncthreads();
+        if (w == 0) {
+            const uint64_t s = sh[lane];
+            uint64_t si = s;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint64_t x = __shfl_up_sync(0xffffffffu, si, o);
+                if (lane >= o)
+                    si += x;
+            }
+            sh[32 + lane] = si - s;
+            if (lane == 31)
+                sh[64] = si;
+        }
+        __syncthreads();
+        if (i < n)
+            offsets[i] = carry + sh[32 + w] + inc - v;
+        carry += sh[64];
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_batch(const BatchArgs &a, int words_per_warp, int grid, cudaStream_t st, uint64_t *launches) {
+    const dim3 block(32 * kBatchWarps);
+    cudaError_t e;
+    switch (words_per_warp) {
+        case 2: e = launch_pdl(k_batch<2>, dim3(grid), block, st, a); break;
+        case 4: e = launch_pdl(k_batch<4>, dim3(grid), block, st, a); break;
+        default: e = launch_pdl(k_batch<8>, dim3(grid), block, st, a); break;
+    }
+    if (launches)
+        *launches += 1;
+    return e;
+}
+
+int batch_unit_words() { return 64; }   // words per unit: kBatchWarps warps x up to 8 words
+
+size_t sort_hist_bytes(uint64_t cap) {
+    const uint64_t tiles = (cap + RS_TILE - 1) / RS_TILE;
+    return (size_t)tiles * 256 * 4;
+}
+
+uint64_t sort_max_tiles(uint64_t cap) { return (cap + RS_TILE - 1) / RS_TILE; }
+
+cudaError_t launch_sort(const SortArgs &base, int key_bits, int grid, cudaStream_t st, uint64_t *launches,
+                        bool *result_in_scratch) {
+    // ping-pong between keys and scratch; an even number of passes ends in keys
+    SortArgs a = base;
+    const int passes = (key_bits + 7) / 8;
+    uint64_t *bufs[2] = {base.src, base.dst};
+    cudaError_t e = cudaSuccess;
+    for (int p = 0; p < passes; ++p) {
+        a.src = bufs[p & 1];
+        a.dst = bufs[(p + 1) & 1];
+        if ((e = launch_pdl(k_rs_hist, dim3(grid), dim3(RS_T), st, a, 8 * p)) != cudaSuccess)
+            return e;
+        if ((e = launch_pdl(k_rs_scan, dim3(1), dim3(1024), st, a)) != cudaSuccess)
+            return e;
+        if ((e = launch_pdl(k_rs_scatter, dim3(grid), dim3(RS_T), st, a, 8 * p)) != cudaSuccess)
+            return e;
+        if (launches)
+            *launches += 3;
+    }
+    *result_in_scratch = (passes & 1) != 0;
+    return e;
+}
+
+cudaError_t launch_pair_offsets(const uint64_t *counts, uint64_t *offsets, int n, cudaStream_t st,
+                                uint64_t *launches) {
+    if (launches)
+        *launches += 1;
+    return launch_pdl(k_pair_offsets, dim3(1), dim3(1024), st, counts, offsets, n);
+}
+
+}  // namespace scr

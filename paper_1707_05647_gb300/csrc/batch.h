@@ -1,0 +1,67 @@
+// Internal structures of the batched screening path (see batch.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace scr {
+
+struct BImage {                        // one image's tables (low planes) and mask layout
+    const uint32_t *L1, *L2, *T1, *T2;
+    int64_t pitch;                     // words per table row
+    int32_t H, W, Wwords, pad;
+    int64_t mask_offset;               // first word of this image in the union mask
+};
+
+struct BGroup {                        // one (image, star radius R) and the records testing it
+    int64_t unit0;                     // first unit of the group (units are ordered by group)
+    int32_t image, R;
+    int32_t y_lo, y_hi, x_lo, x_hi;    // valid candidates (inclusive)
+    int32_t w_lo, w_hi;                // mask words covering [x_lo, x_hi]
+    int32_t blocks_per_row;            // units per row
+    int32_t oL[4], oT[4], oLi[4], oTi[4];   // corner offsets for this image's pitch
+    uint32_t A, Ain, Aring;
+    uint32_t S_lo_hull, S_rng_hull;    // union of the records' mean intervals
+    uint32_t need;                     // features any record of the group tests
+    int32_t rec0, rec1;                // records [rec0, rec1)
+};
+
+struct BRecord {                       // one (pair, scale) test
+    uint32_t pair, s, features;
+    uint32_t S_lo, S_rng;
+    int64_t V_lo;
+    uint64_t V_rng;
+    int64_t N_lo;
+    uint64_t N_rng;
+};
+
+struct BatchArgs {
+    const BImage *images;
+    const BGroup *groups;
+    const BRecord *records;
+    int32_t n_groups;
+    int64_t n_units;
+    uint64_t *counts;                  // per pair
+    uint32_t *union_mask;              // per image [H][Wwords], may be null
+    uint64_t *keys;
+    uint64_t keys_cap;
+    uint64_t *n_keys;
+};
+
+struct SortArgs {
+    uint64_t *src, *dst;
+    uint32_t *hist;                    // [256][max_tiles]
+    const uint64_t *n_keys;
+    uint64_t cap;
+    uint64_t max_tiles;
+};
+
+cudaError_t launch_batch(const BatchArgs &a, int words_per_warp, int grid, cudaStream_t st, uint64_t *launches);
+size_t sort_hist_bytes(uint64_t cap);
+uint64_t sort_max_tiles(uint64_t cap);
+cudaError_t launch_sort(const SortArgs &a, int key_bits, int grid, cudaStream_t st, uint64_t *launches,
+                        bool *result_in_scratch);
+cudaError_t launch_pair_offsets(const uint64_t *counts, uint64_t *offsets, int n, cudaStream_t st,
+                                uint64_t *launches);
+
+}  // namespace scr

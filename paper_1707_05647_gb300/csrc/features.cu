@@ -36,11 +36,6 @@ constexpr int kWarpsPerBlock = 8;
 
 __device__ __forceinline__ uint32_t ld(const uint32_t *p) { return __ldg(p); }
 
-// Sum over a window from its four corner values: c0 - c1 - c2 + c3 (mod 2^32).
-__device__ __forceinline__ uint32_t corners(const uint32_t *base, const int32_t (&o)[4]) {
-    return ld(base + o[0]) - ld(base + o[1]) - ld(base + o[2]) + ld(base + o[3]);
-}
-
 // Eight corner pointers of one star shape pair (square + diamond) for the
 // first word of a warp; word j reads 32*j elements further (immediate offset).
 struct Corners {

@@ -274,3 +274,71 @@ def random_image(seed: int, H: int, W: int, kind: str = "uniform") -> np.ndarray
 
 
 CONFIGS = {1: config1, 2: config2, 3: config3}
+
+
+@dataclass
+class TemplateSpec:
+    template: np.ndarray          # uint8 (2r+1) x (2r+1)
+    r: int
+    scales: list[float]
+    radii: list[int]
+    t_min: int
+
+
+@dataclass
+class BatchWorkload:
+    """Many images of uneven size against many templates (gallery search)."""
+    images: list[np.ndarray]
+    templates: list[TemplateSpec]
+    pairs: list[tuple[int, int]]                 # (image index, template index)
+    features: int
+    tol: Tolerances
+    sum_bits: int
+    sq_bits: int
+    plants: list[list[tuple[int, int, int, float]]]   # per image: (template, y, x, scale)
+
+
+def _batch_templates(rng, n, r_range, scale_range, max_scales):
+    out = []
+    for k in range(n):
+        r = int(rng.integers(r_range[0], r_range[1] + 1))
+        ns = int(rng.integers(1, max_scales + 1))
+        if ns == 1:
+            scales = [1.0]
+        else:
+            scales = geometric_scales(scale_range[0], scale_range[1], ns)
+        trng = rng_for(int(rng.integers(0, 2 ** 31)))
+        tm = _template_from_source(trng, r, src_side=max(192, 4 * (2 * r + 1)))
+        out.append(TemplateSpec(tm, r, scales, radii_for(r, scales), t_min_for(r, scales)))
+    return out
+
+
+def batch_workload(seed: int = BASE_SEED + 3, n_images: int = 64, n_templates: int = 256,
+                   area_range=(640 * 480, 4096 * 3072), r_range=(8, 64), scale_range=(0.5, 2.0),
+                   max_scales: int = 16, plants_per_image: int = 4, all_pairs: bool = True) -> BatchWorkload:
+    """Configuration 4: images with log-uniform area (4:3), templates with r ~ U{8..64}
+    and 1..16 geometric scales in [0.5, 2]; 4 planted copies per image."""
+    rng = rng_for(seed)
+    templates = _batch_templates(rng, n_templates, r_range, scale_range, max_scales)
+    images, plants = [], []
+    for _ in range(n_images):
+        area = math.exp(rng.uniform(math.log(area_range[0]), math.log(area_range[1])))
+        H = max(8, int(round(math.sqrt(area * 3.0 / 4.0))))
+        W = max(8, int(round(H * 4.0 / 3.0)))
+        fld = blob_field(rng, H, W)
+        pl = []
+        for _p in range(plants_per_image):
+            t = int(rng.integers(0, n_templates))
+            ts = templates[t]
+            s = float(math.exp(rng.uniform(math.log(ts.scales[0]), math.log(ts.scales[-1] * 1.0001))))
+            margin = int(math.ceil(s * (2 * ts.r + 1))) + 4
+            if H <= 2 * margin or W <= 2 * margin:
+                continue
+            y = int(rng.integers(margin, H - margin))
+            x = int(rng.integers(margin, W - margin))
+            paste(fld, ts.template, y + 0.5, x + 0.5, float(rng.uniform(0, 2 * math.pi)), s)
+            pl.append((t, y, x, s))
+        images.append(quantize_with_noise(fld, rng))
+        plants.append(pl)
+    pairs = [(i, t) for i in range(n_images) for t in range(n_templates)] if all_pairs else []
+    return BatchWorkload(images, templates, pairs, F_MEAN | F_VAR | F_GRAD, Tolerances(), 32, 64, plants)
