@@ -245,7 +245,7 @@ typedef struct {
 typedef struct {
     int64_t n_groups;       /* (image, star radius) groups */
     int64_t n_records;      /* (pair, scale) tests */
-    int64_t n_units;        /* units of work (one row x one block of mask words) */
+    int64_t n_units;        /* units of work (one row of one image x one star radius) */
     uint64_t candidates;    /* (pair, scale, valid position) candidates per run */
     int32_t words_per_warp, blocks_per_sm;
     uint64_t union_words;   /* words of the union mask */
@@ -267,9 +267,14 @@ typedef struct scr_batch scr_batch;
  *                         scale (may be NULL);
  *   keys_dev[keys_cap]    survivor keys (pair << 37) | (scale << 32) | (y << 16) | x
  *                         in ascending order, i.e. per pair in the (scale, row,
- *                         column) order of compact_mask; *n_keys_dev = the exact
- *                         total.  If the total exceeds keys_cap the keys are
- *                         unspecified (counts and mask stay exact).
+ *                         column) order of compact_mask;
+ *   n_keys_dev[2]         [0] = the exact number of survivors (keys_dev[0 ..
+ *                         n_keys_dev[0]) are the keys), [1] = key slots used.
+ *                         Slots are handed out to warps 256 at a time, so [1]
+ *                         can exceed [0] by at most about 290 per resident warp
+ *                         (< 3 M); the list is complete iff [1] <= keys_cap,
+ *                         otherwise the keys are unspecified (counts, offsets
+ *                         and the union mask stay exact).
  * Images up to 65535 x 65535, n_pairs < 2^26.  tuning NULL (or words_per_warp
  * 0) autotunes the launch shape on this batch and caches the choice in the
  * context.  The run (zeroing, screening kernel, radix sort, offsets) is

@@ -102,6 +102,8 @@ struct scr_batch {
     int64_t n_units = 0;
     uint64_t candidates = 0;         // (record, valid position) pairs screened per run
     uint64_t *offsets = nullptr;
+    uint64_t *n_keys = nullptr;      // caller's total-survivor count
+    uint64_t *n_reserved = nullptr;  // device counters of reserved key slots and handed-out units (in sort_buf)
     uint64_t union_words = 0;
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
@@ -847,16 +849,35 @@ int screen_host(scr_ctx *c, const uint8_t *img_host, int32_t H, int32_t W, int64
 
 namespace {
 
-// Group the (pair, scale) records of every image by star radius and cut the
-// groups into units of one row x (8 * wpw) mask words.
-void plan_layout(scr_batch *b, int wpw) {
-    const int words_per_unit = 8 * wpw;
+// Lay the units out row by row: for each image and row, one unit per group of
+// the image (groups whose valid rows exclude the row leave that unit empty).
+// The groups of an image are contiguous in b->groups.
+void plan_layout(scr_batch *b) {
+    std::vector<int> first(b->images.size(), -1), count(b->images.size(), 0);
+    for (size_t g = 0; g < b->groups.size(); ++g) {
+        const int i = b->groups[g].image;
+        if (first[i] < 0)
+            first[i] = (int)g;
+        ++count[i];
+    }
     int64_t u = 0;
-    for (auto &g : b->groups) {
-        g.unit0 = u;
-        const int words = g.w_hi - g.w_lo + 1;
-        g.blocks_per_row = (words + words_per_unit - 1) / words_per_unit;
-        u += (int64_t)(g.y_hi - g.y_lo + 1) * g.blocks_per_row;
+    for (size_t i = 0; i < b->images.size(); ++i) {
+        BImage &im = b->images[i];
+        im.unit0 = u;
+        im.g0 = std::max(first[i], 0);
+        im.n_grp = count[i];
+        im.y_first = 0;
+        im.rows = 0;
+        if (!count[i])
+            continue;
+        int ylo = INT32_MAX, yhi = -1;
+        for (int g = first[i]; g < first[i] + count[i]; ++g) {
+            ylo = std::min(ylo, b->groups[g].y_lo);
+            yhi = std::max(yhi, b->groups[g].y_hi);
+        }
+        im.y_first = ylo;
+        im.rows = yhi - ylo + 1;
+        u += (int64_t)im.rows * im.n_grp;
     }
     b->n_units = u;
 }
@@ -1009,8 +1030,10 @@ void set_args(scr_batch *b) {
     b->args.groups = (const BGroup *)base;
     base += (b->groups.size() * sizeof(BGroup) + 255) & ~size_t(255);
     b->args.records = (const BRecord *)base;
+    b->args.n_images = (int32_t)b->images.size();
     b->args.n_groups = (int32_t)b->groups.size();
     b->args.n_units = b->n_units;
+    b->args.unit_stride = 1;
 }
 
 int sm_count(int device) {
@@ -1024,7 +1047,7 @@ int enqueue_run(scr_batch *b, cudaStream_t st, uint64_t *launches) {
     if (b->union_words && b->args.union_mask)
         CUDA_TRY(cudaMemsetAsync(b->args.union_mask, 0, b->union_words * 4, st));
     CUDA_TRY(cudaMemsetAsync(b->args.counts, 0, (size_t)b->n_pairs * 8, st));
-    CUDA_TRY(cudaMemsetAsync(b->args.n_keys, 0, 8, st));
+    CUDA_TRY(cudaMemsetAsync(b->n_reserved, 0, 16, st));   // slot counter, unit counter
     if (b->n_units > 0 && !b->groups.empty())
         CUDA_TRY(launch_batch(b->args, b->wpw, b->grid, st, launches));
     if (b->args.keys_cap > 0) {
@@ -1033,8 +1056,7 @@ int enqueue_run(scr_batch *b, cudaStream_t st, uint64_t *launches) {
         if (in_scratch)
             return fail(SCR_ECUDA, "internal: radix sort ended in the scratch buffer");
     }
-    if (b->offsets)
-        CUDA_TRY(launch_pair_offsets(b->args.counts, b->offsets, b->n_pairs, st, launches));
+    CUDA_TRY(launch_pair_offsets(b->args.counts, b->offsets, b->n_keys, b->n_reserved, b->n_pairs, st, launches));
     return SCR_OK;
 }
 
@@ -1100,24 +1122,29 @@ int screen_batch_create(scr_ctx *c, const scr_tables *const *tables, int32_t n_i
     int pbits = 1;
     while ((1 << pbits) < n_pairs)
         ++pbits;
-    b->key_bits = ((37 + pbits + 15) / 16) * 16;   // whole 8-bit passes, an even number of them
+    // whole 8-bit passes, an even number of them, one bit above the largest key
+    // so the sentinel's low bits sort after every key
+    b->key_bits = ((38 + pbits + 15) / 16) * 16;
     const uint64_t tiles = sort_max_tiles(keys_cap ? keys_cap : 1);
     const size_t hist_bytes = (sort_hist_bytes(keys_cap ? keys_cap : 1) + 255) & ~size_t(255);
-    b->sort_bytes = hist_bytes + (size_t)(keys_cap ? keys_cap : 1) * 8;
+    b->sort_bytes = hist_bytes + (size_t)(keys_cap ? keys_cap : 1) * 8 + 256;
     if ((rc = dev_alloc(c, b->desc_bytes, st, &b->desc)) || (rc = dev_alloc(c, b->sort_bytes, st, &b->sort_buf))) {
         free_batch(c, b);
         return rc;
     }
+    b->n_reserved = (uint64_t *)((char *)b->sort_buf + b->sort_bytes - 256);
+    b->n_keys = n_keys_dev;
     b->args.counts = counts_dev;
     b->args.union_mask = union_mask_dev;
     b->args.keys = keys_dev;
     b->args.keys_cap = keys_cap;
-    b->args.n_keys = n_keys_dev;
+    b->args.n_reserved = b->n_reserved;
+    b->args.next_unit = b->n_reserved + 1;
     b->offsets = offsets_dev;
     b->sargs.src = keys_dev;
     b->sargs.dst = (uint64_t *)((char *)b->sort_buf + hist_bytes);
     b->sargs.hist = (uint32_t *)b->sort_buf;
-    b->sargs.n_keys = n_keys_dev;
+    b->sargs.n_keys = b->n_reserved;
     b->sargs.cap = keys_cap;
     b->sargs.max_tiles = tiles;
     const int sms = sm_count(c->device);
@@ -1148,19 +1175,23 @@ int screen_batch_create(scr_ctx *c, const scr_tables *const *tables, int32_t n_i
             b->wpw = cf.first;
             b->blocks_per_sm = cf.second;
             b->grid = sms * cf.second;
-            plan_layout(b, b->wpw);
+            plan_layout(b);
             if ((rc = upload_plan(b, st))) {
                 free_batch(c, b);
                 return rc;
             }
             set_args(b);
+            // time an evenly strided sample of about 2^17 units of this layout
+            BatchArgs sample = b->args;
+            sample.unit_stride = std::max<int64_t>(1, b->n_units >> 17);
+            sample.n_units = b->n_units / sample.unit_stride;
             float ms = 0;
             for (int rep = 0; rep < 2; ++rep) {   // first run warms up, second is timed
                 cudaMemsetAsync(b->args.counts, 0, (size_t)n_pairs * 8, st);
-                cudaMemsetAsync(b->args.n_keys, 0, 8, st);
+                cudaMemsetAsync(b->n_reserved, 0, 16, st);
                 cudaEventRecord(e0, st);
                 if (b->n_units > 0 && !b->groups.empty())
-                    launch_batch(b->args, b->wpw, b->grid, st, nullptr);
+                    launch_batch(sample, b->wpw, b->grid, st, nullptr);
                 cudaEventRecord(e1, st);
                 cudaEventSynchronize(e1);
                 cudaEventElapsedTime(&ms, e0, e1);
@@ -1183,7 +1214,7 @@ int screen_batch_create(scr_ctx *c, const scr_tables *const *tables, int32_t n_i
     b->wpw = chosen.first;
     b->blocks_per_sm = chosen.second;
     b->grid = sms * chosen.second;
-    plan_layout(b, b->wpw);
+    plan_layout(b);
     if ((rc = upload_plan(b, st))) {
         free_batch(c, b);
         return rc;
@@ -1220,7 +1251,7 @@ int screen_batch_run(scr_batch *b, scr_stream stream) {
     DeviceGuard dg(b->ctx->device);
     CUDA_TRY(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
     // the graph holds the screening kernel, the sort passes and the offsets
-    b->ctx->launches += 1 + (uint64_t)(b->key_bits / 8) * 3 + (b->offsets ? 1 : 0);
+    b->ctx->launches += 2 + (uint64_t)(b->key_bits / 8) * 3;
     return SCR_OK;
 }
 

@@ -8,11 +8,13 @@
 // computed once and tested against every record of the group.  A group is cut
 // into units of one row x 64 mask words; a persistent grid walks the units.
 //
-// Survivors are appended as keys (pair << 37 | s << 32 | y << 16 | x) with
-// warp-aggregated atomics, counted per pair, and OR-ed into a per-image union
-// mask; a stable LSD radix sort then puts the keys in ascending order, so the
-// per-pair lists come out in the canonical (scale, row, column) order of the
-// single-image path.  No kernel waits on another CTA.
+// Survivors are written as keys (pair << 37 | s << 32 | y << 16 | x) into
+// slots each warp reserves 256 at a time (one global atomic per chunk; unused
+// slots of a chunk get a sentinel that sorts last), counted per pair, and
+// OR-ed into a per-image union mask; a stable LSD radix sort then puts the
+// keys in ascending order, so the per-pair lists come out in the canonical
+// (scale, row, column) order of the single-image path.  No kernel waits on
+// another CTA.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -62,99 +64,160 @@ constexpr int kBatchWarps = 8;
 template <int WPW>
 __global__ void __launch_bounds__(32 * kBatchWarps) k_batch(const BatchArgs a) {
     pdl_begin();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const uint32_t lt_mask = (1u << lane) - 1u;
-    for (int64_t u = blockIdx.x; u < a.n_units; u += gridDim.x) {
-        // group of this unit: last g with unit0[g] <= u (block-uniform binary search)
-        int lo = 0, hi = a.n_groups - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(&a.groups[mid].unit0) <= u)
-                lo = mid;
-            else
-                hi = mid - 1;
+    uint64_t cpos = 0, cend = 0;   // this warp's reserved key slots [cpos, cend) (warp-uniform)
+    auto fill_rest = [&]() {       // sentinel into the unused slots of the current chunk
+        for (uint64_t k = cpos + lane; k < cend; k += 32)
+            if (k < a.keys_cap)
+                a.keys[k] = kKeySentinel;
+    };
+    // Each warp takes whole units from a global counter, in increasing order,
+    // so the units in flight stay within a few rows of each other and the
+    // table rows they read are still in L2 when the next radius needs them.
+    // The next index is fetched one unit ahead to hide the atomic's latency.
+    int img = -1;   // image of the current unit (warp-uniform)
+    uint64_t next = 0;
+    if (lane == 0)
+        next = atomicAdd((unsigned long long *)a.next_unit, 1ull);
+    next = __shfl_sync(0xffffffffu, next, 0);
+    while (next < (uint64_t)a.n_units) {
+        const int64_t u = (int64_t)next * a.unit_stride;
+        if (lane == 0)
+            next = atomicAdd((unsigned long long *)a.next_unit, 1ull);
+        next = __shfl_sync(0xffffffffu, next, 0);
+        if (img < 0) {
+            // first unit of this warp: last image with unit0 <= u (binary search)
+            int l = 0, h = a.n_images - 1;
+            while (l < h) {
+                const int mid = (l + h + 1) >> 1;
+                if (__ldg(&a.images[mid].unit0) <= u)
+                    l = mid;
+                else
+                    h = mid - 1;
+            }
+            img = l;
+        } else {
+            while (img + 1 < a.n_images && __ldg(&a.images[img + 1].unit0) <= u)
+                ++img;
         }
-        const BGroup &gr = a.groups[lo];
-        const BImage &im = a.images[gr.image];
-        const int64_t local = u - gr.unit0;
-        const int y = gr.y_lo + (int)(local / gr.blocks_per_row);
-        const int cblock = (int)(local % gr.blocks_per_row);
-        const int w0 = gr.w_lo + (cblock * kBatchWarps + warp) * WPW;   // first word of this warp
-        if (w0 > gr.w_hi)
+        const BImage &im = a.images[img];
+        const uint32_t local = (uint32_t)(u - im.unit0);   // < rows * n_grp
+        const int y = im.y_first + (int)(local / (uint32_t)im.n_grp);
+        const BGroup &gr = a.groups[im.g0 + (int)(local % (uint32_t)im.n_grp)];
+        if (y < gr.y_lo || y > gr.y_hi)
             continue;
-        const int x0 = w0 * 32 + lane;
-        uint32_t live = 0;
-#pragma unroll
-        for (int j = 0; j < WPW; ++j) {
-            const int x = x0 + 32 * j;
-            if (x >= gr.x_lo && x <= gr.x_hi)
-                live |= 1u << j;
-        }
-        if (!__any_sync(0xffffffffu, live))
-            continue;
-        const int64_t e = (int64_t)y * im.pitch + x0 + kColOffset;
-        uint32_t S[WPW];
-        corner_sums<WPW>(im.L1 + e, im.T1 + e, gr.oL, gr.oT, live, S);
-        // fast reject against the hull of every record's mean interval
-        uint32_t alive = 0;
-#pragma unroll
-        for (int j = 0; j < WPW; ++j)
-            if (((live >> j) & 1u) && (S[j] - gr.S_lo_hull) <= gr.S_rng_hull)
-                alive |= 1u << j;
-        if (!__any_sync(0xffffffffu, alive))
-            continue;
-        uint64_t V[WPW], N[WPW];
-#pragma unroll
-        for (int j = 0; j < WPW; ++j)
-            V[j] = N[j] = 0;
-        if (gr.need & SCR_F_VAR) {
-            uint64_t Q[WPW];
-            corner_sums64<WPW>(im.L2 + e, im.T2 + e, gr.oL, gr.oT, alive, Q);
-#pragma unroll
-            for (int j = 0; j < WPW; ++j)
-                V[j] = (uint64_t)gr.A * Q[j] - (uint64_t)S[j] * S[j];
-        }
-        if (gr.need & SCR_F_GRAD) {
-            uint32_t Si[WPW];
-            corner_sums<WPW>(im.L1 + e, im.T1 + e, gr.oLi, gr.oTi, alive, Si);
-#pragma unroll
-            for (int j = 0; j < WPW; ++j)
-                N[j] = (uint64_t)((int64_t)((uint64_t)Si[j] * gr.Aring) -
-                                  (int64_t)((uint64_t)(S[j] - Si[j]) * gr.Ain));
-        }
-        uint32_t *umask = a.union_mask ? a.union_mask + im.mask_offset + (int64_t)y * im.Wwords : nullptr;
-        for (int r = gr.rec0; r < gr.rec1; ++r) {
-            const BRecord &rc = a.records[r];
+        // the warp walks the row's mask words WPW at a time
+        for (int w0 = gr.w_lo; w0 <= gr.w_hi; w0 += WPW) {
+            const int x0 = w0 * 32 + lane;
+            uint32_t live = 0;
 #pragma unroll
             for (int j = 0; j < WPW; ++j) {
-                bool keep = (alive >> j) & 1u;
-                if (rc.features & SCR_F_MEAN)
-                    keep = keep && (S[j] - rc.S_lo) <= rc.S_rng;
-                if (rc.features & SCR_F_VAR)
-                    keep = keep && (V[j] - (uint64_t)rc.V_lo) <= rc.V_rng;
-                if (rc.features & SCR_F_GRAD)
-                    keep = keep && (N[j] - (uint64_t)rc.N_lo) <= rc.N_rng;
-                const uint32_t bits = __ballot_sync(0xffffffffu, keep);
-                if (!bits)
+                const int x = x0 + 32 * j;
+                if (x >= gr.x_lo && x <= gr.x_hi)
+                    live |= 1u << j;
+            }
+            if (!__any_sync(0xffffffffu, live))
+                continue;
+            const int64_t e = (int64_t)y * im.pitch + x0 + kColOffset;
+            uint32_t S[WPW];
+            corner_sums<WPW>(im.L1 + e, im.T1 + e, gr.oL, gr.oT, live, S);
+            // fast reject against the hull of every record's mean interval
+            uint32_t alive = 0;
+#pragma unroll
+            for (int j = 0; j < WPW; ++j)
+                if (((live >> j) & 1u) && (S[j] - gr.S_lo_hull) <= gr.S_rng_hull)
+                    alive |= 1u << j;
+            if (!__any_sync(0xffffffffu, alive))
+                continue;
+            // V and N are shared by every record of the group and computed on first
+            // use (warp-uniform), only if some lane still needs them
+            uint64_t V[WPW], N[WPW];
+            bool haveV = false, haveN = false;
+            uint32_t ubits[WPW];
+#pragma unroll
+            for (int j = 0; j < WPW; ++j)
+                V[j] = N[j] = 0, ubits[j] = 0;
+            for (int r = gr.rec0; r < gr.rec1; ++r) {
+                const BRecord &rc = a.records[r];
+                uint32_t keep = alive;
+                if (rc.features & SCR_F_MEAN) {
+#pragma unroll
+                    for (int j = 0; j < WPW; ++j)
+                        if ((S[j] - rc.S_lo) > rc.S_rng)
+                            keep &= ~(1u << j);
+                }
+                if (rc.features & SCR_F_VAR) {
+                    if (!haveV && __any_sync(0xffffffffu, keep)) {
+                        uint64_t Q[WPW];
+                        corner_sums64<WPW>(im.L2 + e, im.T2 + e, gr.oL, gr.oT, alive, Q);
+#pragma unroll
+                        for (int j = 0; j < WPW; ++j)
+                            V[j] = (uint64_t)gr.A * Q[j] - (uint64_t)S[j] * S[j];
+                        haveV = true;
+                    }
+#pragma unroll
+                    for (int j = 0; j < WPW; ++j)
+                        if ((V[j] - (uint64_t)rc.V_lo) > rc.V_rng)
+                            keep &= ~(1u << j);
+                }
+                if (rc.features & SCR_F_GRAD) {
+                    if (!haveN && __any_sync(0xffffffffu, keep)) {
+                        uint32_t Si[WPW];
+                        corner_sums<WPW>(im.L1 + e, im.T1 + e, gr.oLi, gr.oTi, alive, Si);
+#pragma unroll
+                        for (int j = 0; j < WPW; ++j)
+                            N[j] = (uint64_t)((int64_t)((uint64_t)Si[j] * gr.Aring) -
+                                              (int64_t)((uint64_t)(S[j] - Si[j]) * gr.Ain));
+                        haveN = true;
+                    }
+#pragma unroll
+                    for (int j = 0; j < WPW; ++j)
+                        if ((N[j] - (uint64_t)rc.N_lo) > rc.N_rng)
+                            keep &= ~(1u << j);
+                }
+                if (!__any_sync(0xffffffffu, keep))
                     continue;
-                uint64_t base = 0;
-                if (lane == 0) {
+                uint32_t nrec = 0;   // survivors of this record in the warp's words
+#pragma unroll
+                for (int j = 0; j < WPW; ++j) {
+                    const bool kj = (keep >> j) & 1u;
+                    const uint32_t bits = __ballot_sync(0xffffffffu, kj);
+                    if (!bits)
+                        continue;
+                    ubits[j] |= bits;
                     const uint32_t c = __popc(bits);
-                    base = atomicAdd((unsigned long long *)a.n_keys, (unsigned long long)c);
-                    atomicAdd((unsigned long long *)&a.counts[rc.pair], (unsigned long long)c);
-                    if (umask)
-                        atomicOr(umask + w0 + j, bits);
+                    nrec += c;
+                    if (cpos + c > cend) {   // new chunk of key slots
+                        fill_rest();
+                        uint64_t base = 0;
+                        if (lane == 0)
+                            base = atomicAdd((unsigned long long *)a.n_reserved, (unsigned long long)kKeyChunk);
+                        cpos = __shfl_sync(0xffffffffu, base, 0);
+                        cend = cpos + kKeyChunk;
+                    }
+                    if (kj) {
+                        const uint64_t pos = cpos + __popc(bits & lt_mask);
+                        if (pos < a.keys_cap)
+                            a.keys[pos] = ((uint64_t)rc.pair << 37) | ((uint64_t)rc.s << 32) |
+                                          ((uint64_t)y << 16) | (uint64_t)(x0 + 32 * j);
+                    }
+                    cpos += c;
                 }
-                base = __shfl_sync(0xffffffffu, base, 0);
-                if (keep) {
-                    const uint64_t pos = base + __popc(bits & lt_mask);
-                    if (pos < a.keys_cap)
-                        a.keys[pos] = ((uint64_t)rc.pair << 37) | ((uint64_t)rc.s << 32) |
-                                      ((uint64_t)y << 16) | (uint64_t)(x0 + 32 * j);
-                }
+                if (lane == 0 && nrec)
+                    atomicAdd((unsigned long long *)&a.counts[rc.pair], (unsigned long long)nrec);
+            }
+            if (a.union_mask && lane < WPW) {   // one OR per word of the unit: lane j writes word j
+                uint32_t mine = 0;
+#pragma unroll
+                for (int j = 0; j < WPW; ++j)
+                    mine = lane == j ? ubits[j] : mine;
+                if (mine)
+                    atomicOr(a.union_mask + im.mask_offset + (int64_t)y * im.Wwords + w0 + lane, mine);
             }
         }
     }
+    fill_rest();
 }
 
 // ---------------------------------------------------------------------------
@@ -280,7 +343,8 @@ __global__ void __launch_bounds__(RS_T) k_rs_scatter(const SortArgs a, int shift
 }
 
 // offsets[p] = sum of counts[q] for q < p (one block, grid-independent).
-__global__ void __launch_bounds__(1024) k_pair_offsets(const uint64_t *counts, uint64_t *offsets, int n) {
+__global__ void __launch_bounds__(1024) k_pair_offsets(const uint64_t *counts, uint64_t *offsets, uint64_t *total,
+                                                       const uint64_t *reserved, int n) {
     pdl_begin();
     __shared__ uint64_t sh[72];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -312,10 +376,14 @@ __global__ void __launch_bounds__(1024) k_pair_offsets(const uint64_t *counts, u
                 sh[64] = si;
         }
         __syncthreads();
-        if (i < n)
+        if (i < n && offsets)
             offsets[i] = carry + sh[32 + w] + inc - v;
         carry += sh[64];
         __syncthreads();
+    }
+    if (t == 0) {
+        total[0] = carry;                     // survivors
+        total[1] = reserved ? *reserved : 0;  // key slots used (>= survivors)
     }
 }
 
@@ -366,11 +434,11 @@ cudaError_t launch_sort(const SortArgs &base, int key_bits, int grid, cudaStream
     return e;
 }
 
-cudaError_t launch_pair_offsets(const uint64_t *counts, uint64_t *offsets, int n, cudaStream_t st,
-                                uint64_t *launches) {
+cudaError_t launch_pair_offsets(const uint64_t *counts, uint64_t *offsets, uint64_t *total, const uint64_t *reserved,
+                                int n, cudaStream_t st, uint64_t *launches) {
     if (launches)
         *launches += 1;
-    return launch_pdl(k_pair_offsets, dim3(1), dim3(1024), st, counts, offsets, n);
+    return launch_pdl(k_pair_offsets, dim3(1), dim3(1024), st, counts, offsets, total, reserved, n);
 }
 
 }  // namespace scr

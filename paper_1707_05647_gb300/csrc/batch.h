@@ -11,14 +11,18 @@ struct BImage {                        // one image's tables (low planes) and ma
     int64_t pitch;                     // words per table row
     int32_t H, W, Wwords, pad;
     int64_t mask_offset;               // first word of this image in the union mask
+    // units of this image: one per (row, group), row-major, so the blocks that
+    // run together read the same table rows for every radius and the tables
+    // stream from DRAM about once
+    int64_t unit0;                     // first unit of the image
+    int32_t y_first, rows;             // rows y_first .. y_first + rows - 1
+    int32_t g0, n_grp;                 // groups g0 .. g0 + n_grp - 1 belong to this image
 };
 
 struct BGroup {                        // one (image, star radius R) and the records testing it
-    int64_t unit0;                     // first unit of the group (units are ordered by group)
     int32_t image, R;
     int32_t y_lo, y_hi, x_lo, x_hi;    // valid candidates (inclusive)
     int32_t w_lo, w_hi;                // mask words covering [x_lo, x_hi]
-    int32_t blocks_per_row;            // units per row
     int32_t oL[4], oT[4], oLi[4], oTi[4];   // corner offsets for this image's pitch
     uint32_t A, Ain, Aring;
     uint32_t S_lo_hull, S_rng_hull;    // union of the records' mean intervals
@@ -39,19 +43,25 @@ struct BatchArgs {
     const BImage *images;
     const BGroup *groups;
     const BRecord *records;
+    int32_t n_images;
     int32_t n_groups;
-    int64_t n_units;
+    int64_t n_units;                   // units this launch processes
+    int64_t unit_stride;               // unit u of the launch is unit u * unit_stride of the plan
     uint64_t *counts;                  // per pair
     uint32_t *union_mask;              // per image [H][Wwords], may be null
     uint64_t *keys;
     uint64_t keys_cap;
-    uint64_t *n_keys;
+    uint64_t *n_reserved;              // key slots handed out (chunks of kKeyChunk)
+    uint64_t *next_unit;               // next unit to hand out (zero before the launch)
 };
+
+constexpr uint64_t kKeySentinel = ~0ull;   // fills unused reserved slots; sorts last
+constexpr int kKeyChunk = 256;             // key slots a warp reserves at a time
 
 struct SortArgs {
     uint64_t *src, *dst;
     uint32_t *hist;                    // [256][max_tiles]
-    const uint64_t *n_keys;
+    const uint64_t *n_keys;            // slots to sort (clamped to cap)
     uint64_t cap;
     uint64_t max_tiles;
 };
@@ -61,7 +71,7 @@ size_t sort_hist_bytes(uint64_t cap);
 uint64_t sort_max_tiles(uint64_t cap);
 cudaError_t launch_sort(const SortArgs &a, int key_bits, int grid, cudaStream_t st, uint64_t *launches,
                         bool *result_in_scratch);
-cudaError_t launch_pair_offsets(const uint64_t *counts, uint64_t *offsets, int n, cudaStream_t st,
-                                uint64_t *launches);
+cudaError_t launch_pair_offsets(const uint64_t *counts, uint64_t *offsets, uint64_t *total, const uint64_t *reserved,
+                                int n, cudaStream_t st, uint64_t *launches);
 
 }  // namespace scr

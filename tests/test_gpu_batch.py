@@ -71,7 +71,7 @@ def _run(ctx, bw, pairs, tables, tmpls, params, cap, tuning=None):
     uw = sum(im.shape[0] * ((im.shape[1] + 31) // 32) for im in bw.images)
     union = torch.zeros(uw, dtype=torch.int32, device="cuda")
     keys = torch.zeros(cap, dtype=torch.int64, device="cuda")
-    nk = torch.zeros(1, dtype=torch.int64, device="cuda")
+    nk = torch.zeros(2, dtype=torch.int64, device="cuda")
     b = scr.screen_batch_create(ctx, tables, tmpls, params, pairs, counts, keys, nk, offsets=offsets,
                                 union_mask=union, tuning=tuning)
     return b, counts, offsets, union, keys, nk
@@ -81,8 +81,9 @@ def _check(bw, got, want):
     b, counts, offsets, union, keys, nk = got
     wkeys, wcounts, wunions = want
     torch.cuda.synchronize()
-    n = int(nk.item())
+    n, slots = int(nk[0].item()), int(nk[1].item())
     assert n == len(wkeys)
+    assert n <= slots <= keys.numel()
     assert np.array_equal(counts.cpu().numpy().view(np.uint64), wcounts)
     off = np.concatenate([[0], np.cumsum(wcounts)[:-1]]).astype(np.uint64)
     assert np.array_equal(offsets.cpu().numpy().view(np.uint64), off)
@@ -136,6 +137,6 @@ def test_batch_key_overflow_keeps_counts_exact(ctx):
     got = _run(ctx, bw, pairs, tables, tmpls, params, cap=8)
     scr.screen_batch_run(got[0])
     torch.cuda.synchronize()
-    assert int(got[5].item()) == len(want[0])
+    assert int(got[5][0].item()) == len(want[0])
     assert np.array_equal(got[1].cpu().numpy().view(np.uint64), want[1])
     scr.screen_batch_release(ctx, got[0])
