@@ -249,6 +249,8 @@ typedef struct {
     uint64_t candidates;    /* (pair, scale, valid position) candidates per run */
     int32_t words_per_warp, blocks_per_sm;
     uint64_t union_words;   /* words of the union mask */
+    int32_t sort_passes;    /* 8-bit radix passes over the keys packed to their used widths */
+    int32_t reserved;
 } scr_batch_info;
 
 typedef struct scr_batch scr_batch;

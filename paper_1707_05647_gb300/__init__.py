@@ -57,7 +57,8 @@ class _Tuning(ctypes.Structure):
 class _BatchInfo(ctypes.Structure):
     _fields_ = [("n_groups", ctypes.c_int64), ("n_records", ctypes.c_int64), ("n_units", ctypes.c_int64),
                 ("candidates", ctypes.c_uint64), ("words_per_warp", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("union_words", ctypes.c_uint64)]
+                ("blocks_per_sm", ctypes.c_int32), ("union_words", ctypes.c_uint64),
+                ("sort_passes", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _lib = None

@@ -97,7 +97,7 @@ struct scr_batch {
     size_t sort_bytes = 0;
     scr::BatchArgs args = {};
     scr::SortArgs sargs = {};
-    int key_bits = 0;
+    int sort_passes = 0;             // 8-bit radix passes over the packed keys
     int wpw = 8, blocks_per_sm = 4, grid = 0;
     int64_t n_units = 0;
     uint64_t candidates = 0;         // (record, valid position) pairs screened per run
@@ -995,6 +995,10 @@ int build_plan(scr_ctx *c, scr_batch *b, const scr_tables *const *tables, int n_
             gr.S_lo_hull = (uint32_t)hlo;
             gr.S_rng_hull = (uint32_t)(hhi - hlo);
             gr.rec0 = (int32_t)b->records.size();
+            // ascending mean-interval start, so a warp stops at the first record
+            // whose interval starts above every mean it holds
+            std::stable_sort(kv.second.begin(), kv.second.end(),
+                             [](const BRecord &x, const BRecord &y) { return x.S_lo < y.S_lo; });
             b->records.insert(b->records.end(), kv.second.begin(), kv.second.end());
             gr.rec1 = (int32_t)b->records.size();
             b->groups.push_back(gr);
@@ -1051,10 +1055,7 @@ int enqueue_run(scr_batch *b, cudaStream_t st, uint64_t *launches) {
     if (b->n_units > 0 && !b->groups.empty())
         CUDA_TRY(launch_batch(b->args, b->wpw, b->grid, st, launches));
     if (b->args.keys_cap > 0) {
-        bool in_scratch = false;
-        CUDA_TRY(launch_sort(b->sargs, b->key_bits, sm_count(b->ctx->device) * 4, st, launches, &in_scratch));
-        if (in_scratch)
-            return fail(SCR_ECUDA, "internal: radix sort ended in the scratch buffer");
+        CUDA_TRY(launch_sort(b->sargs, b->sort_passes, sm_count(b->ctx->device) * 4, st, launches));
     }
     CUDA_TRY(launch_pair_offsets(b->args.counts, b->offsets, b->n_keys, b->n_reserved, b->n_pairs, st, launches));
     return SCR_OK;
@@ -1119,31 +1120,52 @@ int screen_batch_create(scr_ctx *c, const scr_tables *const *tables, int32_t n_i
     b->n_pairs = n_pairs;
     build_plan(c, b, tables, n_images, tmpls, params, n_tmpls, pairs, n_pairs);
     b->desc_bytes = desc_size(b);
-    int pbits = 1;
-    while ((1 << pbits) < n_pairs)
-        ++pbits;
-    // whole 8-bit passes, an even number of them, one bit above the largest key
-    // so the sentinel's low bits sort after every key
-    b->key_bits = ((38 + pbits + 15) / 16) * 16;
-    const uint64_t tiles = sort_max_tiles(keys_cap ? keys_cap : 1);
-    const size_t hist_bytes = (sort_hist_bytes(keys_cap ? keys_cap : 1) + 255) & ~size_t(255);
-    b->sort_bytes = hist_bytes + (size_t)(keys_cap ? keys_cap : 1) * 8 + 256;
+    // sort on the key fields cut to their used widths: column, row, scale, and
+    // pair with one value to spare so that the all-ones sentinel sorts last
+    auto bits_for = [](uint64_t v) {   // bits to hold 0 .. v
+        uint32_t k = 1;
+        while (k < 64 && (v >> k))
+            ++k;
+        return k;
+    };
+    int maxH = 1, maxW = 1, maxS = 1;
+    for (int i = 0; i < n_images; ++i) {
+        maxH = std::max(maxH, tables[i]->H);
+        maxW = std::max(maxW, tables[i]->W);
+    }
+    for (int t = 0; t < n_tmpls; ++t)
+        maxS = std::max(maxS, params[t].n_scales);
+    b->sargs.xb = bits_for((uint64_t)maxW - 1);
+    b->sargs.yb = bits_for((uint64_t)maxH - 1);
+    b->sargs.sb = bits_for((uint64_t)maxS - 1);
+    b->sargs.pb = bits_for((uint64_t)n_pairs);
+    b->sort_passes = (int)((b->sargs.xb + b->sargs.yb + b->sargs.sb + b->sargs.pb + 7) / 8);
+    const uint64_t cap1 = keys_cap ? keys_cap : 1;
+    const uint64_t tiles = sort_max_tiles(cap1);
+    const size_t hist_bytes = (sort_hist_bytes(cap1) + 255) & ~size_t(255);
+    const size_t csum_bytes = (sort_csum_bytes(cap1) + 255) & ~size_t(255);
+    b->sort_bytes = hist_bytes + csum_bytes + (size_t)cap1 * 8 + 256;
     if ((rc = dev_alloc(c, b->desc_bytes, st, &b->desc)) || (rc = dev_alloc(c, b->sort_bytes, st, &b->sort_buf))) {
         free_batch(c, b);
         return rc;
     }
     b->n_reserved = (uint64_t *)((char *)b->sort_buf + b->sort_bytes - 256);
     b->n_keys = n_keys_dev;
+    uint64_t *scratch = (uint64_t *)((char *)b->sort_buf + hist_bytes + csum_bytes);
+    // the screening kernel writes the unsorted keys where an odd or even number
+    // of sort passes ends in the caller's buffer
+    uint64_t *first = (b->sort_passes & 1) ? scratch : keys_dev;
     b->args.counts = counts_dev;
     b->args.union_mask = union_mask_dev;
-    b->args.keys = keys_dev;
+    b->args.keys = first;
     b->args.keys_cap = keys_cap;
     b->args.n_reserved = b->n_reserved;
     b->args.next_unit = b->n_reserved + 1;
     b->offsets = offsets_dev;
-    b->sargs.src = keys_dev;
-    b->sargs.dst = (uint64_t *)((char *)b->sort_buf + hist_bytes);
+    b->sargs.src = first;
+    b->sargs.dst = (b->sort_passes & 1) ? keys_dev : scratch;
     b->sargs.hist = (uint32_t *)b->sort_buf;
+    b->sargs.csum = (uint64_t *)((char *)b->sort_buf + hist_bytes);
     b->sargs.n_keys = b->n_reserved;
     b->sargs.cap = keys_cap;
     b->sargs.max_tiles = tiles;
@@ -1251,7 +1273,7 @@ int screen_batch_run(scr_batch *b, scr_stream stream) {
     DeviceGuard dg(b->ctx->device);
     CUDA_TRY(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
     // the graph holds the screening kernel, the sort passes and the offsets
-    b->ctx->launches += 2 + (uint64_t)(b->key_bits / 8) * 3;
+    b->ctx->launches += 2 + (uint64_t)(b->args.keys_cap ? b->sort_passes * kSortLaunchesPerPass : 0);
     return SCR_OK;
 }
 
@@ -1265,6 +1287,8 @@ int screen_batch_info(const scr_batch *b, scr_batch_info *out) {
     out->words_per_warp = b->wpw;
     out->blocks_per_sm = b->blocks_per_sm;
     out->union_words = b->union_words;
+    out->sort_passes = b->args.keys_cap ? b->sort_passes : 0;
+    out->reserved = 0;
     return SCR_OK;
 }
 

@@ -138,8 +138,25 @@ __global__ void __launch_bounds__(32 * kBatchWarps) k_batch(const BatchArgs a) {
 #pragma unroll
             for (int j = 0; j < WPW; ++j)
                 V[j] = N[j] = 0, ubits[j] = 0;
+            // the warp's range of means among alive positions: records are sorted
+            // by interval start (records without a mean test start at 0 and span
+            // everything), so the walk skips disjoint intervals and stops early
+            uint32_t smin = UINT32_MAX, smax = 0;
+#pragma unroll
+            for (int j = 0; j < WPW; ++j)
+                if ((alive >> j) & 1u) {
+                    smin = min(smin, S[j]);
+                    smax = max(smax, S[j]);
+                }
+            smin = __reduce_min_sync(0xffffffffu, smin);
+            smax = __reduce_max_sync(0xffffffffu, smax);
             for (int r = gr.rec0; r < gr.rec1; ++r) {
                 const BRecord &rc = a.records[r];
+                const uint32_t slo = __ldg(&rc.S_lo);
+                if (slo > smax)
+                    break;
+                if (slo + __ldg(&rc.S_rng) < smin)
+                    continue;
                 uint32_t keep = alive;
                 if (rc.features & SCR_F_MEAN) {
 #pragma unroll
@@ -228,12 +245,26 @@ __global__ void __launch_bounds__(32 * kBatchWarps) k_batch(const BatchArgs a) {
 constexpr int RS_T = 256;                   // threads
 constexpr int RS_R = 8;                     // rounds (keys per thread) per tile
 constexpr int RS_TILE = RS_T * RS_R;        // 2048 keys per tile
+constexpr int RS_E = 32;                    // scan entries per thread
+constexpr int RS_CH = RS_T * RS_E;          // 8192 histogram entries per scan chunk
 
 __device__ __forceinline__ uint64_t sort_count(const SortArgs &a) {
     const uint64_t n = *a.n_keys;
     return n < a.cap ? n : a.cap;
 }
 
+// The key (pair << 37 | s << 32 | y << 16 | x) with each field cut to its used
+// width; the sentinel ~0 becomes all ones and stays last because every real
+// pair index is below 2^pb - 1.
+__device__ __forceinline__ uint32_t sort_digit(uint64_t k, const SortArgs &a, int shift) {
+    const uint64_t x = k & 0xFFFFu, y = (k >> 16) & 0xFFFFu, s = (k >> 32) & 31u, p = k >> 37;
+    const uint64_t c = (x & ((1ull << a.xb) - 1)) | ((y & ((1ull << a.yb) - 1)) << a.xb) |
+                       ((s & ((1ull << a.sb) - 1)) << (a.xb + a.yb)) |
+                       ((p & ((1ull << a.pb) - 1)) << (a.xb + a.yb + a.sb));
+    return (uint32_t)(c >> shift) & 255u;
+}
+
+// hist[d * ntiles + t] = keys of tile t with digit d
 __global__ void __launch_bounds__(RS_T) k_rs_hist(const SortArgs a, int shift) {
     pdl_begin();
     __shared__ uint32_t h[256];
@@ -245,100 +276,201 @@ __global__ void __launch_bounds__(RS_T) k_rs_hist(const SortArgs a, int shift) {
         for (int k = 0; k < RS_R; ++k) {
             const uint64_t i = t * RS_TILE + (uint64_t)k * RS_T + threadIdx.x;
             if (i < n)
-                atomicAdd(&h[(a.src[i] >> shift) & 255u], 1u);
+                atomicAdd(&h[sort_digit(a.src[i], a, shift)], 1u);
         }
         __syncthreads();
-        a.hist[(uint64_t)threadIdx.x * a.max_tiles + t] = h[threadIdx.x];
+        a.hist[(uint64_t)threadIdx.x * ntiles + t] = h[threadIdx.x];
         __syncthreads();
     }
 }
 
-// Exclusive scan of hist in digit-major order (digit, tile), in place.
+// Exclusive scan of 256 values of one block (one per thread); returns the total.
+__device__ __forceinline__ uint32_t block_exscan256(uint32_t v, uint32_t *sh, uint32_t &total) {
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t x = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o)
+            inc += x;
+    }
+    if (lane == 31)
+        sh[w] = inc;
+    __syncthreads();
+    uint32_t before = 0;
+    total = 0;
+#pragma unroll
+    for (int q = 0; q < RS_T / 32; ++q) {
+        const uint32_t c = sh[q];
+        before += q < w ? c : 0u;
+        total += c;
+    }
+    __syncthreads();
+    return before + inc - v;
+}
+
+// csum[c] = sum of histogram chunk c (RS_CH entries in digit-major order)
+__global__ void __launch_bounds__(RS_T) k_rs_reduce(const SortArgs a) {
+    pdl_begin();
+    __shared__ uint32_t sh[RS_T / 32];
+    const uint64_t n = sort_count(a);
+    const uint64_t m = 256 * ((n + RS_TILE - 1) / RS_TILE);
+    const uint64_t nc = (m + RS_CH - 1) / RS_CH;
+    for (uint64_t c = blockIdx.x; c < nc; c += gridDim.x) {
+        const uint64_t i0 = c * RS_CH + (uint64_t)threadIdx.x * RS_E;   // m is a multiple of RS_E
+        uint32_t v = 0;
+        if (i0 < m) {
+            const uint4 *p = reinterpret_cast<const uint4 *>(a.hist + i0);
+#pragma unroll
+            for (int q = 0; q < RS_E / 4; ++q) {
+                const uint4 x = p[q];
+                v += x.x + x.y + x.z + x.w;
+            }
+        }
+        uint32_t total;
+        block_exscan256(v, sh, total);
+        if (threadIdx.x == 0)
+            a.csum[c] = total;
+    }
+}
+
+// Exclusive scan of the chunk sums, in place (one block).
 __global__ void __launch_bounds__(1024) k_rs_scan(const SortArgs a) {
     pdl_begin();
     __shared__ uint64_t sh[72];
     const uint64_t n = sort_count(a);
-    const uint64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
+    const uint64_t m = 256 * ((n + RS_TILE - 1) / RS_TILE);
+    const uint64_t nc = (m + RS_CH - 1) / RS_CH;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     uint64_t carry = 0;
-    for (int d = 0; d < 256; ++d) {
-        uint32_t *row = a.hist + (uint64_t)d * a.max_tiles;
-        for (uint64_t b0 = 0; b0 < ntiles; b0 += 1024) {
-            const uint64_t i = b0 + t;
-            const uint64_t v = i < ntiles ? row[i] : 0;
-            uint64_t inc = v;
+    for (uint64_t b0 = 0; b0 < nc; b0 += 1024) {
+        const uint64_t i = b0 + t;
+        const uint64_t v = i < nc ? a.csum[i] : 0;
+        uint64_t inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t x = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o)
+                inc += x;
+        }
+        if (lane == 31)
+            sh[w] = inc;
+        __syncthreads();
+        if (w == 0) {
+            const uint64_t s = sh[lane];
+            uint64_t si = s;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const uint64_t x = __shfl_up_sync(0xffffffffu, inc, o);
+                const uint64_t x = __shfl_up_sync(0xffffffffu, si, o);
                 if (lane >= o)
-                    inc += x;
+                    si += x;
             }
+            sh[32 + lane] = si - s;
             if (lane == 31)
-                sh[w] = inc;
-            __syncthreads();
-            if (w == 0) {
-                const uint64_t s = sh[lane];
-                uint64_t si = s;
+                sh[64] = si;
+        }
+        __syncthreads();
+        if (i < nc)
+            a.csum[i] = carry + sh[32 + w] + inc - v;
+        carry += sh[64];
+        __syncthreads();
+    }
+}
+
+// hist entries become offsets within their chunk (below RS_CH * RS_TILE)
+__global__ void __launch_bounds__(RS_T) k_rs_down(const SortArgs a) {
+    pdl_begin();
+    __shared__ uint32_t sh[RS_T / 32];
+    const uint64_t n = sort_count(a);
+    const uint64_t m = 256 * ((n + RS_TILE - 1) / RS_TILE);
+    const uint64_t nc = (m + RS_CH - 1) / RS_CH;
+    for (uint64_t c = blockIdx.x; c < nc; c += gridDim.x) {
+        const uint64_t i0 = c * RS_CH + (uint64_t)threadIdx.x * RS_E;
+        uint4 *p = reinterpret_cast<uint4 *>(a.hist + i0);
+        uint4 x[RS_E / 4];
+        uint32_t v = 0;
+        if (i0 < m) {
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint64_t x = __shfl_up_sync(0xffffffffu, si, o);
-                    if (lane >= o)
-                        si += x;
-                }
-                sh[32 + lane] = si - s;
-                if (lane == 31)
-                    sh[64] = si;
+            for (int q = 0; q < RS_E / 4; ++q) {
+                x[q] = p[q];
+                v += x[q].x + x[q].y + x[q].z + x[q].w;
             }
-            __syncthreads();
-            if (i < ntiles)
-                row[i] = (uint32_t)(carry + sh[32 + w] + inc - v);
-            carry += sh[64];
-            __syncthreads();
+        }
+        uint32_t total;
+        uint32_t run = block_exscan256(v, sh, total);
+        if (i0 < m) {
+#pragma unroll
+            for (int q = 0; q < RS_E / 4; ++q) {
+                uint4 o;
+                o.x = run; run += x[q].x;
+                o.y = run; run += x[q].y;
+                o.z = run; run += x[q].z;
+                o.w = run; run += x[q].w;
+                p[q] = o;
+            }
         }
     }
 }
 
+// Stable scatter of one tile: warp w owns keys [w * 256, w * 256 + 256) of the
+// tile (in order), counts them per digit, the warps' counts are scanned per
+// digit, and each warp then writes its keys at the digit's running position.
 __global__ void __launch_bounds__(RS_T) k_rs_scatter(const SortArgs a, int shift) {
     pdl_begin();
     constexpr int NW = RS_T / 32;
-    __shared__ uint32_t wcnt[NW][256];
-    __shared__ uint32_t run[256];
+    __shared__ uint32_t wofs[NW][256];
+    __shared__ uint64_t start[256];
     const uint64_t n = sort_count(a);
     const uint64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const uint32_t lt_mask = (1u << lane) - 1u;
     for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        run[t] = a.hist[(uint64_t)t * a.max_tiles + tile];   // global start of each digit
+        const uint64_t h = (uint64_t)t * ntiles + tile;
+        start[t] = a.csum[h / RS_CH] + a.hist[h];   // where digit t of this tile starts
+#pragma unroll
+        for (int q = 0; q < NW; ++q)
+            wofs[q][t] = 0;
         __syncthreads();
-        for (int k = 0; k < RS_R; ++k) {
-            const uint64_t i = tile * RS_TILE + (uint64_t)k * RS_T + t;
+        uint64_t key[RS_R];
+        uint32_t dg[RS_R], peers[RS_R];
+        const uint64_t base = tile * RS_TILE + (uint64_t)w * (RS_R * 32) + lane;
+#pragma unroll
+        for (int r = 0; r < RS_R; ++r) {
+            const uint64_t i = base + 32 * r;
             const bool has = i < n;
-            const uint64_t key = has ? a.src[i] : 0;
-            const uint32_t d = has ? (uint32_t)((key >> shift) & 255u) : 256u + lane;   // distinct dummy digits
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
-#pragma unroll
-            for (int q = 0; q < NW; ++q)
-                wcnt[q][t] = 0;
-            __syncthreads();
-            const uint32_t rank = __popc(peers & lt_mask);
-            if (has && rank == 0)
-                wcnt[w][d] = __popc(peers);
-            __syncthreads();
-            // prefix over warps for digit t, and the round total
-            uint32_t acc = 0;
-#pragma unroll
-            for (int q = 0; q < NW; ++q) {
-                const uint32_t c = wcnt[q][t];
-                wcnt[q][t] = acc;
-                acc += c;
-            }
-            __syncthreads();
-            if (has)
-                a.dst[run[d] + wcnt[w][d] + rank] = key;
-            __syncthreads();
-            run[t] += acc;
-            __syncthreads();
+            key[r] = has ? a.src[i] : 0;
+            dg[r] = has ? sort_digit(key[r], a, shift) : 256u + lane;   // distinct dummy digits
         }
+#pragma unroll
+        for (int r = 0; r < RS_R; ++r) {
+            peers[r] = __match_any_sync(0xffffffffu, dg[r]);
+            if (dg[r] < 256u && (peers[r] & lt_mask) == 0)   // lowest lane of its digit group
+                wofs[w][dg[r]] += __popc(peers[r]);
+            __syncwarp();
+        }
+        __syncthreads();
+        uint32_t acc = 0;   // digit t: warps before each warp
+#pragma unroll
+        for (int q = 0; q < NW; ++q) {
+            const uint32_t c = wofs[q][t];
+            wofs[q][t] = acc;
+            acc += c;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < RS_R; ++r) {
+            const uint32_t d = dg[r];
+            uint32_t before = 0;
+            if (d < 256u) {
+                before = wofs[w][d];
+                a.dst[start[d] + before + __popc(peers[r] & lt_mask)] = key[r];
+            }
+            __syncwarp();
+            if (d < 256u && (peers[r] & lt_mask) == 0)
+                wofs[w][d] = before + __popc(peers[r]);
+            __syncwarp();
+        }
+        __syncthreads();
     }
 }
 
@@ -402,35 +534,34 @@ cudaError_t launch_batch(const BatchArgs &a, int words_per_warp, int grid, cudaS
     return e;
 }
 
-int batch_unit_words() { return 64; }   // words per unit: kBatchWarps warps x up to 8 words
-
 size_t sort_hist_bytes(uint64_t cap) {
     const uint64_t tiles = (cap + RS_TILE - 1) / RS_TILE;
     return (size_t)tiles * 256 * 4;
 }
 
+size_t sort_csum_bytes(uint64_t cap) {
+    const uint64_t m = 256 * ((cap + RS_TILE - 1) / RS_TILE);
+    return (size_t)((m + RS_CH - 1) / RS_CH + 1) * 8;
+}
+
 uint64_t sort_max_tiles(uint64_t cap) { return (cap + RS_TILE - 1) / RS_TILE; }
 
-cudaError_t launch_sort(const SortArgs &base, int key_bits, int grid, cudaStream_t st, uint64_t *launches,
-                        bool *result_in_scratch) {
-    // ping-pong between keys and scratch; an even number of passes ends in keys
+cudaError_t launch_sort(const SortArgs &base, int passes, int grid, cudaStream_t st, uint64_t *launches) {
     SortArgs a = base;
-    const int passes = (key_bits + 7) / 8;
     uint64_t *bufs[2] = {base.src, base.dst};
     cudaError_t e = cudaSuccess;
     for (int p = 0; p < passes; ++p) {
         a.src = bufs[p & 1];
         a.dst = bufs[(p + 1) & 1];
-        if ((e = launch_pdl(k_rs_hist, dim3(grid), dim3(RS_T), st, a, 8 * p)) != cudaSuccess)
-            return e;
-        if ((e = launch_pdl(k_rs_scan, dim3(1), dim3(1024), st, a)) != cudaSuccess)
-            return e;
-        if ((e = launch_pdl(k_rs_scatter, dim3(grid), dim3(RS_T), st, a, 8 * p)) != cudaSuccess)
+        if ((e = launch_pdl(k_rs_hist, dim3(grid), dim3(RS_T), st, a, 8 * p)) != cudaSuccess ||
+            (e = launch_pdl(k_rs_reduce, dim3(grid), dim3(RS_T), st, a)) != cudaSuccess ||
+            (e = launch_pdl(k_rs_scan, dim3(1), dim3(1024), st, a)) != cudaSuccess ||
+            (e = launch_pdl(k_rs_down, dim3(grid), dim3(RS_T), st, a)) != cudaSuccess ||
+            (e = launch_pdl(k_rs_scatter, dim3(grid), dim3(RS_T), st, a, 8 * p)) != cudaSuccess)
             return e;
         if (launches)
-            *launches += 3;
+            *launches += kSortLaunchesPerPass;
     }
-    *result_in_scratch = (passes & 1) != 0;
     return e;
 }
 

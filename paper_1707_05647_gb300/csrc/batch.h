@@ -59,18 +59,24 @@ constexpr uint64_t kKeySentinel = ~0ull;   // fills unused reserved slots; sorts
 constexpr int kKeyChunk = 256;             // key slots a warp reserves at a time
 
 struct SortArgs {
-    uint64_t *src, *dst;
-    uint32_t *hist;                    // [256][max_tiles]
+    uint64_t *src, *dst;               // ping-pong key buffers (src holds the unsorted keys)
+    uint32_t *hist;                    // [256][tiles] digit counts, then chunk-local offsets
+    uint64_t *csum;                    // per scan chunk: sum, then exclusive offset
     const uint64_t *n_keys;            // slots to sort (clamped to cap)
     uint64_t cap;
     uint64_t max_tiles;
+    // sort on the key's fields packed to their used widths (column, row, scale,
+    // pair), so fewer 8-bit passes are needed; each field keeps its rank
+    uint32_t xb, yb, sb, pb;
 };
 
 cudaError_t launch_batch(const BatchArgs &a, int words_per_warp, int grid, cudaStream_t st, uint64_t *launches);
 size_t sort_hist_bytes(uint64_t cap);
+size_t sort_csum_bytes(uint64_t cap);
 uint64_t sort_max_tiles(uint64_t cap);
-cudaError_t launch_sort(const SortArgs &a, int key_bits, int grid, cudaStream_t st, uint64_t *launches,
-                        bool *result_in_scratch);
+constexpr int kSortLaunchesPerPass = 5;
+// passes 8-bit passes; the result is in a.src after an even number, a.dst after an odd one
+cudaError_t launch_sort(const SortArgs &a, int passes, int grid, cudaStream_t st, uint64_t *launches);
 cudaError_t launch_pair_offsets(const uint64_t *counts, uint64_t *offsets, uint64_t *total, const uint64_t *reserved,
                                 int n, cudaStream_t st, uint64_t *launches);
 

@@ -130,6 +130,25 @@ def test_batch_subset_and_repeated_pairs(ctx):
     scr.screen_batch_release(ctx, got[0])
 
 
+@pytest.mark.parametrize("n_pairs", [7, 8, 9, 40])
+def test_batch_sort_pass_parity(ctx, n_pairs):
+    """The packed sort key's width (column, row, scale and pair bits) sets the
+    number of 8-bit passes; odd counts start from the scratch buffer.  Both
+    parities end with the canonical order in the caller's buffer."""
+    bw, _, feats, tols, tables, tmpls, params = _setup(ctx, 35, 4, 10)
+    pairs = [(k % 4, (3 * k) % 10) for k in range(n_pairs)]
+    want = _oracle(bw, pairs, feats, tols)
+    got = _run(ctx, bw, pairs, tables, tmpls, params, cap=1 << 20)
+    scr.screen_batch_run(got[0])
+    _check(bw, got, want)
+    H = max(im.shape[0] for im in bw.images)
+    W = max(im.shape[1] for im in bw.images)
+    S = max(len(ts.radii) for ts in bw.templates)
+    bits = (W - 1).bit_length() + (H - 1).bit_length() + max(1, (S - 1).bit_length()) + n_pairs.bit_length()
+    assert scr.screen_batch_info(got[0])["sort_passes"] == (bits + 7) // 8
+    scr.screen_batch_release(ctx, got[0])
+
+
 def test_batch_key_overflow_keeps_counts_exact(ctx):
     bw, pairs, feats, tols, tables, tmpls, params = _setup(ctx, 34, 3, 4)
     want = _oracle(bw, pairs, feats, tols)
