@@ -68,6 +68,7 @@ enum {
     SCR_ECUDA = -4,       /* a CUDA runtime call or kernel launch failed */
     SCR_ETIMEOUT = -5,    /* reserved: a bounded device-side wait gave up */
     SCR_EOVERFLOW = -6,   /* more survivors than list capacity (mask still complete) */
+    SCR_EEVICTED = -7,    /* the image's tables and host copy were dropped (server_forget) */
     SCR_EUNSUPPORTED = -8 /* valid request outside what this build implements */
 };
 
@@ -295,6 +296,115 @@ int screen_batch_run(scr_batch *b, scr_stream stream);
 int screen_batch_info(const scr_batch *b, scr_batch_info *out);
 
 void screen_batch_release(scr_ctx *ctx, scr_batch *b);
+
+/* ---- serving loop ---------------------------------------------------------
+ *
+ * A server owns one worker thread and one stream on the context's device.
+ * Clients upload images (the server keeps a host copy, or borrows the caller's)
+ * and submit screen requests from any thread; both return at once with a
+ * request id.  Whenever the worker is free it takes every queued request
+ * (continuous batching, at most max_batch), makes the images they need resident
+ * (building their tables, or rebuilding tables evicted earlier from the host
+ * copy; least recently used unpinned tables are evicted while the resident
+ * tables would exceed table_budget_bytes), then screens all queued screen
+ * requests of the batch in one batched run (SCR_SERVE_BATCHED: records grouped
+ * per (image, star radius) as in screen_batch_create) or one plain
+ * screen_features + compact_mask each (SCR_SERVE_PLAIN), and writes each
+ * request's survivor list, in compact_mask's key format and order, to the
+ * caller's host buffer.  A request's result does not depend on which other
+ * requests share its batch, nor on the mode.  This is the paper's screen
+ * (Sec. 5, Algorithm 1) served to many clients; the paper has no serving loop. */
+typedef struct scr_server scr_server;
+
+enum { SCR_SERVE_BATCHED = 0, SCR_SERVE_PLAIN = 1 };
+
+typedef struct {
+    uint64_t table_budget_bytes; /* resident tables above this are evicted, LRU first; 0 = no limit */
+    int32_t sum_bits, sq_bits;   /* table widths for every image (32 or 64) */
+    int32_t mode;                /* SCR_SERVE_BATCHED or SCR_SERVE_PLAIN */
+    int32_t max_batch;           /* most requests per batch; 0 = every queued request */
+    int32_t start_held;          /* 1: queue requests without serving them until server_hold(s, 0) */
+    int32_t words_per_warp;      /* batched launch shape (0 = 4) */
+    int32_t blocks_per_sm;       /* (0 = 4) */
+    int32_t reserved;
+} scr_server_config;
+
+typedef struct {
+    int32_t status;     /* SCR_OK; SCR_EOVERFLOW (list truncated to list_cap, count exact); or an error */
+    int32_t kind;       /* 0 upload (tables built), 1 screen, 2 evict */
+    uint64_t count;     /* survivors of a screen */
+    int64_t arrival_ns; /* the arrival stamp given at submission (server_clock_ns clock) */
+    int64_t start_ns;   /* when the worker took the request's batch */
+    int64_t done_ns;    /* when the result was written */
+    uint64_t batch;     /* sequence number of the batch that served it */
+    int32_t batch_size; /* requests in that batch */
+    int32_t built;      /* 1 when this request built or rebuilt tables */
+} scr_request_result;
+
+typedef struct {
+    uint64_t requests, batches, uploads, screens;
+    uint64_t builds, rebuilds, evictions;
+    uint64_t resident_images, resident_bytes, peak_resident_bytes;
+    uint64_t keys_capacity;      /* device key slots the batched path holds */
+    uint64_t launches;           /* kernels the worker launched */
+} scr_server_stats;
+
+/* CLOCK_MONOTONIC in nanoseconds: the clock of arrival, start and done stamps. */
+int64_t server_clock_ns(void);
+
+/* Create a server on ctx (the context must outlive it; screen_shutdown destroys
+ * servers still open).  Synchronous. */
+int server_create(scr_ctx *ctx, const scr_server_config *cfg, scr_server **out);
+
+/* Queue an upload: H x W uint8 at img_host (pitch bytes per row).  borrow = 0
+ * copies the pixels now (the caller may reuse its buffer at once); borrow = 1
+ * keeps the pointer, which must stay valid until server_forget or destroy.
+ * *image_id names the image from now on; the request completes when its tables
+ * are built.  arrival_ns = 0 stamps the call time. */
+int server_upload(scr_server *s, const uint8_t *img_host, int32_t H, int32_t W, int64_t pitch, int32_t borrow,
+                  int64_t arrival_ns, int64_t *image_id, uint64_t *request_id);
+
+/* Queue a screen of image image_id against tm with params p (copied, radii
+ * included; tm must stay valid until the request completes).  list_host
+ * (caller-owned host memory, list_cap keys, may be NULL with list_cap 0) gets
+ * the first list_cap survivor keys (s << 48) | (y << 24) | x in ascending order. */
+int server_screen(scr_server *s, int64_t image_id, const scr_tmpl *tm, const scr_params *p, uint64_t *list_host,
+                  uint64_t list_cap, int64_t arrival_ns, uint64_t *request_id);
+
+/* Queue an eviction of the image's tables (the host copy stays; a later
+ * screen rebuilds them). */
+int server_evict(scr_server *s, int64_t image_id, uint64_t *request_id);
+
+/* Drop the image: its tables when the worker next runs, and the host copy.
+ * Screens queued or submitted later on it complete with SCR_EEVICTED. */
+int server_forget(scr_server *s, int64_t image_id);
+
+/* Wait up to timeout_us (< 0: forever) for the request; on completion write its
+ * result and forget the id.  SCR_ETIMEOUT if still pending, SCR_EINVAL for an
+ * unknown or already collected id. */
+int server_wait(scr_server *s, uint64_t request_id, int64_t timeout_us, scr_request_result *out);
+
+/* hold = 1: the worker takes no new batch (the one running completes);
+ * hold = 0: serving resumes. */
+int server_hold(scr_server *s, int32_t hold);
+
+/* *resident = 1 when the image's tables are on the device now. */
+int server_resident(scr_server *s, int64_t image_id, int32_t *resident);
+
+int server_stats(scr_server *s, scr_server_stats *out);
+
+/* Finish every queued request, stop the worker and free the server. */
+void server_destroy(scr_server *s);
+
+/* Eviction policy of the serving loop, pure host code: among n resident tables
+ * with sizes bytes[i], last-use stamps last_use[i] (larger = more recent) and
+ * pinned[i] != 0 for tables the current batch uses, pick victims least
+ * recently used first (ties: lower index first), skipping pinned ones, until
+ * resident - freed + need <= budget.  Writes their indices in eviction order
+ * to victims (room for n) and their number to *n_victims.  Returns SCR_EBUDGET
+ * when evicting every unpinned table is not enough (then *n_victims = 0). */
+int server_lru_victims(const uint64_t *bytes, const uint64_t *last_use, const int32_t *pinned, int32_t n,
+                       uint64_t resident, uint64_t budget, uint64_t need, int32_t *victims, int32_t *n_victims);
 
 /* ---- whole path from host memory ----------------------------------------- */
 

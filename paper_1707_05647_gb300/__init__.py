@@ -18,7 +18,8 @@ from . import _build
 
 F_MEAN, F_VAR, F_GRAD = 1, 2, 4
 SCR_OK, SCR_EINVAL, SCR_ENOMEM, SCR_EBUDGET, SCR_ECUDA, SCR_ETIMEOUT, SCR_EOVERFLOW = 0, -1, -2, -3, -4, -5, -6
-SCR_EUNSUPPORTED = -8
+SCR_EEVICTED, SCR_EUNSUPPORTED = -7, -8
+SERVE_BATCHED, SERVE_PLAIN = 0, 1
 MAX_SCALES = 32
 
 
@@ -62,6 +63,23 @@ class _BatchInfo(ctypes.Structure):
 
 
 _lib = None
+
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("table_budget_bytes", ctypes.c_uint64), ("sum_bits", ctypes.c_int32), ("sq_bits", ctypes.c_int32),
+                ("mode", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("start_held", ctypes.c_int32),
+                ("words_per_warp", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class _RequestResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("kind", ctypes.c_int32), ("count", ctypes.c_uint64),
+                ("arrival_ns", ctypes.c_int64), ("start_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64),
+                ("batch", ctypes.c_uint64), ("batch_size", ctypes.c_int32), ("built", ctypes.c_int32)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "requests", "batches", "uploads", "screens", "builds", "rebuilds", "evictions", "resident_images",
+        "resident_bytes", "peak_resident_bytes", "keys_capacity", "launches")]
 
 
 def library_path() -> str:
@@ -107,6 +125,18 @@ def load(build_if_missing: bool = True):
         "screen_batch_run": ([vp, vp], ctypes.c_int),
         "screen_batch_info": ([vp, ctypes.POINTER(_BatchInfo)], ctypes.c_int),
         "screen_batch_release": ([vp, vp], None),
+        "server_clock_ns": ([], i64),
+        "server_create": ([vp, ctypes.POINTER(_ServerConfig), pp], ctypes.c_int),
+        "server_upload": ([vp, vp, i32, i32, i64, i32, i64, ctypes.POINTER(i64), ctypes.POINTER(u64)], ctypes.c_int),
+        "server_screen": ([vp, i64, vp, ctypes.POINTER(_Params), vp, u64, i64, ctypes.POINTER(u64)], ctypes.c_int),
+        "server_evict": ([vp, i64, ctypes.POINTER(u64)], ctypes.c_int),
+        "server_forget": ([vp, i64], ctypes.c_int),
+        "server_wait": ([vp, u64, i64, ctypes.POINTER(_RequestResult)], ctypes.c_int),
+        "server_hold": ([vp, i32], ctypes.c_int),
+        "server_resident": ([vp, i64, ctypes.POINTER(i32)], ctypes.c_int),
+        "server_stats": ([vp, ctypes.POINTER(_ServerStats)], ctypes.c_int),
+        "server_destroy": ([vp], None),
+        "server_lru_victims": ([vp, vp, vp, i32, u64, u64, u64, vp, ctypes.POINTER(i32)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -122,7 +152,9 @@ def exported_symbols():
             "template_release", "screen_bounds", "screen_features", "compact_mask", "compact_mask_noalloc",
             "compact_mask_noalloc_error", "screen_positions",
             "screen_positions_async", "screen_host", "screen_batch_create", "screen_batch_run",
-            "screen_batch_info", "screen_batch_release"]
+            "screen_batch_info", "screen_batch_release", "server_clock_ns", "server_create", "server_upload",
+            "server_screen", "server_evict", "server_forget", "server_wait", "server_hold", "server_resident",
+            "server_stats", "server_destroy", "server_lru_victims"]
 
 
 def _check(rc: int, allow=()):
@@ -334,6 +366,91 @@ def screen_batch_info(b) -> dict:
 
 def screen_batch_release(ctx, b) -> None:
     load().screen_batch_release(ctx, b)
+
+
+# ---- serving loop -------------------------------------------------------------
+
+def server_clock_ns() -> int:
+    return int(load().server_clock_ns())
+
+
+def server_create(ctx, table_budget_bytes: int = 0, sum_bits: int = 32, sq_bits: int = 64, mode: int = SERVE_BATCHED,
+                  max_batch: int = 0, start_held: bool = False, words_per_warp: int = 0, blocks_per_sm: int = 0):
+    cfg = _ServerConfig(table_budget_bytes, sum_bits, sq_bits, mode, max_batch, int(start_held), words_per_warp,
+                        blocks_per_sm, 0)
+    s = ctypes.c_void_p()
+    _check(load().server_create(ctx, ctypes.byref(cfg), ctypes.byref(s)))
+    return s
+
+
+def server_upload(s, img: np.ndarray, borrow: bool = False, arrival_ns: int = 0) -> tuple[int, int]:
+    """Queue an upload of a uint8 H x W array; returns (image_id, request_id).
+    With borrow the caller keeps img alive until the image is forgotten."""
+    assert img.dtype == np.uint8 and img.ndim == 2 and img.strides[1] == 1
+    iid, rid = ctypes.c_int64(), ctypes.c_uint64()
+    _check(load().server_upload(s, img.ctypes.data, img.shape[0], img.shape[1], img.strides[0], int(borrow),
+                                arrival_ns, ctypes.byref(iid), ctypes.byref(rid)))
+    return iid.value, rid.value
+
+
+def server_screen(s, image_id: int, tm, params: Params, lst: np.ndarray | None = None, arrival_ns: int = 0) -> int:
+    """Queue a screen; lst (uint64 host array or None) receives the first len(lst) keys."""
+    cap = 0 if lst is None else len(lst)
+    ptr = None if lst is None else lst.ctypes.data
+    if lst is not None:
+        assert lst.dtype == np.uint64 and lst.flags.c_contiguous
+    rid = ctypes.c_uint64()
+    _check(load().server_screen(s, image_id, tm, ctypes.byref(params.c), ptr, cap, arrival_ns, ctypes.byref(rid)))
+    return rid.value
+
+
+def server_evict(s, image_id: int) -> int:
+    rid = ctypes.c_uint64()
+    _check(load().server_evict(s, image_id, ctypes.byref(rid)))
+    return rid.value
+
+
+def server_forget(s, image_id: int) -> None:
+    _check(load().server_forget(s, image_id))
+
+
+def server_wait(s, request_id: int, timeout_us: int = 300_000_000) -> dict:
+    res = _RequestResult()
+    _check(load().server_wait(s, request_id, timeout_us, ctypes.byref(res)))
+    return {n: int(getattr(res, n)) for n, _ in _RequestResult._fields_}
+
+
+def server_hold(s, hold: bool) -> None:
+    _check(load().server_hold(s, int(hold)))
+
+
+def server_resident(s, image_id: int) -> bool:
+    r = ctypes.c_int32()
+    _check(load().server_resident(s, image_id, ctypes.byref(r)))
+    return bool(r.value)
+
+
+def server_stats(s) -> dict:
+    st = _ServerStats()
+    _check(load().server_stats(s, ctypes.byref(st)))
+    return {n: int(getattr(st, n)) for n, _ in _ServerStats._fields_}
+
+
+def server_destroy(s) -> None:
+    load().server_destroy(s)
+
+
+def server_lru_victims(nbytes, last_use, pinned, resident: int, budget: int, need: int) -> list[int]:
+    """The serving loop's eviction choice (pure host code); raises ScreenError(SCR_EBUDGET) when nothing fits."""
+    b = np.ascontiguousarray(nbytes, dtype=np.uint64)
+    lu = np.ascontiguousarray(last_use, dtype=np.uint64)
+    pn = np.ascontiguousarray(pinned, dtype=np.int32)
+    n = len(b)
+    out = np.zeros(max(n, 1), dtype=np.int32)
+    nv = ctypes.c_int32()
+    _check(load().server_lru_victims(b.ctypes.data, lu.ctypes.data, pn.ctypes.data, n, resident, budget, need,
+                                     out.ctypes.data, ctypes.byref(nv)))
+    return [int(v) for v in out[:nv.value]]
 
 
 __all__ = [n for n in dir() if not n.startswith("_")]

@@ -15,23 +15,17 @@
 #include <string>
 #include <vector>
 
-#include "batch.h"
-#include "internal.h"
-#include "screen.h"
-
-#include <chrono>
-#include <map>
+#include "runtime.h"
 
 using namespace scr;
-
-typedef __int128 i128;
+using namespace scr_rt;
 
 // ---------------------------------------------------------------------------
 // errors
 // ---------------------------------------------------------------------------
 static thread_local std::string g_last_error;
 
-static int fail(int code, const char *fmt, ...) {
+int scr_rt::fail(int code, const char *fmt, ...) {
     char buf[512];
     va_list ap;
     va_start(ap, fmt);
@@ -41,94 +35,9 @@ static int fail(int code, const char *fmt, ...) {
     return code;
 }
 
-#define CUDA_TRY(expr)                                                                     \
-    do {                                                                                   \
-        cudaError_t e__ = (expr);                                                          \
-        if (e__ != cudaSuccess)                                                            \
-            return fail(SCR_ECUDA, "%s: %s (%s)", #expr, cudaGetErrorName(e__),            \
-                        cudaGetErrorString(e__));                                          \
-    } while (0)
+const std::string &scr_rt::last_error() { return g_last_error; }
 
-// ---------------------------------------------------------------------------
-// context
-// ---------------------------------------------------------------------------
-struct scr_tables {
-    TableDesc t[4];
-    void *base = nullptr;
-    size_t bytes = 0;
-    int H = 0, W = 0;
-    cudaStream_t stream = nullptr;   // stream of the last use (frees are ordered on it)
-};
-
-struct scr_tmpl {
-    int r = 0, t_min = 0;
-    uint32_t features = 0;
-    std::vector<int64_t> S, Q, Si;   // index t - t_min
-    // hulls as exact rationals num/den (den > 0)
-    int64_t mu_lo_n = 0, mu_lo_d = 1, mu_hi_n = 0, mu_hi_d = 1;
-    int64_t v_lo_n = 0, v_lo_d = 1, v_hi_n = 0, v_hi_d = 1;
-    int64_t g_lo_n = 0, g_lo_d = 1, g_hi_n = 0, g_hi_d = 1;
-};
-
-struct scr_batch;
-
-struct scr_ctx {
-    int device = 0;
-    uint64_t budget = 0;
-    std::atomic<uint64_t> in_use{0}, peak{0}, launches{0};
-    cudaMemPool_t pool = nullptr;
-    std::mutex mu;
-    std::set<scr_tables *> tables;
-    std::set<scr_tmpl *> tmpls;
-    std::set<scr_batch *> batches;
-    std::map<std::string, std::pair<int, int>> tuned;   // batch shape -> (words per warp, blocks per SM)
-    uint64_t *pinned = nullptr;      // 8-byte pinned slot for counts
-};
-
-struct scr_batch {
-    scr_ctx *ctx = nullptr;
-    int n_images = 0, n_pairs = 0;
-    std::vector<scr::BImage> images;
-    std::vector<scr::BGroup> groups;
-    std::vector<scr::BRecord> records;
-    void *desc = nullptr;            // device copy of images, groups, records
-    size_t desc_bytes = 0;
-    void *sort_buf = nullptr;        // radix-sort histogram + ping-pong keys
-    size_t sort_bytes = 0;
-    scr::BatchArgs args = {};
-    scr::SortArgs sargs = {};
-    int sort_passes = 0;             // 8-bit radix passes over the packed keys
-    int wpw = 8, blocks_per_sm = 4, grid = 0;
-    int64_t n_units = 0;
-    uint64_t candidates = 0;         // (record, valid position) pairs screened per run
-    uint64_t *offsets = nullptr;
-    uint64_t *n_keys = nullptr;      // caller's total-survivor count
-    uint64_t *n_reserved = nullptr;  // device counters of reserved key slots and handed-out units (in sort_buf)
-    uint64_t union_words = 0;
-    cudaStream_t cap_stream = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-};
-
-namespace {
-
-void free_batch(scr_ctx *c, scr_batch *b);
-
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = true;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess)
-            prev = -1;
-        if (prev != dev)
-            ok = cudaSetDevice(dev) == cudaSuccess;
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev)
-            cudaSetDevice(prev);
-    }
-};
+namespace scr_rt {
 
 int dev_alloc(scr_ctx *c, size_t bytes, cudaStream_t st, void **p) {
     bytes = std::max<size_t>(bytes, 256);
@@ -159,21 +68,6 @@ void dev_free(scr_ctx *c, void *p, size_t bytes, cudaStream_t st) {
     c->in_use.fetch_sub(bytes);
 }
 
-// A device buffer charged to the context and returned on scope exit
-// (stream-ordered on the stream it was taken on).
-struct Scoped {
-    scr_ctx *c;
-    void *p = nullptr;
-    size_t bytes = 0;
-    cudaStream_t st;
-    Scoped(scr_ctx *c_, cudaStream_t st_) : c(c_), st(st_) {}
-    int take(size_t b) {
-        bytes = b;
-        return dev_alloc(c, b, st, &p);
-    }
-    ~Scoped() { dev_free(c, p, bytes, st); }
-};
-
 int check_ctx(const scr_ctx *c) {
     if (!c)
         return fail(SCR_EINVAL, "null context");
@@ -187,11 +81,6 @@ int64_t isqrt64(int64_t v) {
     while ((m + 1) * (m + 1) <= v) ++m;
     return m;
 }
-
-struct Geo {
-    int n, h, ni, hi;
-    int64_t A, Ain, Aring;
-};
 
 Geo geometry(int R) {
     Geo g;
@@ -292,19 +181,26 @@ void bounds_for(const scr_tmpl *tm, const scr_params *p, int R, scr_bounds *b) {
     }
 }
 
+// words of one u32 plane of a table: (H + 1) rows at the padded pitch, 256-byte multiple
+int64_t table_plane_words(int H, int W) {
+    const int64_t rows = (int64_t)H + 1;
+    return ((rows * table_pitch_words(W) + 63) / 64) * 64;
+}
+
+size_t tables_bytes(int H, int W, int sum_bits, int sq_bits) {
+    return (size_t)table_plane_words(H, W) * 4 * (size_t)(2 * (sum_bits / 32) + 2 * (sq_bits / 32));
+}
+
 int alloc_tables(scr_ctx *c, int H, int W, int sum_bits, int sq_bits, cudaStream_t st, scr_tables **out) {
     auto *t = new (std::nothrow) scr_tables();
     if (!t)
         return fail(SCR_ENOMEM, "host allocation failed");
     const int64_t pitch = table_pitch_words(W);
     const int64_t rows = (int64_t)H + 1;
-    const int64_t plane = ((rows * pitch + 63) / 64) * 64;   // words, 256-byte multiple
+    const int64_t plane = table_plane_words(H, W);
     const int bits[4] = {sum_bits, sq_bits, sum_bits, sq_bits};
     const int64_t cols[4] = {(int64_t)W + 1, (int64_t)W + 1, (int64_t)W + 2, (int64_t)W + 2};
-    int64_t words = 0;
-    for (int k = 0; k < 4; ++k)
-        words += plane * (bits[k] / 32);
-    t->bytes = (size_t)words * 4;
+    t->bytes = tables_bytes(H, W, sum_bits, sq_bits);
     int rc = dev_alloc(c, t->bytes, st, &t->base);
     if (rc) {
         delete t;
@@ -427,7 +323,7 @@ int check_screen_inputs(const scr_tables *t, const scr_tmpl *tm, const scr_param
     return SCR_OK;
 }
 
-}  // namespace
+}  // namespace scr_rt
 
 int scr::square_half(int R) {
     const int64_t m = isqrt64(2 * (int64_t)R * R);
@@ -489,6 +385,7 @@ void screen_shutdown(scr_ctx *c) {
     if (!c)
         return;
     DeviceGuard dg(c->device);
+    destroy_servers(c);
     cudaDeviceSynchronize();
     {
         std::lock_guard<std::mutex> lk(c->mu);
@@ -847,7 +744,7 @@ int screen_host(scr_ctx *c, const uint8_t *img_host, int32_t H, int32_t W, int64
 // ---------------------------------------------------------------------------
 }  // extern "C"
 
-namespace {
+namespace scr_rt {
 
 // Lay the units out row by row: for each image and row, one unit per group of
 // the image (groups whose valid rows exclude the row leave that unit empty).
@@ -1075,43 +972,11 @@ void free_batch(scr_ctx *c, scr_batch *b) {
     delete b;
 }
 
-}  // namespace
-
-extern "C" {
-
-int screen_batch_create(scr_ctx *c, const scr_tables *const *tables, int32_t n_images, const scr_tmpl *const *tmpls,
-                        const scr_params *params, int32_t n_tmpls, const scr_pair *pairs, int32_t n_pairs,
-                        uint64_t *counts_dev, uint64_t *offsets_dev, uint32_t *union_mask_dev, uint64_t *keys_dev,
-                        uint64_t keys_cap, uint64_t *n_keys_dev, const scr_batch_tuning *tuning, scr_stream stream,
-                        scr_batch **out) {
+int batch_prepare(scr_ctx *c, const scr_tables *const *tables, int n_images, const scr_tmpl *const *tmpls,
+                  const scr_params *params, int n_tmpls, const scr_pair *pairs, int n_pairs, uint64_t *counts_dev,
+                  uint64_t *offsets_dev, uint32_t *union_mask_dev, uint64_t *keys_dev, uint64_t keys_cap,
+                  uint64_t *n_keys_dev, cudaStream_t st, scr_batch **out) {
     int rc;
-    if ((rc = check_ctx(c)))
-        return rc;
-    if (!out || !tables || !tmpls || !params || !pairs || n_images < 1 || n_tmpls < 1 || n_pairs < 1)
-        return fail(SCR_EINVAL, "null or empty batch description");
-    if (n_pairs >= (1 << 26))
-        return fail(SCR_EINVAL, "at most 2^26 pairs");
-    if (!counts_dev || !n_keys_dev || (keys_cap && !keys_dev))
-        return fail(SCR_EINVAL, "null counts, key count or keys");
-    for (int i = 0; i < n_images; ++i) {
-        if (!tables[i])
-            return fail(SCR_EINVAL, "null tables for image %d", i);
-        if (tables[i]->H > 65535 || tables[i]->W > 65535)
-            return fail(SCR_EINVAL, "image %d too large for 16-bit key fields", i);
-    }
-    for (int t = 0; t < n_tmpls; ++t) {
-        if ((rc = check_screen_inputs(tables[0], tmpls[t], &params[t])))
-            return fail(rc, "template %d: %s", t, g_last_error.c_str());
-        if (params[t].n_scales > 32)
-            return fail(SCR_EINVAL, "template %d: more than 32 scales", t);
-    }
-    for (int p = 0; p < n_pairs; ++p)
-        if (pairs[p].image < 0 || pairs[p].image >= n_images || pairs[p].tmpl < 0 || pairs[p].tmpl >= n_tmpls)
-            return fail(SCR_EINVAL, "pair %d out of range", p);
-    *out = nullptr;
-    DeviceGuard dg(c->device);
-    std::lock_guard<std::mutex> lk(c->mu);
-    cudaStream_t st = (cudaStream_t)stream;
     auto *b = new (std::nothrow) scr_batch();
     if (!b)
         return fail(SCR_ENOMEM, "host allocation failed");
@@ -1169,6 +1034,59 @@ int screen_batch_create(scr_ctx *c, const scr_tables *const *tables, int32_t n_i
     b->sargs.n_keys = b->n_reserved;
     b->sargs.cap = keys_cap;
     b->sargs.max_tiles = tiles;
+    *out = b;
+    return SCR_OK;
+}
+
+void batch_set_shape(scr_batch *b, int wpw, int blocks_per_sm) {
+    b->wpw = wpw;
+    b->blocks_per_sm = blocks_per_sm;
+    b->grid = sm_count(b->ctx->device) * blocks_per_sm;
+    plan_layout(b);
+    set_args(b);
+}
+
+}  // namespace scr_rt
+
+extern "C" {
+
+int screen_batch_create(scr_ctx *c, const scr_tables *const *tables, int32_t n_images, const scr_tmpl *const *tmpls,
+                        const scr_params *params, int32_t n_tmpls, const scr_pair *pairs, int32_t n_pairs,
+                        uint64_t *counts_dev, uint64_t *offsets_dev, uint32_t *union_mask_dev, uint64_t *keys_dev,
+                        uint64_t keys_cap, uint64_t *n_keys_dev, const scr_batch_tuning *tuning, scr_stream stream,
+                        scr_batch **out) {
+    int rc;
+    if ((rc = check_ctx(c)))
+        return rc;
+    if (!out || !tables || !tmpls || !params || !pairs || n_images < 1 || n_tmpls < 1 || n_pairs < 1)
+        return fail(SCR_EINVAL, "null or empty batch description");
+    if (n_pairs >= (1 << 26))
+        return fail(SCR_EINVAL, "at most 2^26 pairs");
+    if (!counts_dev || !n_keys_dev || (keys_cap && !keys_dev))
+        return fail(SCR_EINVAL, "null counts, key count or keys");
+    for (int i = 0; i < n_images; ++i) {
+        if (!tables[i])
+            return fail(SCR_EINVAL, "null tables for image %d", i);
+        if (tables[i]->H > 65535 || tables[i]->W > 65535)
+            return fail(SCR_EINVAL, "image %d too large for 16-bit key fields", i);
+    }
+    for (int t = 0; t < n_tmpls; ++t) {
+        if ((rc = check_screen_inputs(tables[0], tmpls[t], &params[t])))
+            return fail(rc, "template %d: %s", t, g_last_error.c_str());
+        if (params[t].n_scales > 32)
+            return fail(SCR_EINVAL, "template %d: more than 32 scales", t);
+    }
+    for (int p = 0; p < n_pairs; ++p)
+        if (pairs[p].image < 0 || pairs[p].image >= n_images || pairs[p].tmpl < 0 || pairs[p].tmpl >= n_tmpls)
+            return fail(SCR_EINVAL, "pair %d out of range", p);
+    *out = nullptr;
+    DeviceGuard dg(c->device);
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    scr_batch *b = nullptr;
+    if ((rc = batch_prepare(c, tables, n_images, tmpls, params, n_tmpls, pairs, n_pairs, counts_dev, offsets_dev,
+                            union_mask_dev, keys_dev, keys_cap, n_keys_dev, st, &b)))
+        return rc;
     const int sms = sm_count(c->device);
     // tuning: given, cached for this batch shape, or measured now
     char key[160];

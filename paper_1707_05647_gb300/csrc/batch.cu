@@ -519,7 +519,25 @@ __global__ void __launch_bounds__(1024) k_pair_offsets(const uint64_t *counts, u
     }
 }
 
+// Batched keys (pair << 37 | s << 32 | y << 16 | x) to the single-image key
+// format of compact_mask, in place; the pair's keys are contiguous after the sort.
+__global__ void __launch_bounds__(256) k_keys_to_lists(uint64_t *keys, const uint64_t *n, uint64_t cap) {
+    pdl_begin();
+    const uint64_t m = *n < cap ? *n : cap;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = keys[i];
+        keys[i] = (((k >> 32) & 31u) << 48) | (((k >> 16) & 0xFFFFu) << 24) | (k & 0xFFFFu);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_keys_to_lists(uint64_t *keys, const uint64_t *n, uint64_t cap, int grid, cudaStream_t st,
+                                 uint64_t *launches) {
+    if (launches)
+        *launches += 1;
+    return launch_pdl(k_keys_to_lists, dim3(grid), dim3(256), st, keys, n, cap);
+}
 
 cudaError_t launch_batch(const BatchArgs &a, int words_per_warp, int grid, cudaStream_t st, uint64_t *launches) {
     const dim3 block(32 * kBatchWarps);

@@ -77,6 +77,9 @@ uint64_t sort_max_tiles(uint64_t cap);
 constexpr int kSortLaunchesPerPass = 5;
 // passes 8-bit passes; the result is in a.src after an even number, a.dst after an odd one
 cudaError_t launch_sort(const SortArgs &a, int passes, int grid, cudaStream_t st, uint64_t *launches);
+// keys[i] = the single-image key (s << 48) | (y << 24) | x of batched key i, for i < min(*n, cap)
+cudaError_t launch_keys_to_lists(uint64_t *keys, const uint64_t *n, uint64_t cap, int grid, cudaStream_t st,
+                                 uint64_t *launches);
 cudaError_t launch_pair_offsets(const uint64_t *counts, uint64_t *offsets, uint64_t *total, const uint64_t *reserved,
                                 int n, cudaStream_t st, uint64_t *launches);
 
