@@ -413,6 +413,141 @@ def run_batched(args):
     scr.screen_shutdown(ctx)
 
 
+def run_serve(args):
+    """Configuration 5: replay one seeded Poisson stream of uploads and screens
+    through the serving loop, batched (continuous batching) and plain (one
+    launch pair per screen), each on a fresh server warmed to the same resident
+    set; latency = done - scheduled arrival, so a late submission counts."""
+    import queue
+    import threading
+    import torch
+    import synth
+    import paper_1707_05647_gb300 as scr
+
+    torch.cuda.set_device(0)
+    w = synth.serve_workload(duration=args.duration)
+    ctx = scr.screen_init(0, 0)
+    tmpls = [scr.template_features(ctx, ts.template, ts.r, max(ts.t_min, 2), 7) for ts in w.templates]
+    params = {}
+    for ev in w.events:
+        if ev.kind == "screen" and (ev.template, ev.features) not in params:
+            ts = w.templates[ev.template]
+            params[(ev.template, ev.features)] = scr.Params(ts.radii, ev.features, w.tol.mean_rel, w.tol.std_rel,
+                                                             w.tol.grad_rel, w.tol.grad_abs)
+    cap = 1 << 18
+    n_bufs = 256
+
+    def candidates(img_shape, radii):
+        H, W = img_shape
+        tot = 0
+        for R in radii:
+            n = scr_square_half(R)
+            m = max(n, R)
+            rows = (H - 1 - m) - (m - 1) + 1
+            cols = min(W - 1 - n, W - R) - (m - 1) + 1
+            tot += max(rows, 0) * max(cols, 0)
+        return tot
+
+    def replay(mode):
+        s = scr.server_create(ctx, table_budget_bytes=w.table_budget, sum_bits=w.sum_bits, sq_bits=w.sq_bits,
+                              mode=mode)
+        uploads = []   # image id per upload, in order
+        pending = []
+        for k in w.warm:
+            iid, rid = scr.server_upload(s, w.pool[k], borrow=True)
+            uploads.append((iid, w.pool[k].shape))
+            pending.append(rid)
+        for rid in pending:
+            r = scr.server_wait(s, rid)
+            assert r["status"] == scr.SCR_OK, r
+        warm_stats = scr.server_stats(s)
+        bufs = queue.Queue()
+        for _ in range(n_bufs):
+            bufs.put(np.zeros(cap, np.uint64))
+        todo = queue.Queue()
+        results = {}
+
+        def collect():
+            while True:
+                item = todo.get()
+                if item is None:
+                    return
+                k, rid, buf = item
+                results[k] = scr.server_wait(s, rid, 600_000_000)
+                if buf is not None:
+                    bufs.put(buf)
+
+        th = threading.Thread(target=collect)
+        th.start()
+        t0 = scr.server_clock_ns() + 50_000_000
+        cand = {}
+        for k, ev in enumerate(w.events):
+            due = t0 + int(ev.t * 1e9)
+            while True:
+                now = scr.server_clock_ns()
+                if now >= due:
+                    break
+                if due - now > 300_000:
+                    time.sleep((due - now - 200_000) / 1e9)
+            if ev.kind == "upload":
+                iid, rid = scr.server_upload(s, w.pool[ev.image], borrow=True, arrival_ns=due)
+                uploads.append((iid, w.pool[ev.image].shape))
+                todo.put((k, rid, None))
+            else:
+                iid, shape = uploads[ev.image]
+                buf = bufs.get()
+                rid = scr.server_screen(s, iid, tmpls[ev.template], params[(ev.template, ev.features)], buf,
+                                        arrival_ns=due)
+                cand[k] = candidates(shape, w.templates[ev.template].radii)
+                todo.put((k, rid, buf))
+        todo.put(None)
+        th.join()
+        st = scr.server_stats(s)
+        scr.server_destroy(s)
+        scr_lat = np.array([(results[k]["done_ns"] - results[k]["arrival_ns"]) / 1e6 for k in cand])
+        up_lat = np.array([(results[k]["done_ns"] - results[k]["arrival_ns"]) / 1e6
+                           for k, ev in enumerate(w.events) if ev.kind == "upload"])
+        bad = sum(1 for r in results.values() if r["status"] not in (scr.SCR_OK, scr.SCR_EOVERFLOW))
+        end = max(r["done_ns"] for r in results.values())
+        span = (end - t0) / 1e9
+        counts = {k: results[k]["count"] for k in cand}
+        sizes = np.array([r["batch_size"] for r in results.values()])
+        return {
+            "screen_latency_ms": {"p50": float(np.percentile(scr_lat, 50)), "p99": float(np.percentile(scr_lat, 99)),
+                                  "mean": float(scr_lat.mean()), "max": float(scr_lat.max())},
+            "upload_latency_ms": {"p50": float(np.percentile(up_lat, 50)), "p99": float(np.percentile(up_lat, 99))},
+            "evals_per_s": sum(cand.values()) / span, "requests_per_s": len(w.events) / span,
+            "span_s": span, "errors": bad,
+            "overflowed_lists": sum(1 for k in cand if results[k]["status"] == scr.SCR_EOVERFLOW),
+            "batches": st["batches"] - warm_stats["batches"], "mean_batch_size": float(sizes.mean()),
+            "evictions": st["evictions"], "rebuilds": st["rebuilds"], "builds": st["builds"],
+            "peak_resident_gb": st["peak_resident_bytes"] / 1e9, "launches": st["launches"] - warm_stats["launches"],
+        }, counts
+
+    batched, cb = replay(scr.SERVE_BATCHED)
+    plain, cp = replay(scr.SERVE_PLAIN)
+    n_screens = sum(1 for e in w.events if e.kind == "screen")
+    print(json.dumps({
+        "metric": "served screen latency p50/p99 (ms) and evaluations/s", "workload":
+            f"serving: Poisson {w.rate:.0f} req/s for {w.duration:g} s ({len(w.events)} requests, "
+            f"{len(w.events) - n_screens} uploads of side 256..8192 log-uniform, {n_screens} screens r 8..96, "
+            f"1..16 scales, 2-3 features), {w.table_budget >> 30} GiB table budget, LRU eviction, "
+            f"{len(w.warm)} warm uploads",
+        "batched": batched, "plain": plain,
+        "p99_speedup_vs_plain": plain["screen_latency_ms"]["p99"] / batched["screen_latency_ms"]["p99"],
+        "p50_speedup_vs_plain": plain["screen_latency_ms"]["p50"] / batched["screen_latency_ms"]["p50"],
+        "counts_identical": cb == cp, "list_cap": cap, "data": "synthetic"}), flush=True)
+    for t in tmpls:
+        scr.template_release(ctx, t)
+    scr.screen_shutdown(ctx)
+
+
+def scr_square_half(R: int) -> int:
+    """n with (2n-1)^2 < 2R^2 < (2n+1)^2, for counting valid positions in reports."""
+    m = math.isqrt(2 * R * R)
+    return (m + 1) // 2
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -423,10 +558,14 @@ def main():
     ap.add_argument("--size", type=int, default=4096,
                     help="crop the 4096x4096 image to size x size (smaller ncu captures)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "batched"])
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "serve"])
+    ap.add_argument("--duration", type=float, default=2.0, help="seconds of arrivals (serve workload)")
     ap.add_argument("--images", type=int, default=64)
     ap.add_argument("--templates", type=int, default=256)
     args = ap.parse_args()
+    if args.workload == "serve":
+        run_serve(args)
+        return
     if args.workload == "batched":
         run_batched(args)
         return

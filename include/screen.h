@@ -299,21 +299,24 @@ void screen_batch_release(scr_ctx *ctx, scr_batch *b);
 
 /* ---- serving loop ---------------------------------------------------------
  *
- * A server owns one worker thread and one stream on the context's device.
+ * A server owns two threads, each with its own stream on the context's device.
  * Clients upload images (the server keeps a host copy, or borrows the caller's)
  * and submit screen requests from any thread; both return at once with a
- * request id.  Whenever the worker is free it takes every queued request
- * (continuous batching, at most max_batch), makes the images they need resident
- * (building their tables, or rebuilding tables evicted earlier from the host
- * copy; least recently used unpinned tables are evicted while the resident
- * tables would exceed table_budget_bytes), then screens all queued screen
- * requests of the batch in one batched run (SCR_SERVE_BATCHED: records grouped
- * per (image, star radius) as in screen_batch_create) or one plain
- * screen_features + compact_mask each (SCR_SERVE_PLAIN), and writes each
- * request's survivor list, in compact_mask's key format and order, to the
- * caller's host buffer.  A request's result does not depend on which other
- * requests share its batch, nor on the mode.  This is the paper's screen
- * (Sec. 5, Algorithm 1) served to many clients; the paper has no serving loop. */
+ * request id.  The builder thread builds the tables of uploaded images, and
+ * rebuilds from the host copy the tables of images evicted earlier: it admits
+ * new tables by the table budget, evicting least recently used tables that no
+ * queued or running screen holds, and waits for running screens to release
+ * tables when the rest does not make room.  The screener thread, whenever it is
+ * free, takes every screen whose tables are resident (continuous batching, at
+ * most max_batch) and screens them in one batched run (SCR_SERVE_BATCHED:
+ * records grouped per (image, star radius) as in screen_batch_create) or one
+ * plain screen_features + compact_mask each (SCR_SERVE_PLAIN), while the
+ * builder's copies and table builds overlap on the device; screens whose tables
+ * are being built join a later batch.  Each request's survivor list, in
+ * compact_mask's key format and order, goes to the caller's host buffer.  A
+ * request's result does not depend on which other requests share its batch, nor
+ * on the mode.  This is the paper's screen (Sec. 5, Algorithm 1) served to many
+ * clients; the paper has no serving loop. */
 typedef struct scr_server scr_server;
 
 enum { SCR_SERVE_BATCHED = 0, SCR_SERVE_PLAIN = 1 };
@@ -346,14 +349,16 @@ typedef struct {
     uint64_t builds, rebuilds, evictions;
     uint64_t resident_images, resident_bytes, peak_resident_bytes;
     uint64_t keys_capacity;      /* device key slots the batched path holds */
-    uint64_t launches;           /* kernels the worker launched */
+    uint64_t launches;           /* kernels the server launched */
+    uint64_t build_ns;           /* time the builder spent on uploads, rebuilds and evictions */
+    uint64_t screen_ns;          /* time the screener spent running batches */
 } scr_server_stats;
 
 /* CLOCK_MONOTONIC in nanoseconds: the clock of arrival, start and done stamps. */
 int64_t server_clock_ns(void);
 
-/* Create a server on ctx (the context must outlive it; screen_shutdown destroys
- * servers still open).  Synchronous. */
+/* Create a server on ctx (screen_shutdown destroys servers still open).  An
+ * image whose tables alone exceed table_budget_bytes fails with SCR_EBUDGET. */
 int server_create(scr_ctx *ctx, const scr_server_config *cfg, scr_server **out);
 
 /* Queue an upload: H x W uint8 at img_host (pitch bytes per row).  borrow = 0
@@ -384,8 +389,8 @@ int server_forget(scr_server *s, int64_t image_id);
  * unknown or already collected id. */
 int server_wait(scr_server *s, uint64_t request_id, int64_t timeout_us, scr_request_result *out);
 
-/* hold = 1: the worker takes no new batch (the one running completes);
- * hold = 0: serving resumes. */
+/* hold = 1: the screener takes no new batch (the one running completes; the
+ * builder keeps building); hold = 0: screening resumes. */
 int server_hold(scr_server *s, int32_t hold);
 
 /* *resident = 1 when the image's tables are on the device now. */

@@ -59,6 +59,25 @@ __device__ __forceinline__ void corner_sums64(const uint32_t *L, const uint32_t 
     }
 }
 
+// The eight corner pointers of the star sum (square on L, diamond on T) of one
+// warp-chunk; word j reads at the immediate offset 32 * j.
+struct StarCorners {
+    const uint32_t *p[8];
+    __device__ __forceinline__ StarCorners(const uint32_t *L, const uint32_t *T, const int32_t (&oL)[4],
+                                           const int32_t (&oT)[4]) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            p[k] = L + oL[k];
+            p[4 + k] = T + oT[k];
+        }
+    }
+    __device__ __forceinline__ uint32_t sum(int j) const {
+        const int d = 32 * j;
+        return ldb(p[0] + d) - ldb(p[1] + d) - ldb(p[2] + d) + ldb(p[3] + d) + ldb(p[4] + d) - ldb(p[5] + d) -
+               ldb(p[6] + d) + ldb(p[7] + d);
+    }
+};
+
 constexpr int kBatchWarps = 8;
 
 template <int WPW>
@@ -101,33 +120,57 @@ __global__ void __launch_bounds__(32 * kBatchWarps) k_batch(const BatchArgs a) {
             while (img + 1 < a.n_images && __ldg(&a.images[img + 1].unit0) <= u)
                 ++img;
         }
-        const BImage &im = a.images[img];
-        const uint32_t local = (uint32_t)(u - im.unit0);   // < rows * n_grp
-        const int y = im.y_first + (int)(local / (uint32_t)im.n_grp);
-        const BGroup &gr = a.groups[im.g0 + (int)(local % (uint32_t)im.n_grp)];
-        if (y < gr.y_lo || y > gr.y_hi)
+        const BImage *ip = a.images + img;
+        const int n_grp = __ldg(&ip->n_grp);
+        const uint32_t local = (uint32_t)(u - __ldg(&ip->unit0));   // < rows * n_grp
+        const int y = __ldg(&ip->y_first) + (int)(local / (uint32_t)n_grp);
+        const BGroup *gp = a.groups + __ldg(&ip->g0) + (int)(local % (uint32_t)n_grp);
+        if (y < __ldg(&gp->y_lo) || y > __ldg(&gp->y_hi))
             continue;
-        // the warp walks the row's mask words WPW at a time
-        for (int w0 = gr.w_lo; w0 <= gr.w_hi; w0 += WPW) {
-            const int x0 = w0 * 32 + lane;
-            uint32_t live = 0;
+        // the unit's constants, in registers for the walk along the row
+        const int x_lo = __ldg(&gp->x_lo), x_hi = __ldg(&gp->x_hi);
+        const int w_lo = __ldg(&gp->w_lo), w_hi = __ldg(&gp->w_hi);
+        const uint32_t h_lo = __ldg(&gp->S_lo_hull), h_rng = __ldg(&gp->S_rng_hull);
+        const int rec0 = __ldg(&gp->rec0), rec1 = __ldg(&gp->rec1);
+        const int64_t pitch = __ldg(&ip->pitch);
+        const uint32_t *L1 = (const uint32_t *)__ldg((const unsigned long long *)&ip->L1);
+        const uint32_t *T1 = (const uint32_t *)__ldg((const unsigned long long *)&ip->T1);
+        const int64_t row = (int64_t)y * pitch + kColOffset + lane;   // this lane's element at x = lane
+        int32_t oL[4], oT[4];
 #pragma unroll
-            for (int j = 0; j < WPW; ++j) {
-                const int x = x0 + 32 * j;
-                if (x >= gr.x_lo && x <= gr.x_hi)
-                    live |= 1u << j;
+        for (int k = 0; k < 4; ++k) {
+            oL[k] = __ldg(&gp->oL[k]);
+            oT[k] = __ldg(&gp->oT[k]);
+        }
+        // the warp walks the row's mask words WPW at a time
+        for (int w0 = w_lo; w0 <= w_hi; w0 += WPW) {
+            const int xs = w0 * 32;   // the warp covers x in [xs, xs + 32 * WPW)
+            const int x0 = xs + lane;
+            const int64_t e = row + xs;
+            const StarCorners c(L1 + e, T1 + e, oL, oT);
+            uint32_t S[WPW], live = 0;
+            if (xs >= x_lo && xs + 32 * WPW - 1 <= x_hi) {   // warp-uniform: every position valid
+#pragma unroll
+                for (int j = 0; j < WPW; ++j)
+                    S[j] = c.sum(j);
+                live = (1u << WPW) - 1;
+            } else {
+                const uint32_t span = (uint32_t)(x_hi - x_lo);
+#pragma unroll
+                for (int j = 0; j < WPW; ++j) {
+                    S[j] = 0;
+                    if ((uint32_t)(x0 + 32 * j - x_lo) <= span) {
+                        S[j] = c.sum(j);
+                        live |= 1u << j;
+                    }
+                }
             }
-            if (!__any_sync(0xffffffffu, live))
-                continue;
-            const int64_t e = (int64_t)y * im.pitch + x0 + kColOffset;
-            uint32_t S[WPW];
-            corner_sums<WPW>(im.L1 + e, im.T1 + e, gr.oL, gr.oT, live, S);
             // fast reject against the hull of every record's mean interval
             uint32_t alive = 0;
 #pragma unroll
             for (int j = 0; j < WPW; ++j)
-                if (((live >> j) & 1u) && (S[j] - gr.S_lo_hull) <= gr.S_rng_hull)
-                    alive |= 1u << j;
+                alive |= ((S[j] - h_lo) <= h_rng ? 1u : 0u) << j;
+            alive &= live;
             if (!__any_sync(0xffffffffu, alive))
                 continue;
             // V and N are shared by every record of the group and computed on first
@@ -141,60 +184,79 @@ __global__ void __launch_bounds__(32 * kBatchWarps) k_batch(const BatchArgs a) {
             // the warp's range of means among alive positions: records are sorted
             // by interval start (records without a mean test start at 0 and span
             // everything), so the walk skips disjoint intervals and stops early
-            uint32_t smin = UINT32_MAX, smax = 0;
+            uint32_t smin = 0, smax = UINT32_MAX;
+            if (rec1 - rec0 > 1) {
+                smin = UINT32_MAX;
+                smax = 0;
 #pragma unroll
-            for (int j = 0; j < WPW; ++j)
-                if ((alive >> j) & 1u) {
-                    smin = min(smin, S[j]);
-                    smax = max(smax, S[j]);
-                }
-            smin = __reduce_min_sync(0xffffffffu, smin);
-            smax = __reduce_max_sync(0xffffffffu, smax);
-            for (int r = gr.rec0; r < gr.rec1; ++r) {
-                const BRecord &rc = a.records[r];
-                const uint32_t slo = __ldg(&rc.S_lo);
+                for (int j = 0; j < WPW; ++j)
+                    if ((alive >> j) & 1u) {
+                        smin = min(smin, S[j]);
+                        smax = max(smax, S[j]);
+                    }
+                smin = __reduce_min_sync(0xffffffffu, smin);
+                smax = __reduce_max_sync(0xffffffffu, smax);
+            }
+            for (int r = rec0; r < rec1; ++r) {
+                const BRecord *rc = a.records + r;
+                const uint32_t slo = __ldg(&rc->S_lo), srng = __ldg(&rc->S_rng);
                 if (slo > smax)
                     break;
-                if (slo + __ldg(&rc.S_rng) < smin)
+                if (slo + srng < smin)
                     continue;
+                const uint32_t feats = __ldg(&rc->features);
                 uint32_t keep = alive;
-                if (rc.features & SCR_F_MEAN) {
+                if (feats & SCR_F_MEAN) {
 #pragma unroll
                     for (int j = 0; j < WPW; ++j)
-                        if ((S[j] - rc.S_lo) > rc.S_rng)
+                        if ((S[j] - slo) > srng)
                             keep &= ~(1u << j);
                 }
-                if (rc.features & SCR_F_VAR) {
+                if (feats & SCR_F_VAR) {
                     if (!haveV && __any_sync(0xffffffffu, keep)) {
+                        const uint32_t *L2 = (const uint32_t *)__ldg((const unsigned long long *)&ip->L2);
+                        const uint32_t *T2 = (const uint32_t *)__ldg((const unsigned long long *)&ip->T2);
                         uint64_t Q[WPW];
-                        corner_sums64<WPW>(im.L2 + e, im.T2 + e, gr.oL, gr.oT, alive, Q);
+                        corner_sums64<WPW>(L2 + e, T2 + e, oL, oT, alive, Q);
+                        const uint64_t A = __ldg(&gp->A);
 #pragma unroll
                         for (int j = 0; j < WPW; ++j)
-                            V[j] = (uint64_t)gr.A * Q[j] - (uint64_t)S[j] * S[j];
+                            V[j] = A * Q[j] - (uint64_t)S[j] * S[j];
                         haveV = true;
                     }
+                    const uint64_t vlo = (uint64_t)__ldg(&rc->V_lo), vrng = __ldg(&rc->V_rng);
 #pragma unroll
                     for (int j = 0; j < WPW; ++j)
-                        if ((V[j] - (uint64_t)rc.V_lo) > rc.V_rng)
+                        if ((V[j] - vlo) > vrng)
                             keep &= ~(1u << j);
                 }
-                if (rc.features & SCR_F_GRAD) {
+                if (feats & SCR_F_GRAD) {
                     if (!haveN && __any_sync(0xffffffffu, keep)) {
+                        int32_t oLi[4], oTi[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            oLi[k] = __ldg(&gp->oLi[k]);
+                            oTi[k] = __ldg(&gp->oTi[k]);
+                        }
                         uint32_t Si[WPW];
-                        corner_sums<WPW>(im.L1 + e, im.T1 + e, gr.oLi, gr.oTi, alive, Si);
+                        corner_sums<WPW>(L1 + e, T1 + e, oLi, oTi, alive, Si);
+                        const uint64_t Ain = __ldg(&gp->Ain), Aring = __ldg(&gp->Aring);
 #pragma unroll
                         for (int j = 0; j < WPW; ++j)
-                            N[j] = (uint64_t)((int64_t)((uint64_t)Si[j] * gr.Aring) -
-                                              (int64_t)((uint64_t)(S[j] - Si[j]) * gr.Ain));
+                            N[j] = (uint64_t)((int64_t)((uint64_t)Si[j] * Aring) -
+                                              (int64_t)((uint64_t)(S[j] - Si[j]) * Ain));
                         haveN = true;
                     }
+                    const uint64_t nlo = (uint64_t)__ldg(&rc->N_lo), nrng = __ldg(&rc->N_rng);
 #pragma unroll
                     for (int j = 0; j < WPW; ++j)
-                        if ((N[j] - (uint64_t)rc.N_lo) > rc.N_rng)
+                        if ((N[j] - nlo) > nrng)
                             keep &= ~(1u << j);
                 }
                 if (!__any_sync(0xffffffffu, keep))
                     continue;
+                const uint64_t key_hi = ((uint64_t)__ldg(&rc->pair) << 37) | ((uint64_t)__ldg(&rc->s) << 32) |
+                                        ((uint64_t)y << 16);
                 uint32_t nrec = 0;   // survivors of this record in the warp's words
 #pragma unroll
                 for (int j = 0; j < WPW; ++j) {
@@ -203,9 +265,9 @@ __global__ void __launch_bounds__(32 * kBatchWarps) k_batch(const BatchArgs a) {
                     if (!bits)
                         continue;
                     ubits[j] |= bits;
-                    const uint32_t c = __popc(bits);
-                    nrec += c;
-                    if (cpos + c > cend) {   // new chunk of key slots
+                    const uint32_t cnt = __popc(bits);
+                    nrec += cnt;
+                    if (cpos + cnt > cend) {   // new chunk of key slots
                         fill_rest();
                         uint64_t base = 0;
                         if (lane == 0)
@@ -216,13 +278,12 @@ __global__ void __launch_bounds__(32 * kBatchWarps) k_batch(const BatchArgs a) {
                     if (kj) {
                         const uint64_t pos = cpos + __popc(bits & lt_mask);
                         if (pos < a.keys_cap)
-                            a.keys[pos] = ((uint64_t)rc.pair << 37) | ((uint64_t)rc.s << 32) |
-                                          ((uint64_t)y << 16) | (uint64_t)(x0 + 32 * j);
+                            a.keys[pos] = key_hi | (uint64_t)(x0 + 32 * j);
                     }
-                    cpos += c;
+                    cpos += cnt;
                 }
                 if (lane == 0 && nrec)
-                    atomicAdd((unsigned long long *)&a.counts[rc.pair], (unsigned long long)nrec);
+                    atomicAdd((unsigned long long *)&a.counts[__ldg(&rc->pair)], (unsigned long long)nrec);
             }
             if (a.union_mask && lane < WPW) {   // one OR per word of the unit: lane j writes word j
                 uint32_t mine = 0;
@@ -230,7 +291,8 @@ __global__ void __launch_bounds__(32 * kBatchWarps) k_batch(const BatchArgs a) {
                 for (int j = 0; j < WPW; ++j)
                     mine = lane == j ? ubits[j] : mine;
                 if (mine)
-                    atomicOr(a.union_mask + im.mask_offset + (int64_t)y * im.Wwords + w0 + lane, mine);
+                    atomicOr(a.union_mask + __ldg(&ip->mask_offset) + (int64_t)y * __ldg(&ip->Wwords) + w0 + lane,
+                             mine);
             }
         }
     }

@@ -1,9 +1,13 @@
-// Serving loop of include/screen.h: one worker thread per server takes every
-// queued request whenever it is free (continuous batching), keeps the tables of
-// the images it needs resident under a table budget (least recently used
-// unpinned tables are evicted; evicted tables are rebuilt from the host copy),
-// screens the batch's screen requests in one batched run or one plain launch
-// pair each, and writes each request's list in compact_mask's format.
+// Serving loop of include/screen.h.  Two threads per server:
+//  - the builder builds the tables of uploaded images and rebuilds evicted ones
+//    from their host copy (on its own stream), admitting new tables by the
+//    table budget: it evicts least recently used tables that no ready or running
+//    screen pins, and waits for pins to be released when that is not enough;
+//  - the screener takes every screen whose tables are resident whenever it is
+//    free (continuous batching) and runs them as one batched launch or as one
+//    plain launch pair each, then hands each request its list in the
+//    single-image key format.
+// Copies and table builds of the builder overlap with the screener's kernels.
 #include <condition_variable>
 #include <deque>
 #include <thread>
@@ -26,19 +30,23 @@ int64_t now_ns() {
 
 enum { kUpload = 0, kScreen = 1, kEvict = 2 };
 
+struct SrvRequest;
+
 struct SrvImage {
     int64_t id = 0;
     const uint8_t *host = nullptr;   // pixels (own copy or borrowed)
     std::vector<uint8_t> own;
     int H = 0, W = 0;
     int64_t pitch = 0;
+    // everything below is read and written under the server lock
     scr_tables *t = nullptr;         // resident tables, or null
-    uint64_t last_use = 0;           // LRU stamp (worker only)
-    int builds = 0;                  // worker only
-    // under the server lock: queued or running requests naming the image, and
-    // whether server_forget dropped it (freed once no request names it)
-    int refs = 0;
-    bool forgotten = false;
+    uint64_t last_use = 0;           // LRU stamp
+    int builds = 0;
+    int refs = 0;                    // submitted requests naming the image, not yet completed
+    int pins = 0;                    // ready or running screens using the tables
+    bool building = false;           // a build job is queued or running
+    bool forgotten = false;          // dropped by server_forget; freed once refs == 0 and not building
+    std::vector<SrvRequest *> waiting;   // screens waiting for the build
 };
 
 struct SrvRequest {
@@ -54,6 +62,11 @@ struct SrvRequest {
     scr_request_result res = {};
 };
 
+struct BuildJob {
+    SrvImage *img;
+    SrvRequest *req;   // the upload or evict request, or null for a rebuild
+};
+
 // device or pinned host buffer that only grows
 struct DevBuf {
     void *p = nullptr;
@@ -66,37 +79,42 @@ struct scr_server {
     scr_ctx *ctx = nullptr;
     scr_server_config cfg = {};
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
-    std::deque<SrvRequest *> pending;
+    std::condition_variable cv_screen, cv_build, cv_unpin, cv_done;
+    std::deque<SrvRequest *> pending;                  // submitted, not yet sorted by the screener
+    std::vector<SrvRequest *> ready;                   // screens with pinned resident tables
+    std::deque<BuildJob> jobs;                         // builder queue
     std::unordered_map<uint64_t, SrvRequest *> reqs;   // submitted, not yet collected
     std::unordered_map<int64_t, SrvImage *> images;
-    std::vector<SrvImage *> dropped;                   // forgotten, tables still to free (worker)
+    std::vector<SrvImage *> dropped;                   // forgotten images to free (builder)
     uint64_t next_req = 1;
     int64_t next_image = 1;
-    bool stop = false, hold = false;
-    std::thread worker;
-    cudaStream_t st = nullptr;
-    // worker state
+    bool stop = false, hold = false, stop_builder = false;
+    int jobs_in_flight = 0;
+    std::thread screener, builder;
+    cudaStream_t st = nullptr, bst = nullptr;          // screener and builder streams
     uint64_t lru_clock = 0, resident = 0, batch_seq = 0;
     scr_server_stats stats = {};
-    DevBuf img_dev, counts_dev, keys_dev, mask_dev, list_dev, small_dev;
-    DevBuf counts_host, keys_host, small_host;   // pinned
+    // screener buffers
+    DevBuf counts_dev, keys_dev, mask_dev, list_dev, small_dev;
+    DevBuf counts_host, keys_host, small_host;         // pinned
     uint64_t keys_cap = 0, list_dev_cap = 0;
+    // builder buffer
+    DevBuf img_dev;
 };
 
 namespace {
 
-int grow_dev(scr_server *s, DevBuf &b, size_t bytes) {
+int grow_dev(scr_server *s, DevBuf &b, size_t bytes, cudaStream_t st) {
     if (b.bytes >= bytes)
         return SCR_OK;
     if (b.p) {
-        cudaStreamSynchronize(s->st);
-        dev_free(s->ctx, b.p, b.bytes, s->st);
+        cudaStreamSynchronize(st);
+        dev_free(s->ctx, b.p, b.bytes, st);
         b.p = nullptr;
         b.bytes = 0;
     }
     bytes = std::max<size_t>(bytes, 4096);
-    int rc = dev_alloc(s->ctx, bytes, s->st, &b.p);
+    int rc = dev_alloc(s->ctx, bytes, st, &b.p);
     if (rc)
         return rc;
     b.bytes = bytes;
@@ -120,80 +138,220 @@ int grow_host(DevBuf &b, size_t bytes) {
     return SCR_OK;
 }
 
-uint64_t table_bytes_for(const scr_server *s, const SrvImage *im) {
-    return tables_bytes(im->H, im->W, s->cfg.sum_bits, s->cfg.sq_bits);
-}
-
-void drop_tables(scr_server *s, SrvImage *im) {
-    if (!im->t)
-        return;
-    s->resident -= im->t->bytes;
-    {
-        std::lock_guard<std::mutex> lk(s->ctx->mu);
-        im->t->stream = s->st;
-        free_tables(s->ctx, im->t);
+// Finish a request (server lock held): stamp, release the image, wake waiters.
+void complete(scr_server *s, SrvRequest *r, int status) {
+    r->res.status = status;
+    r->res.done_ns = now_ns();
+    r->done = true;
+    SrvImage *im = r->img;
+    if (--im->refs == 0 && im->forgotten && !im->building) {
+        s->dropped.push_back(im);
+        s->cv_build.notify_one();
     }
-    im->t = nullptr;
+    s->cv_done.notify_all();
 }
 
-// Make im's tables resident; images in `pinned` are not evicted.
-int make_resident(scr_server *s, SrvImage *im, const std::vector<SrvImage *> &pinned, bool *built) {
-    *built = false;
-    if (im->t) {
-        im->last_use = ++s->lru_clock;
+void free_tables_on(scr_server *s, scr_tables *t, cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(s->ctx->mu);
+    t->stream = st;
+    free_tables(s->ctx, t);
+}
+
+// ---------------------------------------------------------------------------
+// builder
+// ---------------------------------------------------------------------------
+
+// Admission by the table budget (server lock held): take the tables of least
+// recently used unpinned images out until `need` more bytes fit; they are
+// returned in `victims` to be freed without the lock.  Waits for running
+// screens to release their pins when only pinned tables stand in the way.
+int admit(scr_server *s, std::unique_lock<std::mutex> &lk, SrvImage *im, uint64_t need,
+          std::vector<scr_tables *> &victims) {
+    const uint64_t budget = s->cfg.table_budget_bytes;
+    if (!budget)
         return SCR_OK;
-    }
-    const uint64_t need = table_bytes_for(s, im);
-    if (s->cfg.table_budget_bytes && s->resident + need > s->cfg.table_budget_bytes) {
+    if (need > budget)
+        return fail(SCR_EBUDGET, "image %lld: its tables (%llu bytes) exceed the table budget (%llu)",
+                    (long long)im->id, (unsigned long long)need, (unsigned long long)budget);
+    for (;;) {
+        if (s->resident + need <= budget)
+            return SCR_OK;
         std::vector<SrvImage *> cand;
         std::vector<uint64_t> bytes, last;
         std::vector<int32_t> pin;
-        {
-            std::lock_guard<std::mutex> lk(s->mu);
-            for (auto &kv : s->images)
-                if (kv.second->t) {
-                    cand.push_back(kv.second);
-                    bytes.push_back(kv.second->t->bytes);
-                    last.push_back(kv.second->last_use);
-                    pin.push_back(std::find(pinned.begin(), pinned.end(), kv.second) != pinned.end());
-                }
-        }
-        std::vector<int32_t> victims(cand.size() + 1);
+        for (auto &kv : s->images)
+            if (kv.second->t) {
+                cand.push_back(kv.second);
+                bytes.push_back(kv.second->t->bytes);
+                last.push_back(kv.second->last_use);
+                pin.push_back(kv.second->pins > 0);
+            }
+        std::vector<int32_t> v(cand.size() + 1);
         int32_t nv = 0;
-        int rc = server_lru_victims(bytes.data(), last.data(), pin.data(), (int32_t)cand.size(), s->resident,
-                                    s->cfg.table_budget_bytes, need, victims.data(), &nv);
-        if (rc)
-            return fail(SCR_EBUDGET, "image %lld: its tables (%llu bytes) do not fit the table budget",
-                        (long long)im->id, (unsigned long long)need);
-        for (int k = 0; k < nv; ++k) {
-            drop_tables(s, cand[victims[k]]);
+        if (server_lru_victims(bytes.data(), last.data(), pin.data(), (int32_t)cand.size(), s->resident, budget,
+                               need, v.data(), &nv) == SCR_OK) {
+            for (int k = 0; k < nv; ++k) {
+                SrvImage *x = cand[v[k]];
+                victims.push_back(x->t);
+                s->resident -= x->t->bytes;
+                x->t = nullptr;
+                s->stats.evictions++;
+            }
+            return SCR_OK;
+        }
+        // only pinned tables are left to evict: wait for the screener to release some
+        s->cv_unpin.wait_for(lk, std::chrono::milliseconds(100));
+    }
+}
+
+void run_job(scr_server *s, BuildJob j) {
+    const int64_t t0 = now_ns();
+    SrvImage *im = j.img;
+    std::unique_lock<std::mutex> lk(s->mu);
+    if (j.req)
+        j.req->res.start_ns = t0;
+    if (j.req && j.req->kind == kEvict) {
+        s->cv_unpin.wait(lk, [&] { return im->pins == 0 || im->forgotten; });
+        scr_tables *t = nullptr;
+        if (!im->forgotten && im->t) {
+            t = im->t;
+            im->t = nullptr;
+            s->resident -= t->bytes;
             s->stats.evictions++;
         }
+        const int status = im->forgotten ? SCR_EEVICTED : SCR_OK;
+        lk.unlock();
+        if (t)
+            free_tables_on(s, t, s->bst);
+        lk.lock();
+        s->jobs_in_flight--;
+        complete(s, j.req, status);
+        s->stats.build_ns += now_ns() - t0;
+        s->cv_screen.notify_one();
+        return;
     }
-    int rc;
-    if ((rc = grow_dev(s, s->img_dev, (size_t)im->H * im->W)))
-        return rc;
-    CUDA_TRY(cudaMemcpy2DAsync(s->img_dev.p, im->W, im->host, im->pitch, im->W, im->H, cudaMemcpyHostToDevice, s->st));
+    int rc = SCR_OK;
     scr_tables *t = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(s->ctx->mu);
-        if ((rc = alloc_tables(s->ctx, im->H, im->W, s->cfg.sum_bits, s->cfg.sq_bits, s->st, &t)))
-            return rc;
-        if ((rc = run_build(s->ctx, (const uint8_t *)s->img_dev.p, im->H, im->W, im->W, t, s->st))) {
-            free_tables(s->ctx, t);
-            return rc;
+    std::vector<scr_tables *> victims;
+    uint64_t need = 0;
+    bool reserved = false;
+    if (im->forgotten) {
+        rc = SCR_EEVICTED;
+    } else if (!im->t) {
+        need = tables_bytes(im->H, im->W, s->cfg.sum_bits, s->cfg.sq_bits);
+        rc = admit(s, lk, im, need, victims);
+        if (rc == SCR_OK) {
+            s->resident += need;   // held for this build
+            reserved = true;
+            s->stats.peak_resident_bytes = std::max<uint64_t>(s->stats.peak_resident_bytes, s->resident);
         }
     }
-    im->t = t;
-    s->resident += t->bytes;
-    s->stats.peak_resident_bytes = std::max<uint64_t>(s->stats.peak_resident_bytes, s->resident);
-    im->last_use = ++s->lru_clock;
-    if (im->builds++)
-        s->stats.rebuilds++;
-    s->stats.builds++;
-    *built = true;
-    return SCR_OK;
+    const bool build = rc == SCR_OK && !im->t;
+    std::string err = rc ? last_error() : std::string();
+    lk.unlock();
+    for (scr_tables *v : victims)
+        free_tables_on(s, v, s->bst);
+    if (build) {
+        if ((rc = grow_dev(s, s->img_dev, (size_t)im->H * im->W, s->bst)) == SCR_OK) {
+            cudaError_t e = cudaMemcpy2DAsync(s->img_dev.p, im->W, im->host, im->pitch, im->W, im->H,
+                                              cudaMemcpyHostToDevice, s->bst);
+            if (e != cudaSuccess)
+                rc = fail(SCR_ECUDA, "image copy: %s", cudaGetErrorString(e));
+        }
+        if (rc == SCR_OK) {
+            const uint64_t before = s->ctx->launches.load();
+            std::lock_guard<std::mutex> g(s->ctx->mu);
+            if ((rc = alloc_tables(s->ctx, im->H, im->W, s->cfg.sum_bits, s->cfg.sq_bits, s->bst, &t)) == SCR_OK &&
+                (rc = run_build(s->ctx, (const uint8_t *)s->img_dev.p, im->H, im->W, im->W, t, s->bst)) != SCR_OK) {
+                free_tables(s->ctx, t);
+                t = nullptr;
+            }
+            s->stats.launches += s->ctx->launches.load() - before;
+        }
+        if (rc == SCR_OK && cudaStreamSynchronize(s->bst) != cudaSuccess)
+            rc = fail(SCR_ECUDA, "table build failed");
+        if (rc)
+            err = last_error();
+    }
+    lk.lock();
+    if (reserved)
+        s->resident -= need;
+    if (build && rc == SCR_OK) {
+        if (im->forgotten) {   // dropped while building: do not install
+            lk.unlock();
+            free_tables_on(s, t, s->bst);
+            lk.lock();
+            rc = SCR_EEVICTED;
+        } else {
+            im->t = t;
+            s->resident += t->bytes;
+            s->stats.peak_resident_bytes = std::max<uint64_t>(s->stats.peak_resident_bytes, s->resident);
+            if (im->builds++)
+                s->stats.rebuilds++;
+            s->stats.builds++;
+        }
+    }
+    if (rc == SCR_OK)
+        im->last_use = ++s->lru_clock;
+    im->building = false;
+    s->jobs_in_flight--;
+    for (SrvRequest *w : im->waiting) {
+        if (rc == SCR_OK) {
+            w->res.built = build;
+            im->pins++;
+            s->ready.push_back(w);
+        } else {
+            complete(s, w, rc);
+        }
+    }
+    im->waiting.clear();
+    if (j.req) {
+        j.req->res.built = build && rc == SCR_OK;
+        complete(s, j.req, rc);
+    }
+    s->stats.build_ns += now_ns() - t0;
+    s->stats.resident_bytes = s->resident;
+    if (rc && !err.empty())
+        fail(rc, "%s", err.c_str());
+    s->cv_screen.notify_one();
 }
+
+void builder_main(scr_server *s) {
+    cudaSetDevice(s->ctx->device);
+    for (;;) {
+        BuildJob j = {nullptr, nullptr};
+        std::vector<SrvImage *> dropped;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv_build.wait(lk, [&] { return s->stop_builder || !s->jobs.empty() || !s->dropped.empty(); });
+            dropped.swap(s->dropped);
+            for (SrvImage *im : dropped)
+                if (im->t) {
+                    s->resident -= im->t->bytes;
+                }
+            if (!s->jobs.empty()) {
+                j = s->jobs.front();
+                s->jobs.pop_front();
+            }
+        }
+        for (SrvImage *im : dropped) {
+            if (im->t)
+                free_tables_on(s, im->t, s->bst);
+            delete im;
+        }
+        if (j.img)
+            run_job(s, j);
+        else if (dropped.empty()) {
+            std::lock_guard<std::mutex> lk(s->mu);
+            if (s->stop_builder && s->jobs.empty())
+                break;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// screener
+// ---------------------------------------------------------------------------
 
 void deliver(SrvRequest *r, const uint64_t *keys, uint64_t count) {
     r->res.count = count;
@@ -203,7 +361,8 @@ void deliver(SrvRequest *r, const uint64_t *keys, uint64_t count) {
     r->res.status = count > r->list_cap ? SCR_EOVERFLOW : SCR_OK;
 }
 
-// All screens of the batch in one batched run.
+// All screens of the batch in one batched run; only the keys each request has
+// room for come back to the host.
 int run_batched(scr_server *s, const std::vector<SrvRequest *> &scr) {
     const int n = (int)scr.size();
     std::vector<const scr_tables *> tabs;
@@ -223,11 +382,11 @@ int run_batched(scr_server *s, const std::vector<SrvRequest *> &scr) {
         ps[k] = scr[k]->p;
     }
     int rc;
-    if ((rc = grow_dev(s, s->counts_dev, (size_t)n * 16)) || (rc = grow_dev(s, s->small_dev, 64)) ||
-        (rc = grow_host(s->counts_host, (size_t)n * 8)) || (rc = grow_host(s->small_host, 64)))
+    if ((rc = grow_dev(s, s->counts_dev, (size_t)n * 16, s->st)) || (rc = grow_dev(s, s->small_dev, 64, s->st)) ||
+        (rc = grow_host(s->counts_host, (size_t)n * 16)) || (rc = grow_host(s->small_host, 64)))
         return rc;
     if (!s->keys_cap) {
-        if ((rc = grow_dev(s, s->keys_dev, (size_t)8 << 20)))
+        if ((rc = grow_dev(s, s->keys_dev, (size_t)8 << 20, s->st)))
             return rc;
         s->keys_cap = s->keys_dev.bytes / 8;
     }
@@ -247,12 +406,12 @@ int run_batched(scr_server *s, const std::vector<SrvRequest *> &scr) {
         batch_set_shape(b, wpw, bps);
         uint64_t launches = 0;
         if (!(rc = upload_plan(b, s->st)) && !(rc = enqueue_run(b, s->st, &launches))) {
-            cudaError_t e = launch_keys_to_lists((uint64_t *)s->keys_dev.p, nk, s->keys_cap, sm_count(s->ctx->device) * 4,
-                                                 s->st, &launches);
+            cudaError_t e = launch_keys_to_lists((uint64_t *)s->keys_dev.p, nk, s->keys_cap,
+                                                 sm_count(s->ctx->device) * 4, s->st, &launches);
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(nk_host, nk, 16, cudaMemcpyDeviceToHost, s->st);
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(s->counts_host.p, counts, (size_t)n * 8, cudaMemcpyDeviceToHost, s->st);
+                e = cudaMemcpyAsync(s->counts_host.p, counts, (size_t)n * 16, cudaMemcpyDeviceToHost, s->st);
             if (e == cudaSuccess)
                 e = cudaStreamSynchronize(s->st);
             if (e != cudaSuccess)
@@ -270,26 +429,34 @@ int run_batched(scr_server *s, const std::vector<SrvRequest *> &scr) {
             break;
         if (attempt)
             return fail(SCR_ECUDA, "internal: key slots grew on the repeated run");
-        // the list did not fit: grow the key buffer and run the batch again
+        // the keys did not fit: grow the key buffer and run the batch again
         const uint64_t want = ((nk_host[1] >> 20) + 2) << 20;
-        if ((rc = grow_dev(s, s->keys_dev, want * 8)))
+        if ((rc = grow_dev(s, s->keys_dev, want * 8, s->st)))
             return rc;
         s->keys_cap = s->keys_dev.bytes / 8;
     }
     s->stats.keys_capacity = s->keys_cap;
-    const uint64_t total = nk_host[0];
+    const uint64_t *cnt = (const uint64_t *)s->counts_host.p, *off = cnt + n;
+    uint64_t total = 0;
+    for (int k = 0; k < n; ++k)
+        total += std::min(cnt[k], scr[k]->list_cap);
     if ((rc = grow_host(s->keys_host, (size_t)std::max<uint64_t>(total, 1) * 8)))
         return rc;
-    if (total) {
-        CUDA_TRY(cudaMemcpyAsync(s->keys_host.p, s->keys_dev.p, total * 8, cudaMemcpyDeviceToHost, s->st));
-        CUDA_TRY(cudaStreamSynchronize(s->st));
-    }
-    const uint64_t *cnt = (const uint64_t *)s->counts_host.p;
-    const uint64_t *keys = (const uint64_t *)s->keys_host.p;
-    uint64_t off = 0;
+    uint64_t *keys = (uint64_t *)s->keys_host.p;
+    uint64_t pos = 0;
     for (int k = 0; k < n; ++k) {
-        deliver(scr[k], keys + off, cnt[k]);
-        off += cnt[k];
+        const uint64_t m = std::min(cnt[k], scr[k]->list_cap);
+        if (m)
+            CUDA_TRY(cudaMemcpyAsync(keys + pos, (const uint64_t *)s->keys_dev.p + off[k], m * 8,
+                                     cudaMemcpyDeviceToHost, s->st));
+        pos += m;
+    }
+    if (total)
+        CUDA_TRY(cudaStreamSynchronize(s->st));
+    pos = 0;
+    for (int k = 0; k < n; ++k) {
+        deliver(scr[k], keys + pos, cnt[k]);
+        pos += std::min(cnt[k], scr[k]->list_cap);
     }
     return SCR_OK;
 }
@@ -300,11 +467,11 @@ int run_plain(scr_server *s, SrvRequest *r) {
     const int S = r->p.n_scales;
     const uint64_t words = (uint64_t)S * im->H * ((im->W + 31) / 32);
     int rc;
-    if ((rc = grow_dev(s, s->mask_dev, words * 4)) || (rc = grow_dev(s, s->small_dev, 64)) ||
+    if ((rc = grow_dev(s, s->mask_dev, words * 4, s->st)) || (rc = grow_dev(s, s->small_dev, 64, s->st)) ||
         (rc = grow_host(s->small_host, 64)))
         return rc;
     if (!s->list_dev_cap) {
-        if ((rc = grow_dev(s, s->list_dev, (size_t)8 << 20)))
+        if ((rc = grow_dev(s, s->list_dev, (size_t)8 << 20, s->st)))
             return rc;
         s->list_dev_cap = s->list_dev.bytes / 8;
     }
@@ -321,7 +488,7 @@ int run_plain(scr_server *s, SrvRequest *r) {
         const uint64_t want = std::min(cnt_host[0], r->list_cap);
         if (want <= s->list_dev_cap || pass)
             break;
-        if ((rc = grow_dev(s, s->list_dev, (size_t)(((want >> 20) + 1) << 20) * 8)))
+        if ((rc = grow_dev(s, s->list_dev, (size_t)(((want >> 20) + 1) << 20) * 8, s->st)))
             return rc;
         s->list_dev_cap = s->list_dev.bytes / 8;
     }
@@ -338,105 +505,84 @@ int run_plain(scr_server *s, SrvRequest *r) {
     return SCR_OK;
 }
 
-void serve_batch(scr_server *s, std::vector<SrvRequest *> &batch) {
-    const int64_t t0 = now_ns();
-    const uint64_t seq = ++s->batch_seq;
-    s->stats.batches++;
-    std::vector<SrvImage *> dropped;
-    {
-        std::lock_guard<std::mutex> lk(s->mu);
-        dropped.swap(s->dropped);
-    }
-    for (SrvImage *im : dropped) {
-        drop_tables(s, im);
-        delete im;
-    }
-    for (SrvRequest *r : batch) {
-        r->res.start_ns = t0;
-        r->res.batch = seq;
-        r->res.batch_size = (int32_t)batch.size();
-    }
-    // the images this batch uses stay resident until it ends
-    std::vector<SrvImage *> pinned;
-    std::vector<SrvRequest *> screens;
-    for (SrvRequest *r : batch) {
-        bool forgotten;
-        {
-            std::lock_guard<std::mutex> lk(s->mu);
-            forgotten = r->img->forgotten;
-        }
-        if (forgotten) {
-            r->res.status = SCR_EEVICTED;
+// Sort newly submitted screens (server lock held): to the ready list, pinning
+// their tables, or to their image's waiting list, asking for a rebuild when
+// none is under way.
+void sort_pending(scr_server *s) {
+    while (!s->pending.empty()) {
+        SrvRequest *r = s->pending.front();
+        s->pending.pop_front();
+        SrvImage *im = r->img;
+        if (im->forgotten) {
+            complete(s, r, SCR_EEVICTED);
             continue;
         }
-        if (r->kind == kEvict) {
-            if (r->img->t && std::find(pinned.begin(), pinned.end(), r->img) == pinned.end()) {
-                drop_tables(s, r->img);
-                s->stats.evictions++;
-            }
-            r->res.status = SCR_OK;
-            continue;
-        }
-        bool built = false;
-        const int rc = make_resident(s, r->img, pinned, &built);
-        r->res.built = built;
-        if (rc) {
-            r->res.status = rc;
-            continue;
-        }
-        if (std::find(pinned.begin(), pinned.end(), r->img) == pinned.end())
-            pinned.push_back(r->img);
-        if (r->kind == kUpload)
-            r->res.status = SCR_OK;
-        else
-            screens.push_back(r);
-    }
-    if (!screens.empty()) {
-        if (s->cfg.mode == SCR_SERVE_BATCHED) {
-            const int rc = run_batched(s, screens);
-            if (rc)
-                for (SrvRequest *r : screens)
-                    r->res.status = rc;
+        if (im->t && !im->building) {
+            im->pins++;
+            s->ready.push_back(r);
         } else {
-            for (SrvRequest *r : screens) {
-                const int rc = run_plain(s, r);
-                if (rc)
-                    r->res.status = rc;
+            im->waiting.push_back(r);
+            if (!im->building) {
+                im->building = true;
+                s->jobs.push_back({im, nullptr});
+                s->jobs_in_flight++;
+                s->cv_build.notify_one();
             }
         }
     }
-    const int64_t t1 = now_ns();
-    std::lock_guard<std::mutex> lk(s->mu);
-    for (SrvRequest *r : batch) {
-        r->res.done_ns = t1;
-        r->done = true;
-        if (--r->img->refs == 0 && r->img->forgotten)
-            s->dropped.push_back(r->img);
-    }
-    s->stats.resident_bytes = s->resident;
-    uint64_t ri = 0;
-    for (auto &kv : s->images)
-        ri += kv.second->t != nullptr;
-    s->stats.resident_images = ri;
-    s->cv_done.notify_all();
 }
 
-void worker_main(scr_server *s) {
+bool drained(const scr_server *s) {
+    return s->pending.empty() && s->ready.empty() && s->jobs.empty() && s->jobs_in_flight == 0;
+}
+
+void screener_main(scr_server *s) {
     cudaSetDevice(s->ctx->device);
     for (;;) {
         std::vector<SrvRequest *> batch;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            s->cv_work.wait(lk, [&] { return s->stop || (!s->hold && !s->pending.empty()); });
-            if (s->pending.empty())
-                break;   // stopping, nothing left
-            const size_t lim = s->cfg.max_batch > 0 ? (size_t)s->cfg.max_batch : s->pending.size();
-            while (!s->pending.empty() && batch.size() < lim) {
-                batch.push_back(s->pending.front());
-                s->pending.pop_front();
+            s->cv_screen.wait(lk, [&] {
+                return (!s->hold && (!s->pending.empty() || !s->ready.empty())) || (s->stop && drained(s));
+            });
+            if (s->stop && drained(s))
+                break;
+            sort_pending(s);
+            const size_t lim = s->cfg.max_batch > 0 ? (size_t)s->cfg.max_batch : s->ready.size();
+            const size_t take = std::min(lim, s->ready.size());
+            batch.assign(s->ready.begin(), s->ready.begin() + take);
+            s->ready.erase(s->ready.begin(), s->ready.begin() + take);
+        }
+        if (batch.empty())
+            continue;
+        const int64_t t0 = now_ns();
+        const uint64_t seq = ++s->batch_seq;
+        for (SrvRequest *r : batch) {
+            r->res.start_ns = t0;
+            r->res.batch = seq;
+            r->res.batch_size = (int32_t)batch.size();
+        }
+        if (s->cfg.mode == SCR_SERVE_BATCHED) {
+            const int rc = run_batched(s, batch);
+            if (rc)
+                for (SrvRequest *r : batch)
+                    r->res.status = rc;
+        } else {
+            for (SrvRequest *r : batch) {
+                const int rc = run_plain(s, r);
+                if (rc)
+                    r->res.status = rc;
             }
         }
-        serve_batch(s, batch);
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stats.batches++;
+        s->stats.screen_ns += now_ns() - t0;
+        for (SrvRequest *r : batch) {
+            r->img->pins--;
+            r->img->last_use = ++s->lru_clock;
+            complete(s, r, r->res.status);
+        }
+        s->cv_unpin.notify_all();
     }
 }
 
@@ -449,11 +595,19 @@ int submit(scr_server *s, SrvRequest *r, uint64_t *request_id) {
     r->id = s->next_req++;
     r->img->refs++;
     s->reqs[r->id] = r;
-    s->pending.push_back(r);
     s->stats.requests++;
     if (request_id)
         *request_id = r->id;
-    s->cv_work.notify_one();
+    if (r->kind == kScreen) {
+        s->pending.push_back(r);
+        s->cv_screen.notify_one();
+    } else {   // uploads and evictions go straight to the builder, held or not
+        if (r->kind == kUpload)
+            r->img->building = true;
+        s->jobs.push_back({r->img, r});
+        s->jobs_in_flight++;
+        s->cv_build.notify_one();
+    }
     return SCR_OK;
 }
 
@@ -492,8 +646,7 @@ int server_lru_victims(const uint64_t *bytes, const uint64_t *last_use, const in
     for (int32_t i = 0; i < n; ++i)
         if (!pinned[i])
             order.push_back(i);
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int32_t a, int32_t b) { return last_use[a] < last_use[b]; });
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return last_use[a] < last_use[b]; });
     uint64_t cur = resident;
     int32_t k = 0;
     for (int32_t i : order) {
@@ -532,11 +685,16 @@ int server_create(scr_ctx *c, const scr_server_config *cfg, scr_server **out) {
     s->cfg = *cfg;
     s->hold = cfg->start_held != 0;
     cudaError_t e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithFlags(&s->bst, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
+        if (s->st)
+            cudaStreamDestroy(s->st);
         delete s;
         return fail(SCR_ECUDA, "stream creation: %s", cudaGetErrorString(e));
     }
-    s->worker = std::thread(worker_main, s);
+    s->builder = std::thread(builder_main, s);
+    s->screener = std::thread(screener_main, s);
     {
         std::lock_guard<std::mutex> lk(c->mu);
         c->servers.insert(s);
@@ -656,9 +814,11 @@ int server_forget(scr_server *s, int64_t image_id) {
         return fail(SCR_EEVICTED, "image %lld is unknown or was forgotten", (long long)image_id);
     s->images.erase(image_id);
     im->forgotten = true;
-    if (im->refs == 0)
-        s->dropped.push_back(im);   // the worker frees it before its next batch
-    s->cv_work.notify_one();
+    if (im->refs == 0 && !im->building) {
+        s->dropped.push_back(im);   // the builder frees it
+        s->cv_build.notify_one();
+    }
+    s->cv_unpin.notify_all();
     return SCR_OK;
 }
 
@@ -667,7 +827,7 @@ int server_wait(scr_server *s, uint64_t request_id, int64_t timeout_us, scr_requ
         return fail(SCR_EINVAL, "null server or result");
     std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->reqs.find(request_id);
-    if (it == s->reqs.end() || request_id == 0)
+    if (it == s->reqs.end())
         return fail(SCR_EINVAL, "unknown or collected request %llu", (unsigned long long)request_id);
     SrvRequest *r = it->second;
     auto ready = [&] { return r->done; };
@@ -686,7 +846,7 @@ int server_hold(scr_server *s, int32_t hold) {
         return fail(SCR_EINVAL, "null server");
     std::lock_guard<std::mutex> lk(s->mu);
     s->hold = hold != 0;
-    s->cv_work.notify_one();
+    s->cv_screen.notify_one();
     return SCR_OK;
 }
 
@@ -705,6 +865,11 @@ int server_stats(scr_server *s, scr_server_stats *out) {
     if (!s || !out)
         return fail(SCR_EINVAL, "null argument");
     std::lock_guard<std::mutex> lk(s->mu);
+    s->stats.resident_bytes = s->resident;
+    uint64_t ri = 0;
+    for (auto &kv : s->images)
+        ri += kv.second->t != nullptr;
+    s->stats.resident_images = ri;
     *out = s->stats;
     return SCR_OK;
 }
@@ -716,30 +881,43 @@ void server_destroy(scr_server *s) {
         std::lock_guard<std::mutex> lk(s->mu);
         s->stop = true;
         s->hold = false;
-        s->cv_work.notify_all();
+        s->cv_screen.notify_all();
     }
-    if (s->worker.joinable())
-        s->worker.join();
+    if (s->screener.joinable())
+        s->screener.join();   // returns once every request is served
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop_builder = true;
+        s->cv_build.notify_all();
+    }
+    if (s->builder.joinable())
+        s->builder.join();
     scr_ctx *c = s->ctx;
     DeviceGuard dg(c->device);
     cudaStreamSynchronize(s->st);
+    cudaStreamSynchronize(s->bst);
     for (auto &kv : s->images) {
-        drop_tables(s, kv.second);
+        if (kv.second->t)
+            free_tables_on(s, kv.second->t, s->bst);
         delete kv.second;
     }
     for (SrvImage *im : s->dropped) {
-        drop_tables(s, im);
+        if (im->t)
+            free_tables_on(s, im->t, s->bst);
         delete im;
     }
     for (auto &kv : s->reqs)
         delete kv.second;
-    for (DevBuf *b : {&s->img_dev, &s->counts_dev, &s->keys_dev, &s->mask_dev, &s->list_dev, &s->small_dev})
+    for (DevBuf *b : {&s->counts_dev, &s->keys_dev, &s->mask_dev, &s->list_dev, &s->small_dev})
         dev_free(c, b->p, b->bytes, s->st);
+    dev_free(c, s->img_dev.p, s->img_dev.bytes, s->bst);
     cudaStreamSynchronize(s->st);
+    cudaStreamSynchronize(s->bst);
     for (DevBuf *b : {&s->counts_host, &s->keys_host, &s->small_host})
         if (b->p)
             cudaFreeHost(b->p);
     cudaStreamDestroy(s->st);
+    cudaStreamDestroy(s->bst);
     {
         std::lock_guard<std::mutex> lk(c->mu);
         c->servers.erase(s);

@@ -342,3 +342,74 @@ def batch_workload(seed: int = BASE_SEED + 3, n_images: int = 64, n_templates: i
         plants.append(pl)
     pairs = [(i, t) for i in range(n_images) for t in range(n_templates)] if all_pairs else []
     return BatchWorkload(images, templates, pairs, F_MEAN | F_VAR | F_GRAD, Tolerances(), 32, 64, plants)
+
+
+@dataclass
+class ServeEvent:
+    t: float            # arrival time, seconds after the start of the stream
+    kind: str           # "upload" or "screen"
+    image: int          # upload: pool index; screen: index in the upload sequence (warm uploads first)
+    template: int = -1  # screen: template index
+    features: int = 0   # screen: feature bits (2 or 3 features)
+
+
+@dataclass
+class ServeWorkload:
+    """Configuration 5: a Poisson stream of uploads and screens against resident tables."""
+    pool: list[np.ndarray]          # distinct images the uploads draw their pixels from
+    templates: list[TemplateSpec]
+    warm: list[int]                 # pool indices uploaded before the stream starts
+    events: list[ServeEvent]
+    tol: Tolerances
+    rate: float
+    duration: float
+    table_budget: int
+    sum_bits: int = 32
+    sq_bits: int = 64
+
+
+def serve_workload(seed: int = BASE_SEED + 4, duration: float = 2.0, rate: float = 2000.0,
+                   upload_frac: float = 0.1, n_pool: int = 16, n_templates: int = 64,
+                   side_range=(256, 8192), r_range=(8, 96), max_scales: int = 16,
+                   table_budget: int = 120 << 30, warm_fill: float = 0.85,
+                   table_bytes_per_px: int = 24) -> ServeWorkload:
+    """Poisson arrivals at `rate`/s for `duration` s; a fraction upload_frac are
+    uploads of a square image with side log-uniform in side_range (pixels drawn
+    from a pool of n_pool blob images, stratified over the log-side range), the rest screen a uniformly chosen
+    uploaded image with a template of radius U{8..96}, 1..16 geometric scales in
+    [0.5, min(2, 181/r)] and 2 (mean, variance) or 3 (plus contrast) features.
+    Before the stream, warm uploads fill warm_fill of the table budget (table
+    bytes estimated at table_bytes_per_px) so that eviction starts early."""
+    rng = rng_for(seed)
+    pool = []
+    lo, hi = math.log(side_range[0]), math.log(side_range[1])
+    for k in range(n_pool):   # stratified over the log-side range
+        side = int(round(math.exp(lo + (k + rng.uniform()) / n_pool * (hi - lo))))
+        pool.append(quantize_with_noise(blob_field(rng, side, side), rng))
+    templates = []
+    for _ in range(n_templates):
+        r = int(rng.integers(r_range[0], r_range[1] + 1))
+        ns = int(rng.integers(1, max_scales + 1))
+        hi = min(2.0, 181.0 / r)
+        scales = [1.0] if ns == 1 else geometric_scales(0.5, hi, ns)
+        trng = rng_for(int(rng.integers(0, 2 ** 31)))
+        tm = _template_from_source(trng, r, src_side=max(192, 4 * (2 * r + 1)))
+        templates.append(TemplateSpec(tm, r, scales, radii_for(r, scales), t_min_for(r, scales)))
+    warm, filled = [], 0
+    while filled < warm_fill * table_budget:
+        k = int(rng.integers(0, n_pool))
+        warm.append(k)
+        filled += pool[k].size * table_bytes_per_px
+    events, t, n_up = [], 0.0, len(warm)
+    while True:
+        t += float(rng.exponential(1.0 / rate))
+        if t >= duration:
+            break
+        if rng.random() < upload_frac:
+            events.append(ServeEvent(t, "upload", int(rng.integers(0, n_pool))))
+            n_up += 1
+        else:
+            feats = F_MEAN | F_VAR | (F_GRAD if rng.random() < 0.5 else 0)
+            events.append(ServeEvent(t, "screen", int(rng.integers(0, n_up)), int(rng.integers(0, n_templates)),
+                                     feats))
+    return ServeWorkload(pool, templates, warm, events, Tolerances(), rate, duration, table_budget)
