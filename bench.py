@@ -425,7 +425,8 @@ def run_serve(args):
     import paper_1707_05647_gb300 as scr
 
     torch.cuda.set_device(0)
-    w = synth.serve_workload(duration=args.duration)
+    rates = [float(r) for r in args.rates.split(",")]
+    w = synth.serve_workload(duration=args.duration, rate=rates[0])
     ctx = scr.screen_init(0, 0)
     tmpls = [scr.template_features(ctx, ts.template, ts.r, max(ts.t_min, 2), 7) for ts in w.templates]
     params = {}
@@ -505,6 +506,8 @@ def run_serve(args):
         st = scr.server_stats(s)
         scr.server_destroy(s)
         scr_lat = np.array([(results[k]["done_ns"] - results[k]["arrival_ns"]) / 1e6 for k in cand])
+        rebuilt = np.array([results[k]["built"] == 1 for k in cand])
+        queue_ms = np.array([(results[k]["start_ns"] - results[k]["arrival_ns"]) / 1e6 for k in cand])
         up_lat = np.array([(results[k]["done_ns"] - results[k]["arrival_ns"]) / 1e6
                            for k, ev in enumerate(w.events) if ev.kind == "upload"])
         bad = sum(1 for r in results.values() if r["status"] not in (scr.SCR_OK, scr.SCR_EOVERFLOW))
@@ -516,6 +519,16 @@ def run_serve(args):
             "screen_latency_ms": {"p50": float(np.percentile(scr_lat, 50)), "p99": float(np.percentile(scr_lat, 99)),
                                   "mean": float(scr_lat.mean()), "max": float(scr_lat.max())},
             "upload_latency_ms": {"p50": float(np.percentile(up_lat, 50)), "p99": float(np.percentile(up_lat, 99))},
+            "screens_waiting_for_rebuild": int(rebuilt.sum()),
+            "screen_latency_no_rebuild_ms": {"p50": float(np.percentile(scr_lat[~rebuilt], 50)),
+                                             "p99": float(np.percentile(scr_lat[~rebuilt], 99))},
+            "screen_start_delay_ms": {"p50": float(np.percentile(queue_ms, 50)),
+                                      "p99": float(np.percentile(queue_ms, 99))},
+            "builder_busy": (st["build_ns"] - warm_stats["build_ns"]) / 1e9 / span,
+            "screener_busy": (st["screen_ns"] - warm_stats["screen_ns"]) / 1e9 / span,
+            "screener_us_per_batch": {k: (st[k + "_ns"] - warm_stats[k + "_ns"]) / 1e3 / max(1, st["batches"] -
+                                                                                       warm_stats["batches"])
+                                      for k in ("plan", "wait", "copy")},
             "evals_per_s": sum(cand.values()) / span, "requests_per_s": len(w.events) / span,
             "span_s": span, "errors": bad,
             "overflowed_lists": sum(1 for k in cand if results[k]["status"] == scr.SCR_EOVERFLOW),
@@ -527,6 +540,24 @@ def run_serve(args):
     batched, cb = replay(scr.SERVE_BATCHED)
     plain, cp = replay(scr.SERVE_PLAIN)
     n_screens = sum(1 for e in w.events if e.kind == "screen")
+    head = w
+    sweep = []
+    for rate in rates[1:]:
+        # same seed: same image pool, templates and warm set; a denser stream
+        w = synth.serve_workload(duration=args.duration, rate=rate)
+        assert [t.r for t in w.templates] == [t.r for t in head.templates]
+        params.update({(ev.template, ev.features): scr.Params(w.templates[ev.template].radii, ev.features,
+                                                               w.tol.mean_rel, w.tol.std_rel, w.tol.grad_rel,
+                                                               w.tol.grad_abs)
+                       for ev in w.events if ev.kind == "screen" and (ev.template, ev.features) not in params})
+        b2, c2b = replay(scr.SERVE_BATCHED)
+        p2, c2p = replay(scr.SERVE_PLAIN)
+        sweep.append({"rate": rate, "requests": len(w.events), "counts_identical": c2b == c2p,
+                      "batched": {k: b2[k] for k in ("screen_latency_ms", "evals_per_s", "requests_per_s",
+                                                     "mean_batch_size", "errors")},
+                      "plain": {k: p2[k] for k in ("screen_latency_ms", "evals_per_s", "requests_per_s",
+                                                   "mean_batch_size", "errors")}})
+    w = head
     print(json.dumps({
         "metric": "served screen latency p50/p99 (ms) and evaluations/s", "workload":
             f"serving: Poisson {w.rate:.0f} req/s for {w.duration:g} s ({len(w.events)} requests, "
@@ -536,7 +567,7 @@ def run_serve(args):
         "batched": batched, "plain": plain,
         "p99_speedup_vs_plain": plain["screen_latency_ms"]["p99"] / batched["screen_latency_ms"]["p99"],
         "p50_speedup_vs_plain": plain["screen_latency_ms"]["p50"] / batched["screen_latency_ms"]["p50"],
-        "counts_identical": cb == cp, "list_cap": cap, "data": "synthetic"}), flush=True)
+        "counts_identical": cb == cp, "list_cap": cap, "load_sweep": sweep, "data": "synthetic"}), flush=True)
     for t in tmpls:
         scr.template_release(ctx, t)
     scr.screen_shutdown(ctx)
@@ -560,6 +591,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="single", choices=["single", "batched", "serve"])
     ap.add_argument("--duration", type=float, default=2.0, help="seconds of arrivals (serve workload)")
+    ap.add_argument("--rates", default="2000,8000,16000",
+                    help="arrival rates (req/s) of the serve workload; the first is the headline")
     ap.add_argument("--images", type=int, default=64)
     ap.add_argument("--templates", type=int, default=256)
     args = ap.parse_args()

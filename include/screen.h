@@ -348,10 +348,13 @@ typedef struct {
     uint64_t requests, batches, uploads, screens;
     uint64_t builds, rebuilds, evictions;
     uint64_t resident_images, resident_bytes, peak_resident_bytes;
-    uint64_t keys_capacity;      /* device key slots the batched path holds */
+    uint64_t mask_bytes;         /* device bytes of the batched path's mask buffers */
     uint64_t launches;           /* kernels the server launched */
     uint64_t build_ns;           /* time the builder spent on uploads, rebuilds and evictions */
-    uint64_t screen_ns;          /* time the screener spent running batches */
+    uint64_t screen_ns;          /* time the screener spent running batches, of which: */
+    uint64_t plan_ns;            /*   planning and launching (host) */
+    uint64_t wait_ns;            /*   waiting for the device */
+    uint64_t copy_ns;            /*   copying results to the callers' buffers */
 } scr_server_stats;
 
 /* CLOCK_MONOTONIC in nanoseconds: the clock of arrival, start and done stamps. */

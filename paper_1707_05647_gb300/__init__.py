@@ -79,7 +79,7 @@ class _RequestResult(ctypes.Structure):
 class _ServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "requests", "batches", "uploads", "screens", "builds", "rebuilds", "evictions", "resident_images",
-        "resident_bytes", "peak_resident_bytes", "keys_capacity", "launches", "build_ns", "screen_ns")]
+        "resident_bytes", "peak_resident_bytes", "mask_bytes", "launches", "build_ns", "screen_ns", "plan_ns", "wait_ns", "copy_ns")]
 
 
 def library_path() -> str:

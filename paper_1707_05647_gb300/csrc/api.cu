@@ -905,14 +905,19 @@ int build_plan(scr_ctx *c, scr_batch *b, const scr_tables *const *tables, int n_
     return SCR_OK;
 }
 
+void pack_plan(const scr_batch *b, void *dst) {
+    char *host = (char *)dst;
+    size_t off = 0;
+    memcpy(host + off, b->images.data(), b->images.size() * sizeof(BImage));
+    off += (b->images.size() * sizeof(BImage) + 255) & ~size_t(255);
+    memcpy(host + off, b->groups.data(), b->groups.size() * sizeof(BGroup));
+    off += (b->groups.size() * sizeof(BGroup) + 255) & ~size_t(255);
+    memcpy(host + off, b->records.data(), b->records.size() * sizeof(BRecord));
+}
+
 int upload_plan(scr_batch *b, cudaStream_t st) {
     std::vector<char> host(b->desc_bytes);
-    size_t off = 0;
-    memcpy(host.data() + off, b->images.data(), b->images.size() * sizeof(BImage));
-    off += (b->images.size() * sizeof(BImage) + 255) & ~size_t(255);
-    memcpy(host.data() + off, b->groups.data(), b->groups.size() * sizeof(BGroup));
-    off += (b->groups.size() * sizeof(BGroup) + 255) & ~size_t(255);
-    memcpy(host.data() + off, b->records.data(), b->records.size() * sizeof(BRecord));
+    pack_plan(b, host.data());
     CUDA_TRY(cudaMemcpyAsync(b->desc, host.data(), b->desc_bytes, cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     return SCR_OK;
@@ -956,6 +961,12 @@ int enqueue_run(scr_batch *b, cudaStream_t st, uint64_t *launches) {
     }
     CUDA_TRY(launch_pair_offsets(b->args.counts, b->offsets, b->n_keys, b->n_reserved, b->n_pairs, st, launches));
     return SCR_OK;
+}
+
+void free_batch_on(scr_ctx *c, scr_batch *b, cudaStream_t st) {
+    dev_free(c, b->desc, b->desc_bytes, st);
+    dev_free(c, b->sort_buf, b->sort_bytes, st);
+    delete b;
 }
 
 void free_batch(scr_ctx *c, scr_batch *b) {

@@ -255,6 +255,17 @@ __global__ void __launch_bounds__(32 * kBatchWarps) k_batch(const BatchArgs a) {
                 }
                 if (!__any_sync(0xffffffffu, keep))
                     continue;
+                if (a.masks) {   // mask mode: lane j writes word j of the record's row
+                    uint32_t mine = 0;
+#pragma unroll
+                    for (int j = 0; j < WPW; ++j) {
+                        const uint32_t bits = __ballot_sync(0xffffffffu, (keep >> j) & 1u);
+                        mine = lane == j ? bits : mine;
+                    }
+                    if (mine)
+                        a.masks[__ldg(&rc->mask_plane) + (int64_t)y * __ldg(&ip->Wwords) + w0 + lane] = mine;
+                    continue;
+                }
                 const uint64_t key_hi = ((uint64_t)__ldg(&rc->pair) << 37) | ((uint64_t)__ldg(&rc->s) << 32) |
                                         ((uint64_t)y << 16);
                 uint32_t nrec = 0;   // survivors of this record in the warp's words
@@ -592,7 +603,37 @@ __global__ void __launch_bounds__(256) k_keys_to_lists(uint64_t *keys, const uin
     }
 }
 
+// One block per pair (grid-stride): the pair's first keys, converted, into its
+// staging slot.
+__global__ void __launch_bounds__(256) k_gather_lists(const uint64_t *keys, const uint64_t *counts,
+                                                      const uint64_t *offsets, const uint64_t *total,
+                                                      const uint64_t *stage, uint64_t *out, uint64_t *out_counts,
+                                                      int n) {
+    pdl_begin();
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        const uint64_t c = counts[k], cap = stage[2 * k], dst = stage[2 * k + 1], src = offsets[k];
+        const uint64_t m = c < cap ? c : cap;
+        for (uint64_t i = threadIdx.x; i < m; i += blockDim.x) {
+            const uint64_t key = keys[src + i];
+            out[dst + i] = (((key >> 32) & 31u) << 48) | (((key >> 16) & 0xFFFFu) << 24) | (key & 0xFFFFu);
+        }
+        if (threadIdx.x == 0)
+            out_counts[k] = c;
+    }
+    if (blockIdx.x == 0 && threadIdx.x < 2)
+        out_counts[n + threadIdx.x] = total[threadIdx.x];
+}
+
 }  // namespace
+
+cudaError_t launch_gather_lists(const uint64_t *keys, const uint64_t *counts, const uint64_t *offsets,
+                                const uint64_t *total, const uint64_t *stage, uint64_t *out, uint64_t *out_counts,
+                                int n, int grid, cudaStream_t st, uint64_t *launches) {
+    if (launches)
+        *launches += 1;
+    return launch_pdl(k_gather_lists, dim3(grid), dim3(256), st, keys, counts, offsets, total, stage, out, out_counts,
+                      n);
+}
 
 cudaError_t launch_keys_to_lists(uint64_t *keys, const uint64_t *n, uint64_t cap, int grid, cudaStream_t st,
                                  uint64_t *launches) {

@@ -37,6 +37,7 @@ struct BRecord {                       // one (pair, scale) test
     uint64_t V_rng;
     int64_t N_lo;
     uint64_t N_rng;
+    int64_t mask_plane;                // mask mode: first word of this (pair, scale) plane
 };
 
 struct BatchArgs {
@@ -51,6 +52,7 @@ struct BatchArgs {
     uint32_t *union_mask;              // per image [H][Wwords], may be null
     uint64_t *keys;
     uint64_t keys_cap;
+    uint32_t *masks;                   // non-null: mask mode (bits to each record's plane, no keys, no counts)
     uint64_t *n_reserved;              // key slots handed out (chunks of kKeyChunk)
     uint64_t *next_unit;               // next unit to hand out (zero before the launch)
 };
@@ -77,6 +79,12 @@ uint64_t sort_max_tiles(uint64_t cap);
 constexpr int kSortLaunchesPerPass = 5;
 // passes 8-bit passes; the result is in a.src after an even number, a.dst after an odd one
 cudaError_t launch_sort(const SortArgs &a, int passes, int grid, cudaStream_t st, uint64_t *launches);
+// For each pair k < n: out[stage[2k + 1] + i] = the single-image key (s << 48) | (y << 24) | x of
+// sorted batched key offsets[k] + i, for i < min(counts[k], stage[2k]); then out_counts[k] =
+// counts[k] and out_counts[n + 0..1] = total[0..1].  stage, out and out_counts may be host-mapped.
+cudaError_t launch_gather_lists(const uint64_t *keys, const uint64_t *counts, const uint64_t *offsets,
+                                const uint64_t *total, const uint64_t *stage, uint64_t *out, uint64_t *out_counts,
+                                int n, int grid, cudaStream_t st, uint64_t *launches);
 // keys[i] = the single-image key (s << 48) | (y << 24) | x of batched key i, for i < min(*n, cap)
 cudaError_t launch_keys_to_lists(uint64_t *keys, const uint64_t *n, uint64_t cap, int grid, cudaStream_t st,
                                  uint64_t *launches);

@@ -155,12 +155,15 @@ int check_screen_inputs(const scr_tables *t, const scr_tmpl *tm, const scr_param
 void plan_layout(scr_batch *b);
 int build_plan(scr_ctx *c, scr_batch *b, const scr_tables *const *tables, int n_images, const scr_tmpl *const *tmpls,
                const scr_params *params, int n_tmpls, const scr_pair *pairs, int n_pairs);
+void pack_plan(const scr_batch *b, void *dst);   // the device descriptor image (desc_bytes) into dst
 int upload_plan(scr_batch *b, cudaStream_t st);
 size_t desc_size(const scr_batch *b);
 void set_args(scr_batch *b);
 int sm_count(int device);
 int enqueue_run(scr_batch *b, cudaStream_t st, uint64_t *launches);
 void free_batch(scr_ctx *c, scr_batch *b);
+// frees a batch without graph whose buffers are stream-ordered on st (runs may be in flight there)
+void free_batch_on(scr_ctx *c, scr_batch *b, cudaStream_t st);
 // plan, device buffers and launch arguments of a batch (inputs already
 // validated, context lock held); no tuning and no graph
 int batch_prepare(scr_ctx *c, const scr_tables *const *tables, int n_images, const scr_tmpl *const *tmpls,

@@ -94,10 +94,19 @@ struct scr_server {
     cudaStream_t st = nullptr, bst = nullptr;          // screener and builder streams
     uint64_t lru_clock = 0, resident = 0, batch_seq = 0;
     scr_server_stats stats = {};
-    // screener buffers
-    DevBuf counts_dev, keys_dev, mask_dev, list_dev, small_dev;
-    DevBuf counts_host, keys_host, small_host;         // pinned
-    uint64_t keys_cap = 0, list_dev_cap = 0;
+    // screener buffers: the plain path's, and one set per batched run in flight
+    DevBuf mask_dev, list_dev, small_dev;
+    DevBuf keys_host, small_host;                      // pinned
+    uint64_t list_dev_cap = 0;
+    struct Slot {
+        DevBuf mask_dev;       // every request's mask planes, one segment each
+        DevBuf segs_dev;       // the segments (MaskSeg)
+        DevBuf scratch_dev;    // segmented compaction scratch
+        DevBuf desc_host;      // pinned copy of the plan and the segments for the upload
+        DevBuf out_host;       // mapped pinned: counts[n] | staged keys
+        cudaEvent_t done = nullptr;
+        bool busy = false;
+    } slots[2];
     // builder buffer
     DevBuf img_dev;
 };
@@ -136,6 +145,33 @@ int grow_host(DevBuf &b, size_t bytes) {
     }
     b.bytes = bytes;
     return SCR_OK;
+}
+
+int grow_mapped(DevBuf &b, size_t bytes) {
+    if (b.bytes >= bytes)
+        return SCR_OK;
+    if (b.p)
+        cudaFreeHost(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    bytes = std::max<size_t>(bytes + (bytes >> 2), 1 << 20);
+    if (cudaHostAlloc(&b.p, bytes, cudaHostAllocMapped) != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return fail(SCR_ENOMEM, "mapped host allocation of %zu bytes failed", bytes);
+    }
+    b.bytes = bytes;
+    return SCR_OK;
+}
+
+template <class T>
+T *device_view(void *host) {   // device address of mapped pinned host memory
+    void *d = nullptr;
+    if (cudaHostGetDevicePointer(&d, host, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return (T *)d;
 }
 
 // Finish a request (server lock held): stamp, release the image, wake waiters.
@@ -361,103 +397,169 @@ void deliver(SrvRequest *r, const uint64_t *keys, uint64_t count) {
     r->res.status = count > r->list_cap ? SCR_EOVERFLOW : SCR_OK;
 }
 
-// All screens of the batch in one batched run; only the keys each request has
-// room for come back to the host.
-int run_batched(scr_server *s, const std::vector<SrvRequest *> &scr) {
+// Keys a request's list gets through the staging area; longer lists get the
+// rest from the device after the run.
+constexpr uint64_t kStageKeys = 1ull << 22;
+
+uint64_t mask_words_of(const SrvRequest *r) {
+    return (uint64_t)r->p.n_scales * r->img->H * ((r->img->W + 31) / 32);
+}
+
+uint64_t seg_words_of(const SrvRequest *r) {   // rounded up to whole compaction chunks
+    return (mask_words_of(r) + kCompactChunk - 1) / kCompactChunk * kCompactChunk;
+}
+
+struct StageLayout {
+    size_t counts, keys, bytes;          // byte offsets in the mapped area
+    std::vector<uint64_t> cap, off;      // per request: staged keys and their offset
+};
+
+StageLayout stage_layout(const std::vector<SrvRequest *> &scr) {
+    StageLayout L;
+    L.counts = 0;
+    L.keys = (8 * scr.size() + 255) & ~size_t(255);
+    uint64_t pos = 0;
+    for (SrvRequest *r : scr) {
+        const uint64_t c = std::min(r->list_cap, kStageKeys);
+        L.cap.push_back(c);
+        L.off.push_back(pos);
+        pos += c;
+    }
+    L.bytes = L.keys + pos * 8 + 8;
+    return L;
+}
+
+// Enqueue one batched run of `scr` on the screener stream using slot `sl`:
+// the screening kernel in mask mode writes each (request, scale) plane of a
+// zeroed mask buffer (records grouped per (image, star radius), so positions
+// and radii shared by several requests are computed once), then one segmented
+// compaction writes each request's first keys, in compact_mask's format and
+// order, and its count into mapped host memory; then the slot's event.
+// Nothing waits for the device.
+int launch_batched(scr_server *s, scr_server::Slot &sl, const std::vector<SrvRequest *> &scr) {
     const int n = (int)scr.size();
     std::vector<const scr_tables *> tabs;
     std::unordered_map<SrvImage *, int> idx;
     std::vector<scr_pair> pairs(n);
     std::vector<const scr_tmpl *> tms(n);
     std::vector<scr_params> ps(n);
+    std::vector<MaskSeg> segs(n);
+    const StageLayout L = stage_layout(scr);
+    uint64_t words = 0;
     for (int k = 0; k < n; ++k) {
-        auto it = idx.find(scr[k]->img);
+        SrvRequest *r = scr[k];
+        auto it = idx.find(r->img);
         if (it == idx.end()) {
-            it = idx.emplace(scr[k]->img, (int)tabs.size()).first;
-            tabs.push_back(scr[k]->img->t);
+            it = idx.emplace(r->img, (int)tabs.size()).first;
+            tabs.push_back(r->img->t);
         }
         pairs[k].image = it->second;
         pairs[k].tmpl = k;
-        tms[k] = scr[k]->tm;
-        ps[k] = scr[k]->p;
+        tms[k] = r->tm;
+        ps[k] = r->p;
+        MaskSeg &g = segs[k];
+        g.word0 = words;
+        g.words = mask_words_of(r);
+        g.chunk0 = (uint32_t)(words / kCompactChunk);
+        g.nchunks = (uint32_t)(seg_words_of(r) / kCompactChunk);
+        g.H = r->img->H;
+        g.Wwords = (r->img->W + 31) / 32;
+        g.cap = L.cap[k];
+        g.out0 = L.off[k];
+        words += seg_words_of(r);
     }
+    const uint64_t nchunks = words / kCompactChunk;
     int rc;
-    if ((rc = grow_dev(s, s->counts_dev, (size_t)n * 16, s->st)) || (rc = grow_dev(s, s->small_dev, 64, s->st)) ||
-        (rc = grow_host(s->counts_host, (size_t)n * 16)) || (rc = grow_host(s->small_host, 64)))
+    if ((rc = grow_dev(s, sl.mask_dev, words * 4, s->st)) ||
+        (rc = grow_dev(s, sl.segs_dev, (size_t)n * sizeof(MaskSeg), s->st)) ||
+        (rc = grow_dev(s, sl.scratch_dev, compact_segments_scratch_bytes(nchunks), s->st)) ||
+        (rc = grow_mapped(sl.out_host, L.bytes)))
         return rc;
-    if (!s->keys_cap) {
-        if ((rc = grow_dev(s, s->keys_dev, (size_t)8 << 20, s->st)))
-            return rc;
-        s->keys_cap = s->keys_dev.bytes / 8;
+    s->stats.mask_bytes = s->slots[0].mask_dev.bytes + s->slots[1].mask_dev.bytes;
+    char *dout = device_view<char>(sl.out_host.p);
+    if (!dout)
+        return fail(SCR_ECUDA, "no device address for the mapped staging area");
+    scr_batch *b = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(s->ctx->mu);
+        rc = batch_prepare(s->ctx, tabs.data(), (int)tabs.size(), tms.data(), ps.data(), n, pairs.data(), n,
+                           (uint64_t *)sl.segs_dev.p, nullptr, nullptr, nullptr, 0, (uint64_t *)sl.segs_dev.p, s->st,
+                           &b);
     }
-    uint64_t *counts = (uint64_t *)s->counts_dev.p, *offsets = counts + n;
-    uint64_t *nk = (uint64_t *)s->small_dev.p, *nk_host = (uint64_t *)s->small_host.p;
-    const int wpw = s->cfg.words_per_warp ? s->cfg.words_per_warp : 4;
-    const int bps = s->cfg.blocks_per_sm ? s->cfg.blocks_per_sm : 4;
-    for (int attempt = 0;; ++attempt) {
-        scr_batch *b = nullptr;
-        {
-            std::lock_guard<std::mutex> lk(s->ctx->mu);
-            rc = batch_prepare(s->ctx, tabs.data(), (int)tabs.size(), tms.data(), ps.data(), n, pairs.data(), n,
-                               counts, offsets, nullptr, (uint64_t *)s->keys_dev.p, s->keys_cap, nk, s->st, &b);
-        }
-        if (rc)
-            return rc;
-        batch_set_shape(b, wpw, bps);
-        uint64_t launches = 0;
-        if (!(rc = upload_plan(b, s->st)) && !(rc = enqueue_run(b, s->st, &launches))) {
-            cudaError_t e = launch_keys_to_lists((uint64_t *)s->keys_dev.p, nk, s->keys_cap,
-                                                 sm_count(s->ctx->device) * 4, s->st, &launches);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(nk_host, nk, 16, cudaMemcpyDeviceToHost, s->st);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(s->counts_host.p, counts, (size_t)n * 16, cudaMemcpyDeviceToHost, s->st);
-            if (e == cudaSuccess)
-                e = cudaStreamSynchronize(s->st);
-            if (e != cudaSuccess)
-                rc = fail(SCR_ECUDA, "batched run: %s", cudaGetErrorString(e));
-        }
-        s->stats.launches += launches;
-        s->ctx->launches += launches;
-        {
-            std::lock_guard<std::mutex> lk(s->ctx->mu);
-            free_batch(s->ctx, b);
-        }
-        if (rc)
-            return rc;
-        if (nk_host[1] <= s->keys_cap)
-            break;
-        if (attempt)
-            return fail(SCR_ECUDA, "internal: key slots grew on the repeated run");
-        // the keys did not fit: grow the key buffer and run the batch again
-        const uint64_t want = ((nk_host[1] >> 20) + 2) << 20;
-        if ((rc = grow_dev(s, s->keys_dev, want * 8, s->st)))
-            return rc;
-        s->keys_cap = s->keys_dev.bytes / 8;
-    }
-    s->stats.keys_capacity = s->keys_cap;
-    const uint64_t *cnt = (const uint64_t *)s->counts_host.p, *off = cnt + n;
-    uint64_t total = 0;
-    for (int k = 0; k < n; ++k)
-        total += std::min(cnt[k], scr[k]->list_cap);
-    if ((rc = grow_host(s->keys_host, (size_t)std::max<uint64_t>(total, 1) * 8)))
+    if (rc)
         return rc;
-    uint64_t *keys = (uint64_t *)s->keys_host.p;
-    uint64_t pos = 0;
-    for (int k = 0; k < n; ++k) {
-        const uint64_t m = std::min(cnt[k], scr[k]->list_cap);
-        if (m)
-            CUDA_TRY(cudaMemcpyAsync(keys + pos, (const uint64_t *)s->keys_dev.p + off[k], m * 8,
-                                     cudaMemcpyDeviceToHost, s->st));
-        pos += m;
+    for (BRecord &rc_ : b->records)   // each (request, scale) plane of the mask buffer
+        rc_.mask_plane = (int64_t)(segs[rc_.pair].word0 + (uint64_t)rc_.s * segs[rc_.pair].H * segs[rc_.pair].Wwords);
+    batch_set_shape(b, s->cfg.words_per_warp ? s->cfg.words_per_warp : 4,
+                    s->cfg.blocks_per_sm ? s->cfg.blocks_per_sm : 4);
+    b->args.masks = (uint32_t *)sl.mask_dev.p;
+    uint64_t launches = 0;
+    const size_t seg_at = (b->desc_bytes + 255) & ~size_t(255);
+    if ((rc = grow_host(sl.desc_host, seg_at + (size_t)n * sizeof(MaskSeg))) == SCR_OK) {
+        pack_plan(b, sl.desc_host.p);
+        memcpy((char *)sl.desc_host.p + seg_at, segs.data(), (size_t)n * sizeof(MaskSeg));
+        cudaError_t e = cudaMemcpyAsync(b->desc, sl.desc_host.p, b->desc_bytes, cudaMemcpyHostToDevice, s->st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(sl.segs_dev.p, (char *)sl.desc_host.p + seg_at, (size_t)n * sizeof(MaskSeg),
+                                cudaMemcpyHostToDevice, s->st);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(sl.mask_dev.p, 0, words * 4, s->st);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(b->n_reserved, 0, 16, s->st);   // the kernel's unit counter
+        if (e == cudaSuccess && b->n_units > 0 && !b->groups.empty())
+            e = launch_batch(b->args, b->wpw, b->grid, s->st, &launches);
+        if (e == cudaSuccess)
+            e = launch_compact_segments((const uint32_t *)sl.mask_dev.p, (const MaskSeg *)sl.segs_dev.p, n, nchunks,
+                                        (uint64_t *)(dout + L.keys), (uint64_t *)(dout + L.counts), sl.scratch_dev.p,
+                                        s->st, &launches);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(sl.done, s->st);
+        if (e != cudaSuccess)
+            rc = fail(SCR_ECUDA, "batched run: %s", cudaGetErrorString(e));
     }
-    if (total)
-        CUDA_TRY(cudaStreamSynchronize(s->st));
-    pos = 0;
-    for (int k = 0; k < n; ++k) {
-        deliver(scr[k], keys + pos, cnt[k]);
-        pos += std::min(cnt[k], scr[k]->list_cap);
+    s->stats.launches += launches;
+    s->ctx->launches += launches;
+    {
+        std::lock_guard<std::mutex> lk(s->ctx->mu);
+        free_batch_on(s->ctx, b, s->st);   // stream-ordered after the run
     }
+    return rc;
+}
+
+// Wait for a run launched by launch_batched and deliver every request's list.
+int finish_batched(scr_server *s, scr_server::Slot &sl, const std::vector<SrvRequest *> &scr) {
+    const int64_t t0 = now_ns();
+    CUDA_TRY(cudaEventSynchronize(sl.done));
+    const int64_t t1 = now_ns();
+    s->stats.wait_ns += t1 - t0;
+    const StageLayout L = stage_layout(scr);
+    const char *out = (const char *)sl.out_host.p;
+    const uint64_t *cnt = (const uint64_t *)(out + L.counts);
+    const uint64_t *keys = (const uint64_t *)(out + L.keys);
+    uint64_t word0 = 0;
+    for (size_t k = 0; k < scr.size(); ++k) {
+        SrvRequest *r = scr[k];
+        const uint64_t c = cnt[k], m = std::min(c, r->list_cap);
+        const uint64_t staged = std::min(m, L.cap[k]);
+        if (staged && r->list_host)
+            memcpy(r->list_host, keys + L.off[k], staged * 8);
+        if (m > staged) {   // a list longer than its staging slot: compact the mask again, in full
+            int rc;
+            if ((rc = grow_dev(s, s->list_dev, (size_t)m * 8, s->st)) || (rc = grow_dev(s, s->small_dev, 64, s->st)))
+                return rc;
+            if ((rc = compact_mask(s->ctx, (const uint32_t *)sl.mask_dev.p + word0, r->p.n_scales, r->img->H,
+                                   r->img->W, (uint64_t *)s->list_dev.p, m, (uint64_t *)s->small_dev.p,
+                                   (scr_stream)s->st)))
+                return rc;
+            CUDA_TRY(cudaMemcpyAsync(r->list_host, s->list_dev.p, m * 8, cudaMemcpyDeviceToHost, s->st));
+            CUDA_TRY(cudaStreamSynchronize(s->st));
+            s->list_dev_cap = s->list_dev.bytes / 8;
+        }
+        r->res.count = c;
+        r->res.status = c > r->list_cap ? SCR_EOVERFLOW : SCR_OK;
+        word0 += seg_words_of(r);
+    }
+    s->stats.copy_ns += now_ns() - t1;
     return SCR_OK;
 }
 
@@ -536,53 +638,106 @@ bool drained(const scr_server *s) {
     return s->pending.empty() && s->ready.empty() && s->jobs.empty() && s->jobs_in_flight == 0;
 }
 
+constexpr uint64_t kBatchMaskWords = 1ull << 31;   // 8 GiB of masks per batched run at most
+
+struct Flight {
+    std::vector<SrvRequest *> reqs;
+    int slot = 0;
+    int rc = SCR_OK;
+    int64_t t0 = 0;
+};
+
+// Release a finished batch's requests (takes the server lock).
+void retire(scr_server *s, const std::vector<SrvRequest *> &batch, int64_t t0) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stats.batches++;
+    s->stats.screen_ns += now_ns() - t0;
+    for (SrvRequest *r : batch) {
+        r->img->pins--;
+        r->img->last_use = ++s->lru_clock;
+        complete(s, r, r->res.status);
+    }
+    s->cv_unpin.notify_all();
+}
+
+// The screener: batched mode keeps up to two runs in flight, so the next batch
+// is planned and enqueued while the device still works on the previous one;
+// plain mode serves each screen with its own launches and waits for it.
 void screener_main(scr_server *s) {
     cudaSetDevice(s->ctx->device);
+    std::deque<Flight> flights;
+    const bool batched = s->cfg.mode == SCR_SERVE_BATCHED;
     for (;;) {
         std::vector<SrvRequest *> batch;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            s->cv_screen.wait(lk, [&] {
-                return (!s->hold && (!s->pending.empty() || !s->ready.empty())) || (s->stop && drained(s));
-            });
-            if (s->stop && drained(s))
+            auto can_take = [&] { return !s->hold && (!s->pending.empty() || !s->ready.empty()); };
+            if (flights.empty())
+                s->cv_screen.wait(lk, [&] { return can_take() || (s->stop && drained(s)); });
+            else if (!can_take())   // poll the oldest run while waiting for arrivals
+                s->cv_screen.wait_for(lk, std::chrono::microseconds(20), can_take);
+            if (flights.empty() && s->stop && drained(s))
                 break;
-            sort_pending(s);
-            const size_t lim = s->cfg.max_batch > 0 ? (size_t)s->cfg.max_batch : s->ready.size();
-            const size_t take = std::min(lim, s->ready.size());
-            batch.assign(s->ready.begin(), s->ready.begin() + take);
-            s->ready.erase(s->ready.begin(), s->ready.begin() + take);
+            if (flights.size() < 2 && can_take()) {
+                sort_pending(s);
+                const size_t lim = s->cfg.max_batch > 0 ? (size_t)s->cfg.max_batch : s->ready.size();
+                size_t take = 0;
+                uint64_t words = 0;   // the batched path's mask buffer stays below kBatchMaskWords
+                while (take < std::min(lim, s->ready.size())) {
+                    words += seg_words_of(s->ready[take]);
+                    if (take && batched && words > kBatchMaskWords)
+                        break;
+                    ++take;
+                }
+                batch.assign(s->ready.begin(), s->ready.begin() + take);
+                s->ready.erase(s->ready.begin(), s->ready.begin() + take);
+            }
         }
-        if (batch.empty())
-            continue;
-        const int64_t t0 = now_ns();
-        const uint64_t seq = ++s->batch_seq;
-        for (SrvRequest *r : batch) {
-            r->res.start_ns = t0;
-            r->res.batch = seq;
-            r->res.batch_size = (int32_t)batch.size();
-        }
-        if (s->cfg.mode == SCR_SERVE_BATCHED) {
-            const int rc = run_batched(s, batch);
-            if (rc)
-                for (SrvRequest *r : batch)
-                    r->res.status = rc;
-        } else {
+        if (!batch.empty()) {
+            const int64_t t0 = now_ns();
+            const uint64_t seq = ++s->batch_seq;
+            for (SrvRequest *r : batch) {
+                r->res.start_ns = t0;
+                r->res.batch = seq;
+                r->res.batch_size = (int32_t)batch.size();
+            }
+            if (batched) {
+                Flight f;
+                f.reqs = std::move(batch);
+                f.t0 = t0;
+                f.slot = s->slots[0].busy ? 1 : 0;
+                s->slots[f.slot].busy = true;
+                f.rc = launch_batched(s, s->slots[f.slot], f.reqs);
+                s->stats.plan_ns += now_ns() - t0;
+                flights.push_back(std::move(f));
+                continue;
+            }
             for (SrvRequest *r : batch) {
                 const int rc = run_plain(s, r);
                 if (rc)
                     r->res.status = rc;
             }
+            retire(s, batch, t0);
+            continue;
         }
-        std::lock_guard<std::mutex> lk(s->mu);
-        s->stats.batches++;
-        s->stats.screen_ns += now_ns() - t0;
-        for (SrvRequest *r : batch) {
-            r->img->pins--;
-            r->img->last_use = ++s->lru_clock;
-            complete(s, r, r->res.status);
+        if (flights.empty())
+            continue;
+        Flight &f = flights.front();
+        // with room for another run, keep polling (arrivals get planned and
+        // enqueued behind it); with two in flight, wait for the oldest
+        if (f.rc == SCR_OK && flights.size() < 2 && cudaEventQuery(s->slots[f.slot].done) == cudaErrorNotReady) {
+            cudaGetLastError();
+            continue;
         }
-        s->cv_unpin.notify_all();
+        cudaGetLastError();
+        if (f.rc == SCR_OK)
+            f.rc = finish_batched(s, s->slots[f.slot], f.reqs);
+        if (f.rc)
+            for (SrvRequest *r : f.reqs)
+                r->res.status = f.rc;
+        s->slots[f.slot].busy = false;
+        retire(s, f.reqs, f.t0);
+        flights.pop_front();
     }
 }
 
@@ -692,6 +847,18 @@ int server_create(scr_ctx *c, const scr_server_config *cfg, scr_server **out) {
             cudaStreamDestroy(s->st);
         delete s;
         return fail(SCR_ECUDA, "stream creation: %s", cudaGetErrorString(e));
+    }
+    for (auto &sl : s->slots)
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        for (auto &sl : s->slots)
+            if (sl.done)
+                cudaEventDestroy(sl.done);
+        cudaStreamDestroy(s->st);
+        cudaStreamDestroy(s->bst);
+        delete s;
+        return fail(SCR_ECUDA, "event creation: %s", cudaGetErrorString(e));
     }
     s->builder = std::thread(builder_main, s);
     s->screener = std::thread(screener_main, s);
@@ -908,14 +1075,23 @@ void server_destroy(scr_server *s) {
     }
     for (auto &kv : s->reqs)
         delete kv.second;
-    for (DevBuf *b : {&s->counts_dev, &s->keys_dev, &s->mask_dev, &s->list_dev, &s->small_dev})
+    for (DevBuf *b : {&s->mask_dev, &s->list_dev, &s->small_dev})
         dev_free(c, b->p, b->bytes, s->st);
+    for (auto &sl : s->slots)
+        for (DevBuf *b : {&sl.mask_dev, &sl.segs_dev, &sl.scratch_dev})
+            dev_free(c, b->p, b->bytes, s->st);
     dev_free(c, s->img_dev.p, s->img_dev.bytes, s->bst);
     cudaStreamSynchronize(s->st);
     cudaStreamSynchronize(s->bst);
-    for (DevBuf *b : {&s->counts_host, &s->keys_host, &s->small_host})
+    for (DevBuf *b : {&s->keys_host, &s->small_host})
         if (b->p)
             cudaFreeHost(b->p);
+    for (auto &sl : s->slots) {
+        for (DevBuf *b : {&sl.desc_host, &sl.out_host})
+            if (b->p)
+                cudaFreeHost(b->p);
+        cudaEventDestroy(sl.done);
+    }
     cudaStreamDestroy(s->st);
     cudaStreamDestroy(s->bst);
     {
