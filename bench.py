@@ -436,7 +436,7 @@ def run_serve(args):
             params[(ev.template, ev.features)] = scr.Params(ts.radii, ev.features, w.tol.mean_rel, w.tol.std_rel,
                                                              w.tol.grad_rel, w.tol.grad_abs)
     cap = 1 << 18
-    n_bufs = 256
+    n_bufs = 1024   # list buffers in flight (2 GiB of host memory)
 
     def candidates(img_shape, radii):
         H, W = img_shape
@@ -465,18 +465,34 @@ def run_serve(args):
         bufs = queue.Queue()
         for _ in range(n_bufs):
             bufs.put(np.zeros(cap, np.uint64))
-        todo = queue.Queue()
         results = {}
+        lock = threading.Lock()
+        meta, early = {}, {}          # request id -> (event index, buffer); results seen before their id
+        state = {"done": 0, "expected": None}
 
-        def collect():
+        def record(k, buf, res):      # lock held
+            results[k] = res
+            state["done"] += 1
+            if buf is not None:
+                bufs.put(buf)
+
+        def collect():                # completion order: a slow request holds no one else's buffer
             while True:
-                item = todo.get()
-                if item is None:
-                    return
-                k, rid, buf = item
-                results[k] = scr.server_wait(s, rid, 600_000_000)
-                if buf is not None:
-                    bufs.put(buf)
+                with lock:
+                    if state["expected"] is not None and state["done"] >= state["expected"]:
+                        return
+                try:
+                    rid, res = scr.server_next(s, 100_000)
+                except scr.ScreenError as e:
+                    if e.code == scr.SCR_ETIMEOUT:
+                        continue
+                    raise
+                with lock:
+                    if rid in meta:
+                        k, buf = meta.pop(rid)
+                        record(k, buf, res)
+                    else:
+                        early[rid] = res
 
         th = threading.Thread(target=collect)
         th.start()
@@ -493,15 +509,20 @@ def run_serve(args):
             if ev.kind == "upload":
                 iid, rid = scr.server_upload(s, w.pool[ev.image], borrow=True, arrival_ns=due)
                 uploads.append((iid, w.pool[ev.image].shape))
-                todo.put((k, rid, None))
+                buf = None
             else:
                 iid, shape = uploads[ev.image]
                 buf = bufs.get()
                 rid = scr.server_screen(s, iid, tmpls[ev.template], params[(ev.template, ev.features)], buf,
                                         arrival_ns=due)
                 cand[k] = candidates(shape, w.templates[ev.template].radii)
-                todo.put((k, rid, buf))
-        todo.put(None)
+            with lock:
+                if rid in early:
+                    record(k, buf, early.pop(rid))
+                else:
+                    meta[rid] = (k, buf)
+        with lock:
+            state["expected"] = len(w.events)
         th.join()
         st = scr.server_stats(s)
         scr.server_destroy(s)
@@ -529,6 +550,9 @@ def run_serve(args):
             "screener_us_per_batch": {k: (st[k + "_ns"] - warm_stats[k + "_ns"]) / 1e3 / max(1, st["batches"] -
                                                                                        warm_stats["batches"])
                                       for k in ("plan", "wait", "copy")},
+            "builder_us_per_build": {k: (st[k] - warm_stats[k]) / 1e3 / max(1, st["builds"] - warm_stats["builds"])
+                                     for k in ("build_ns", "build_copy_ns", "build_alloc_ns", "build_run_ns",
+                                               "build_gpu_ns")},
             "evals_per_s": sum(cand.values()) / span, "requests_per_s": len(w.events) / span,
             "span_s": span, "errors": bad,
             "overflowed_lists": sum(1 for k in cand if results[k]["status"] == scr.SCR_EOVERFLOW),

@@ -299,11 +299,11 @@ void screen_batch_release(scr_ctx *ctx, scr_batch *b);
 
 /* ---- serving loop ---------------------------------------------------------
  *
- * A server owns two threads, each with its own stream on the context's device.
- * Clients upload images (the server keeps a host copy, or borrows the caller's)
- * and submit screen requests from any thread; both return at once with a
- * request id.  The builder thread builds the tables of uploaded images, and
- * rebuilds from the host copy the tables of images evicted earlier: it admits
+ * A server owns three threads, each with its own stream on the context's
+ * device.  Clients upload images (the server keeps a host copy, or borrows the
+ * caller's) and submit screen requests from any thread; both return at once
+ * with a request id.  Two builder threads build the tables of uploaded images,
+ * and rebuild from the host copy the tables of images evicted earlier: they admit
  * new tables by the table budget, evicting least recently used tables that no
  * queued or running screen holds, and waits for running screens to release
  * tables when the rest does not make room.  The screener thread, whenever it is
@@ -350,7 +350,11 @@ typedef struct {
     uint64_t resident_images, resident_bytes, peak_resident_bytes;
     uint64_t mask_bytes;         /* device bytes of the batched path's mask buffers */
     uint64_t launches;           /* kernels the server launched */
-    uint64_t build_ns;           /* time the builder spent on uploads, rebuilds and evictions */
+    uint64_t build_ns;           /* time the builders spent on uploads, rebuilds and evictions (summed), of which: */
+    uint64_t build_copy_ns;      /*   copying images to the device */
+    uint64_t build_alloc_ns;     /*   allocating tables */
+    uint64_t build_run_ns;       /*   building tables (launch to completion) */
+    uint64_t build_gpu_ns;       /*   of which the device ran the builds (events) */
     uint64_t screen_ns;          /* time the screener spent running batches, of which: */
     uint64_t plan_ns;            /*   planning and launching (host) */
     uint64_t wait_ns;            /*   waiting for the device */
@@ -392,8 +396,13 @@ int server_forget(scr_server *s, int64_t image_id);
  * unknown or already collected id. */
 int server_wait(scr_server *s, uint64_t request_id, int64_t timeout_us, scr_request_result *out);
 
+/* Wait up to timeout_us (< 0: forever) for any completed request not yet
+ * collected, in completion order; write its id and result and forget it.
+ * SCR_ETIMEOUT if none completes in time. */
+int server_next(scr_server *s, int64_t timeout_us, uint64_t *request_id, scr_request_result *out);
+
 /* hold = 1: the screener takes no new batch (the one running completes; the
- * builder keeps building); hold = 0: screening resumes. */
+ * builders keep building); hold = 0: screening resumes. */
 int server_hold(scr_server *s, int32_t hold);
 
 /* *resident = 1 when the image's tables are on the device now. */

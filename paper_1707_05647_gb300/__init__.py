@@ -79,7 +79,8 @@ class _RequestResult(ctypes.Structure):
 class _ServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "requests", "batches", "uploads", "screens", "builds", "rebuilds", "evictions", "resident_images",
-        "resident_bytes", "peak_resident_bytes", "mask_bytes", "launches", "build_ns", "screen_ns", "plan_ns", "wait_ns", "copy_ns")]
+        "resident_bytes", "peak_resident_bytes", "mask_bytes", "launches", "build_ns", "build_copy_ns", "build_alloc_ns", "build_run_ns", "build_gpu_ns", "screen_ns", "plan_ns",
+        "wait_ns", "copy_ns")]
 
 
 def library_path() -> str:
@@ -132,6 +133,7 @@ def load(build_if_missing: bool = True):
         "server_evict": ([vp, i64, ctypes.POINTER(u64)], ctypes.c_int),
         "server_forget": ([vp, i64], ctypes.c_int),
         "server_wait": ([vp, u64, i64, ctypes.POINTER(_RequestResult)], ctypes.c_int),
+        "server_next": ([vp, i64, ctypes.POINTER(u64), ctypes.POINTER(_RequestResult)], ctypes.c_int),
         "server_hold": ([vp, i32], ctypes.c_int),
         "server_resident": ([vp, i64, ctypes.POINTER(i32)], ctypes.c_int),
         "server_stats": ([vp, ctypes.POINTER(_ServerStats)], ctypes.c_int),
@@ -153,7 +155,7 @@ def exported_symbols():
             "compact_mask_noalloc_error", "screen_positions",
             "screen_positions_async", "screen_host", "screen_batch_create", "screen_batch_run",
             "screen_batch_info", "screen_batch_release", "server_clock_ns", "server_create", "server_upload",
-            "server_screen", "server_evict", "server_forget", "server_wait", "server_hold", "server_resident",
+            "server_screen", "server_evict", "server_forget", "server_wait", "server_next", "server_hold", "server_resident",
             "server_stats", "server_destroy", "server_lru_victims"]
 
 
@@ -418,6 +420,13 @@ def server_wait(s, request_id: int, timeout_us: int = 300_000_000) -> dict:
     res = _RequestResult()
     _check(load().server_wait(s, request_id, timeout_us, ctypes.byref(res)))
     return {n: int(getattr(res, n)) for n, _ in _RequestResult._fields_}
+
+
+def server_next(s, timeout_us: int = 300_000_000) -> tuple[int, dict]:
+    """The next completed, uncollected request (completion order): (request_id, result)."""
+    res, rid = _RequestResult(), ctypes.c_uint64()
+    _check(load().server_next(s, timeout_us, ctypes.byref(rid), ctypes.byref(res)))
+    return rid.value, {n: int(getattr(res, n)) for n, _ in _RequestResult._fields_}
 
 
 def server_hold(s, hold: bool) -> None:

@@ -191,22 +191,16 @@ size_t tables_bytes(int H, int W, int sum_bits, int sq_bits) {
     return (size_t)table_plane_words(H, W) * 4 * (size_t)(2 * (sum_bits / 32) + 2 * (sq_bits / 32));
 }
 
-int alloc_tables(scr_ctx *c, int H, int W, int sum_bits, int sq_bits, cudaStream_t st, scr_tables **out) {
-    auto *t = new (std::nothrow) scr_tables();
-    if (!t)
-        return fail(SCR_ENOMEM, "host allocation failed");
+void layout_tables(scr_tables *t, void *base, size_t bytes, int H, int W, int sum_bits, int sq_bits,
+                   cudaStream_t st) {
     const int64_t pitch = table_pitch_words(W);
     const int64_t rows = (int64_t)H + 1;
     const int64_t plane = table_plane_words(H, W);
     const int bits[4] = {sum_bits, sq_bits, sum_bits, sq_bits};
     const int64_t cols[4] = {(int64_t)W + 1, (int64_t)W + 1, (int64_t)W + 2, (int64_t)W + 2};
-    t->bytes = tables_bytes(H, W, sum_bits, sq_bits);
-    int rc = dev_alloc(c, t->bytes, st, &t->base);
-    if (rc) {
-        delete t;
-        return rc;
-    }
-    uint32_t *p = (uint32_t *)t->base;
+    t->base = base;
+    t->bytes = bytes;
+    uint32_t *p = (uint32_t *)base;
     for (int k = 0; k < 4; ++k) {
         TableDesc &d = t->t[k];
         d.lo = p;
@@ -224,7 +218,30 @@ int alloc_tables(scr_ctx *c, int H, int W, int sum_bits, int sq_bits, cudaStream
     t->H = H;
     t->W = W;
     t->stream = st;
+}
+
+int alloc_tables(scr_ctx *c, int H, int W, int sum_bits, int sq_bits, cudaStream_t st, scr_tables **out) {
+    auto *t = new (std::nothrow) scr_tables();
+    if (!t)
+        return fail(SCR_ENOMEM, "host allocation failed");
+    const size_t bytes = tables_bytes(H, W, sum_bits, sq_bits);
+    void *base = nullptr;
+    int rc = dev_alloc(c, bytes, st, &base);
+    if (rc) {
+        delete t;
+        return rc;
+    }
+    layout_tables(t, base, bytes, H, W, sum_bits, sq_bits, st);
     *out = t;
+    return SCR_OK;
+}
+
+int run_build_in(scr_ctx *c, const uint8_t *img, int H, int W, int64_t pitch, scr_tables *t, void *scratch,
+                 cudaStream_t st) {
+    uint64_t n = 0;
+    cudaError_t e = launch_build_tables(img, H, W, pitch, t->t[0], t->t[1], t->t[2], t->t[3], scratch, st, &n);
+    c->launches += n;
+    CUDA_TRY(e);
     return SCR_OK;
 }
 
@@ -233,11 +250,7 @@ int run_build(scr_ctx *c, const uint8_t *img, int H, int W, int64_t pitch, scr_t
     int rc = scratch.take(TableScratch::bytes(H, W, t->t[0].bits, t->t[1].bits));
     if (rc)
         return rc;
-    uint64_t n = 0;
-    cudaError_t e = launch_build_tables(img, H, W, pitch, t->t[0], t->t[1], t->t[2], t->t[3], scratch.p, st, &n);
-    c->launches += n;
-    CUDA_TRY(e);
-    return SCR_OK;
+    return run_build_in(c, img, H, W, pitch, t, scratch.p, st);
 }
 
 void free_tables(scr_ctx *c, scr_tables *t) {

@@ -78,7 +78,7 @@ struct StarCorners {
     }
 };
 
-constexpr int kBatchWarps = 8;
+constexpr int kBatchWarps = kBatchWarpsPerBlock;
 
 template <int WPW>
 __global__ void __launch_bounds__(32 * kBatchWarps) k_batch(const BatchArgs a) {
@@ -95,16 +95,22 @@ __global__ void __launch_bounds__(32 * kBatchWarps) k_batch(const BatchArgs a) {
     // so the units in flight stay within a few rows of each other and the
     // table rows they read are still in L2 when the next radius needs them.
     // The next index is fetched one unit ahead to hide the atomic's latency.
+    // With a unit limit the warp fetches no index it will not process.
     int img = -1;   // image of the current unit (warp-uniform)
     uint64_t next = 0;
+    uint32_t taken = 0;
     if (lane == 0)
         next = atomicAdd((unsigned long long *)a.next_unit, 1ull);
     next = __shfl_sync(0xffffffffu, next, 0);
     while (next < (uint64_t)a.n_units) {
         const int64_t u = (int64_t)next * a.unit_stride;
-        if (lane == 0)
-            next = atomicAdd((unsigned long long *)a.next_unit, 1ull);
-        next = __shfl_sync(0xffffffffu, next, 0);
+        if (a.units_per_warp == 0 || ++taken < a.units_per_warp) {
+            if (lane == 0)
+                next = atomicAdd((unsigned long long *)a.next_unit, 1ull);
+            next = __shfl_sync(0xffffffffu, next, 0);
+        } else {
+            next = ~0ull;   // this is the warp's last unit
+        }
         if (img < 0) {
             // first unit of this warp: last image with unit0 <= u (binary search)
             int l = 0, h = a.n_images - 1;

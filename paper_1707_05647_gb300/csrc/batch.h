@@ -48,6 +48,8 @@ struct BatchArgs {
     int32_t n_groups;
     int64_t n_units;                   // units this launch processes
     int64_t unit_stride;               // unit u of the launch is unit u * unit_stride of the plan
+    uint32_t units_per_warp;           // 0: warps run until no unit is left (persistent); else a
+                                       // warp stops after this many, so blocks come and go
     uint64_t *counts;                  // per pair
     uint32_t *union_mask;              // per image [H][Wwords], may be null
     uint64_t *keys;
@@ -57,6 +59,7 @@ struct BatchArgs {
     uint64_t *next_unit;               // next unit to hand out (zero before the launch)
 };
 
+constexpr int kBatchWarpsPerBlock = 8;     // warps of a k_batch block
 constexpr uint64_t kKeySentinel = ~0ull;   // fills unused reserved slots; sorts last
 constexpr int kKeyChunk = 256;             // key slots a warp reserves at a time
 

@@ -129,8 +129,14 @@ int validate_params(const scr_params *p);
 void bounds_for(const scr_tmpl *tm, const scr_params *p, int R, scr_bounds *b);
 int64_t table_plane_words(int H, int W);
 size_t tables_bytes(int H, int W, int sum_bits, int sq_bits);   // device bytes of one image's four tables
+// the four tables of an H x W image laid out in the device block [base, base + bytes)
+void layout_tables(scr_tables *t, void *base, size_t bytes, int H, int W, int sum_bits, int sq_bits,
+                   cudaStream_t st);
 int alloc_tables(scr_ctx *c, int H, int W, int sum_bits, int sq_bits, cudaStream_t st, scr_tables **out);
 int run_build(scr_ctx *c, const uint8_t *img, int H, int W, int64_t pitch, scr_tables *t, cudaStream_t st);
+// as run_build with caller-provided scratch of TableScratch::bytes
+int run_build_in(scr_ctx *c, const uint8_t *img, int H, int W, int64_t pitch, scr_tables *t, void *scratch,
+                 cudaStream_t st);
 void free_tables(scr_ctx *c, scr_tables *t);
 
 // A device buffer charged to the context and returned on scope exit

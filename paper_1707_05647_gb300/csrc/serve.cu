@@ -1,6 +1,6 @@
 // Serving loop of include/screen.h.  Two threads per server:
-//  - the builder builds the tables of uploaded images and rebuilds evicted ones
-//    from their host copy (on its own stream), admitting new tables by the
+//  - two builders build the tables of uploaded images and rebuild evicted ones
+//    from their host copy (each on its own stream), admitting new tables by the
 //    table budget: it evicts least recently used tables that no ready or running
 //    screen pins, and waits for pins to be released when that is not enough;
 //  - the screener takes every screen whose tables are resident whenever it is
@@ -10,6 +10,7 @@
 // Copies and table builds of the builder overlap with the screener's kernels.
 #include <condition_variable>
 #include <deque>
+#include <map>
 #include <thread>
 #include <unordered_map>
 
@@ -84,15 +85,27 @@ struct scr_server {
     std::vector<SrvRequest *> ready;                   // screens with pinned resident tables
     std::deque<BuildJob> jobs;                         // builder queue
     std::unordered_map<uint64_t, SrvRequest *> reqs;   // submitted, not yet collected
+    std::deque<uint64_t> done_q;                       // completed ids, in completion order
     std::unordered_map<int64_t, SrvImage *> images;
     std::vector<SrvImage *> dropped;                   // forgotten images to free (builder)
     uint64_t next_req = 1;
     int64_t next_image = 1;
     bool stop = false, hold = false, stop_builder = false;
     int jobs_in_flight = 0;
-    std::thread screener, builder;
-    cudaStream_t st = nullptr, bst = nullptr;          // screener and builder streams
+    std::thread screener;
+    cudaStream_t st = nullptr;                         // screener stream
+    struct Builder {                                   // builders work on different images at once
+        std::thread th;
+        cudaStream_t st = nullptr;
+        DevBuf img;                                    // the image on the device while its tables build
+        DevBuf scratch;                                // table build scratch
+        cudaEvent_t ev[2] = {nullptr, nullptr};        // around each build, for its device time
+    } builders[2];
     uint64_t lru_clock = 0, resident = 0, batch_seq = 0;
+    void *arena = nullptr;                             // table memory when there is a budget
+    size_t arena_bytes = 0;
+    std::map<size_t, size_t> free_by_off;              // the arena's holes: offset -> size
+    std::multimap<size_t, size_t> free_by_size;        // size -> offset
     scr_server_stats stats = {};
     // screener buffers: the plain path's, and one set per batched run in flight
     DevBuf mask_dev, list_dev, small_dev;
@@ -107,8 +120,6 @@ struct scr_server {
         cudaEvent_t done = nullptr;
         bool busy = false;
     } slots[2];
-    // builder buffer
-    DevBuf img_dev;
 };
 
 namespace {
@@ -179,6 +190,7 @@ void complete(scr_server *s, SrvRequest *r, int status) {
     r->res.status = status;
     r->res.done_ns = now_ns();
     r->done = true;
+    s->done_q.push_back(r->id);
     SrvImage *im = r->img;
     if (--im->refs == 0 && im->forgotten && !im->building) {
         s->dropped.push_back(im);
@@ -187,31 +199,94 @@ void complete(scr_server *s, SrvRequest *r, int status) {
     s->cv_done.notify_all();
 }
 
-void free_tables_on(scr_server *s, scr_tables *t, cudaStream_t st) {
-    std::lock_guard<std::mutex> lk(s->ctx->mu);
-    t->stream = st;
-    free_tables(s->ctx, t);
-}
-
 // ---------------------------------------------------------------------------
 // builder
+//
+// With a table budget, table memory comes from one device arena reserved when
+// the server starts (the budget plus 1/16 for fragmentation) and is handed out
+// best-fit by host bookkeeping, so building and evicting tables make no device
+// allocation.  Without a budget every table is its own allocation.
 // ---------------------------------------------------------------------------
 
-// Admission by the table budget (server lock held): take the tables of least
-// recently used unpinned images out until `need` more bytes fit; they are
-// returned in `victims` to be freed without the lock.  Waits for running
-// screens to release their pins when only pinned tables stand in the way.
+constexpr size_t kArenaAlign = 256;
+
+bool arena_alloc(scr_server *s, size_t need, void **block) {   // lock held
+    auto it = s->free_by_size.lower_bound(need);
+    if (it == s->free_by_size.end())
+        return false;
+    const size_t size = it->first, off = it->second;
+    s->free_by_size.erase(it);
+    s->free_by_off.erase(off);
+    if (size > need) {
+        s->free_by_off[off + need] = size - need;
+        s->free_by_size.emplace(size - need, off + need);
+    }
+    *block = (char *)s->arena + off;
+    return true;
+}
+
+void arena_release(scr_server *s, void *block, size_t size) {   // lock held; coalesces neighbours
+    size_t off = (size_t)((char *)block - (char *)s->arena);
+    auto erase_size = [&](size_t o, size_t sz) {
+        auto r = s->free_by_size.equal_range(sz);
+        for (auto i = r.first; i != r.second; ++i)
+            if (i->second == o) {
+                s->free_by_size.erase(i);
+                return;
+            }
+    };
+    auto next = s->free_by_off.lower_bound(off);
+    if (next != s->free_by_off.end() && next->first == off + size) {
+        size += next->second;
+        erase_size(next->first, next->second);
+        next = s->free_by_off.erase(next);
+    }
+    if (next != s->free_by_off.begin()) {
+        auto prev = std::prev(next);
+        if (prev->first + prev->second == off) {
+            off = prev->first;
+            size += prev->second;
+            erase_size(prev->first, prev->second);
+            s->free_by_off.erase(prev);
+        }
+    }
+    s->free_by_off[off] = size;
+    s->free_by_size.emplace(size, off);
+}
+
+// Take the tables off an image (lock held); without an arena their block is
+// returned in to_free, to be freed without the lock.
+void retire_tables(scr_server *s, SrvImage *im, std::vector<std::pair<size_t, void *>> *to_free) {
+    scr_tables *t = im->t;
+    im->t = nullptr;
+    s->resident -= t->bytes;
+    if (s->arena)
+        arena_release(s, t->base, t->bytes);
+    else if (to_free)
+        to_free->push_back({t->bytes, t->base});
+    delete t;
+}
+
+// Admission by the table budget (server lock held): room for `need` bytes,
+// made by evicting the least recently used unpinned tables (also when the
+// budget allows but the arena has no hole that large).  Waits for running
+// screens to release their pins when only pinned tables stand in the way.  On
+// success `need` is charged to resident and *block is the arena block (null
+// without an arena: the caller allocates).
 int admit(scr_server *s, std::unique_lock<std::mutex> &lk, SrvImage *im, uint64_t need,
-          std::vector<scr_tables *> &victims) {
+          std::vector<std::pair<size_t, void *>> &to_free, void **block) {
     const uint64_t budget = s->cfg.table_budget_bytes;
-    if (!budget)
-        return SCR_OK;
-    if (need > budget)
+    *block = nullptr;
+    if (budget && need > budget)
         return fail(SCR_EBUDGET, "image %lld: its tables (%llu bytes) exceed the table budget (%llu)",
                     (long long)im->id, (unsigned long long)need, (unsigned long long)budget);
     for (;;) {
-        if (s->resident + need <= budget)
-            return SCR_OK;
+        if (!budget || s->resident + need <= budget) {
+            if (!s->arena || arena_alloc(s, need, block)) {
+                s->resident += need;
+                return SCR_OK;
+            }
+        }
         std::vector<SrvImage *> cand;
         std::vector<uint64_t> bytes, last;
         std::vector<int32_t> pin;
@@ -224,23 +299,27 @@ int admit(scr_server *s, std::unique_lock<std::mutex> &lk, SrvImage *im, uint64_
             }
         std::vector<int32_t> v(cand.size() + 1);
         int32_t nv = 0;
-        if (server_lru_victims(bytes.data(), last.data(), pin.data(), (int32_t)cand.size(), s->resident, budget,
-                               need, v.data(), &nv) == SCR_OK) {
+        const bool fits = s->resident + need <= budget;   // then only the arena is fragmented
+        if (server_lru_victims(bytes.data(), last.data(), pin.data(), (int32_t)cand.size(),
+                               fits ? budget : s->resident, budget, fits ? 1 : need, v.data(), &nv) == SCR_OK &&
+            nv > 0) {
             for (int k = 0; k < nv; ++k) {
-                SrvImage *x = cand[v[k]];
-                victims.push_back(x->t);
-                s->resident -= x->t->bytes;
-                x->t = nullptr;
+                retire_tables(s, cand[v[k]], &to_free);
                 s->stats.evictions++;
             }
-            return SCR_OK;
+            continue;
         }
         // only pinned tables are left to evict: wait for the screener to release some
         s->cv_unpin.wait_for(lk, std::chrono::milliseconds(100));
     }
 }
 
-void run_job(scr_server *s, BuildJob j) {
+void free_blocks(scr_server *s, const std::vector<std::pair<size_t, void *>> &blocks, cudaStream_t st) {
+    for (auto &b : blocks)
+        dev_free(s->ctx, b.second, b.first, st);
+}
+
+void run_job(scr_server *s, scr_server::Builder &bd, BuildJob j) {
     const int64_t t0 = now_ns();
     SrvImage *im = j.img;
     std::unique_lock<std::mutex> lk(s->mu);
@@ -248,83 +327,94 @@ void run_job(scr_server *s, BuildJob j) {
         j.req->res.start_ns = t0;
     if (j.req && j.req->kind == kEvict) {
         s->cv_unpin.wait(lk, [&] { return im->pins == 0 || im->forgotten; });
-        scr_tables *t = nullptr;
+        std::vector<std::pair<size_t, void *>> blocks;
         if (!im->forgotten && im->t) {
-            t = im->t;
-            im->t = nullptr;
-            s->resident -= t->bytes;
+            retire_tables(s, im, &blocks);
             s->stats.evictions++;
         }
-        const int status = im->forgotten ? SCR_EEVICTED : SCR_OK;
-        lk.unlock();
-        if (t)
-            free_tables_on(s, t, s->bst);
-        lk.lock();
         s->jobs_in_flight--;
-        complete(s, j.req, status);
+        complete(s, j.req, im->forgotten ? SCR_EEVICTED : SCR_OK);
         s->stats.build_ns += now_ns() - t0;
         s->cv_screen.notify_one();
+        lk.unlock();
+        free_blocks(s, blocks, bd.st);
         return;
     }
     int rc = SCR_OK;
-    scr_tables *t = nullptr;
-    std::vector<scr_tables *> victims;
+    std::vector<std::pair<size_t, void *>> to_free;
     uint64_t need = 0;
-    bool reserved = false;
-    if (im->forgotten) {
+    void *block = nullptr;
+    if (im->forgotten)
         rc = SCR_EEVICTED;
-    } else if (!im->t) {
-        need = tables_bytes(im->H, im->W, s->cfg.sum_bits, s->cfg.sq_bits);
-        rc = admit(s, lk, im, need, victims);
-        if (rc == SCR_OK) {
-            s->resident += need;   // held for this build
-            reserved = true;
+    else if (!im->t) {
+        need = (tables_bytes(im->H, im->W, s->cfg.sum_bits, s->cfg.sq_bits) + kArenaAlign - 1) & ~(kArenaAlign - 1);
+        rc = admit(s, lk, im, need, to_free, &block);
+        if (rc == SCR_OK)
             s->stats.peak_resident_bytes = std::max<uint64_t>(s->stats.peak_resident_bytes, s->resident);
-        }
     }
     const bool build = rc == SCR_OK && !im->t;
     std::string err = rc ? last_error() : std::string();
     lk.unlock();
-    for (scr_tables *v : victims)
-        free_tables_on(s, v, s->bst);
+    free_blocks(s, to_free, bd.st);
+    int64_t t_copy = 0, t_alloc = 0, t_run = 0, t_gpu = 0;
+    scr_tables *t = nullptr;
     if (build) {
-        if ((rc = grow_dev(s, s->img_dev, (size_t)im->H * im->W, s->bst)) == SCR_OK) {
-            cudaError_t e = cudaMemcpy2DAsync(s->img_dev.p, im->W, im->host, im->pitch, im->W, im->H,
-                                              cudaMemcpyHostToDevice, s->bst);
+        int64_t ta = now_ns();
+        if ((rc = grow_dev(s, bd.img, (size_t)im->H * im->W, bd.st)) == SCR_OK) {
+            cudaError_t e = im->pitch == im->W   // contiguous rows: one plain copy
+                                ? cudaMemcpyAsync(bd.img.p, im->host, (size_t)im->H * im->W, cudaMemcpyHostToDevice,
+                                                  bd.st)
+                                : cudaMemcpy2DAsync(bd.img.p, im->W, im->host, im->pitch, im->W, im->H,
+                                                    cudaMemcpyHostToDevice, bd.st);
             if (e != cudaSuccess)
                 rc = fail(SCR_ECUDA, "image copy: %s", cudaGetErrorString(e));
         }
+        const int64_t tb = now_ns();
+        t_copy = tb - ta;
+        if (rc == SCR_OK && !block)
+            rc = dev_alloc(s->ctx, need, bd.st, &block);
+        if (rc == SCR_OK)
+            rc = grow_dev(s, bd.scratch, TableScratch::bytes(im->H, im->W, s->cfg.sum_bits, s->cfg.sq_bits), bd.st);
+        const int64_t tc = now_ns();
+        t_alloc = tc - tb;
         if (rc == SCR_OK) {
+            t = new (std::nothrow) scr_tables();
+            if (!t)
+                rc = fail(SCR_ENOMEM, "host allocation failed");
+        }
+        if (rc == SCR_OK) {
+            layout_tables(t, block, need, im->H, im->W, s->cfg.sum_bits, s->cfg.sq_bits, bd.st);
             const uint64_t before = s->ctx->launches.load();
-            std::lock_guard<std::mutex> g(s->ctx->mu);
-            if ((rc = alloc_tables(s->ctx, im->H, im->W, s->cfg.sum_bits, s->cfg.sq_bits, s->bst, &t)) == SCR_OK &&
-                (rc = run_build(s->ctx, (const uint8_t *)s->img_dev.p, im->H, im->W, im->W, t, s->bst)) != SCR_OK) {
-                free_tables(s->ctx, t);
-                t = nullptr;
-            }
+            cudaEventRecord(bd.ev[0], bd.st);
+            rc = run_build_in(s->ctx, (const uint8_t *)bd.img.p, im->H, im->W, im->W, t, bd.scratch.p, bd.st);
+            cudaEventRecord(bd.ev[1], bd.st);
+            if (rc == SCR_OK && cudaStreamSynchronize(bd.st) != cudaSuccess)
+                rc = fail(SCR_ECUDA, "table build failed");
+            float ms = 0;
+            if (rc == SCR_OK && cudaEventElapsedTime(&ms, bd.ev[0], bd.ev[1]) == cudaSuccess)
+                t_gpu = (int64_t)(ms * 1e6f);
             s->stats.launches += s->ctx->launches.load() - before;
         }
-        if (rc == SCR_OK && cudaStreamSynchronize(s->bst) != cudaSuccess)
-            rc = fail(SCR_ECUDA, "table build failed");
+        t_run = now_ns() - tc;
         if (rc)
             err = last_error();
     }
     lk.lock();
-    if (reserved)
-        s->resident -= need;
-    if (build && rc == SCR_OK) {
-        if (im->forgotten) {   // dropped while building: do not install
-            lk.unlock();
-            free_tables_on(s, t, s->bst);
-            lk.lock();
-            rc = SCR_EEVICTED;
-        } else {
+    if (build) {
+        if (rc == SCR_OK && !im->forgotten) {
             im->t = t;
-            s->resident += t->bytes;
-            s->stats.peak_resident_bytes = std::max<uint64_t>(s->stats.peak_resident_bytes, s->resident);
             if (im->builds++)
                 s->stats.rebuilds++;
             s->stats.builds++;
+        } else {   // failed, or dropped while building: give the block back
+            if (rc == SCR_OK)
+                rc = SCR_EEVICTED;
+            delete t;
+            s->resident -= need;
+            if (block && s->arena)
+                arena_release(s, block, need);
+            else if (block)
+                to_free.push_back({need, block});
         }
     }
     if (rc == SCR_OK)
@@ -346,37 +436,42 @@ void run_job(scr_server *s, BuildJob j) {
         complete(s, j.req, rc);
     }
     s->stats.build_ns += now_ns() - t0;
-    s->stats.resident_bytes = s->resident;
+    s->stats.build_copy_ns += t_copy;
+    s->stats.build_alloc_ns += t_alloc;
+    s->stats.build_run_ns += t_run;
+    s->stats.build_gpu_ns += t_gpu;
     if (rc && !err.empty())
         fail(rc, "%s", err.c_str());
     s->cv_screen.notify_one();
+    std::vector<std::pair<size_t, void *>> late;
+    late.swap(to_free);
+    lk.unlock();
+    free_blocks(s, late, bd.st);
 }
 
-void builder_main(scr_server *s) {
+void builder_main(scr_server *s, scr_server::Builder *bd) {
     cudaSetDevice(s->ctx->device);
     for (;;) {
         BuildJob j = {nullptr, nullptr};
         std::vector<SrvImage *> dropped;
+        std::vector<std::pair<size_t, void *>> blocks;
         {
             std::unique_lock<std::mutex> lk(s->mu);
             s->cv_build.wait(lk, [&] { return s->stop_builder || !s->jobs.empty() || !s->dropped.empty(); });
             dropped.swap(s->dropped);
             for (SrvImage *im : dropped)
-                if (im->t) {
-                    s->resident -= im->t->bytes;
-                }
+                if (im->t)
+                    retire_tables(s, im, &blocks);
             if (!s->jobs.empty()) {
                 j = s->jobs.front();
                 s->jobs.pop_front();
             }
         }
-        for (SrvImage *im : dropped) {
-            if (im->t)
-                free_tables_on(s, im->t, s->bst);
+        for (SrvImage *im : dropped)
             delete im;
-        }
+        free_blocks(s, blocks, bd->st);
         if (j.img)
-            run_job(s, j);
+            run_job(s, *bd, j);
         else if (dropped.empty()) {
             std::lock_guard<std::mutex> lk(s->mu);
             if (s->stop_builder && s->jobs.empty())
@@ -492,6 +587,18 @@ int launch_batched(scr_server *s, scr_server::Slot &sl, const std::vector<SrvReq
         rc_.mask_plane = (int64_t)(segs[rc_.pair].word0 + (uint64_t)rc_.s * segs[rc_.pair].H * segs[rc_.pair].Wwords);
     batch_set_shape(b, s->cfg.words_per_warp ? s->cfg.words_per_warp : 4,
                     s->cfg.blocks_per_sm ? s->cfg.blocks_per_sm : 4);
+    // Short-lived blocks: each warp takes at most kUnitsPerWarp units and the
+    // grid covers the plan, so blocks keep finishing and the builders'
+    // higher-priority table builds get SMs while a batch runs.
+    {
+        constexpr uint32_t kUnitsPerWarp = 4;
+        const uint64_t warps = ((uint64_t)b->n_units + kUnitsPerWarp - 1) / kUnitsPerWarp;
+        const uint64_t blocks = (warps + kBatchWarpsPerBlock - 1) / kBatchWarpsPerBlock;
+        b->grid = (int)std::max<uint64_t>(std::min<uint64_t>(blocks, 1u << 20), (uint64_t)b->grid);
+        b->args.units_per_warp = (uint32_t)std::max<uint64_t>(
+            1, ((uint64_t)b->n_units + (uint64_t)b->grid * kBatchWarpsPerBlock - 1) /
+                   ((uint64_t)b->grid * kBatchWarpsPerBlock));
+    }
     b->args.masks = (uint32_t *)sl.mask_dev.p;
     uint64_t launches = 0;
     const size_t seg_at = (b->desc_bytes + 255) & ~size_t(255);
@@ -839,12 +946,19 @@ int server_create(scr_ctx *c, const scr_server_config *cfg, scr_server **out) {
     s->ctx = c;
     s->cfg = *cfg;
     s->hold = cfg->start_held != 0;
+    // table builds go first when they and screening kernels wait for the same SMs
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     cudaError_t e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
-    if (e == cudaSuccess)
-        e = cudaStreamCreateWithFlags(&s->bst, cudaStreamNonBlocking);
+    for (auto &bd : s->builders)
+        if (e == cudaSuccess)
+            e = cudaStreamCreateWithPriority(&bd.st, cudaStreamNonBlocking, prio_hi);
     if (e != cudaSuccess) {
         if (s->st)
             cudaStreamDestroy(s->st);
+        for (auto &bd : s->builders)
+            if (bd.st)
+                cudaStreamDestroy(bd.st);
         delete s;
         return fail(SCR_ECUDA, "stream creation: %s", cudaGetErrorString(e));
     }
@@ -856,11 +970,32 @@ int server_create(scr_ctx *c, const scr_server_config *cfg, scr_server **out) {
             if (sl.done)
                 cudaEventDestroy(sl.done);
         cudaStreamDestroy(s->st);
-        cudaStreamDestroy(s->bst);
+        for (auto &bd : s->builders)
+            cudaStreamDestroy(bd.st);
         delete s;
         return fail(SCR_ECUDA, "event creation: %s", cudaGetErrorString(e));
     }
-    s->builder = std::thread(builder_main, s);
+    if (cfg->table_budget_bytes) {
+        const size_t want = (size_t)cfg->table_budget_bytes + (size_t)(cfg->table_budget_bytes >> 4);
+        if ((rc = dev_alloc(c, (want + kArenaAlign - 1) & ~(kArenaAlign - 1), s->st, &s->arena))) {
+            cudaStreamDestroy(s->st);
+            for (auto &bd : s->builders)
+                cudaStreamDestroy(bd.st);
+            for (auto &sl : s->slots)
+                cudaEventDestroy(sl.done);
+            delete s;
+            return rc;
+        }
+        s->arena_bytes = (want + kArenaAlign - 1) & ~(kArenaAlign - 1);
+        s->free_by_off[0] = s->arena_bytes;
+        s->free_by_size.emplace(s->arena_bytes, 0);
+        cudaStreamSynchronize(s->st);
+    }
+    for (auto &bd : s->builders) {
+        cudaEventCreate(&bd.ev[0]);
+        cudaEventCreate(&bd.ev[1]);
+        bd.th = std::thread(builder_main, s, &bd);
+    }
     s->screener = std::thread(screener_main, s);
     {
         std::lock_guard<std::mutex> lk(c->mu);
@@ -1008,6 +1143,29 @@ int server_wait(scr_server *s, uint64_t request_id, int64_t timeout_us, scr_requ
     return SCR_OK;
 }
 
+int server_next(scr_server *s, int64_t timeout_us, uint64_t *request_id, scr_request_result *out) {
+    if (!s || !out || !request_id)
+        return fail(SCR_EINVAL, "null server, id or result");
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto ready = [&] {   // drop ids that server_wait collected already
+        while (!s->done_q.empty() && !s->reqs.count(s->done_q.front()))
+            s->done_q.pop_front();
+        return !s->done_q.empty();
+    };
+    if (timeout_us < 0)
+        s->cv_done.wait(lk, ready);
+    else if (!s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready))
+        return fail(SCR_ETIMEOUT, "no request completed in time");
+    const uint64_t id = s->done_q.front();
+    s->done_q.pop_front();
+    auto it = s->reqs.find(id);
+    *request_id = id;
+    *out = it->second->res;
+    delete it->second;
+    s->reqs.erase(it);
+    return SCR_OK;
+}
+
 int server_hold(scr_server *s, int32_t hold) {
     if (!s)
         return fail(SCR_EINVAL, "null server");
@@ -1057,22 +1215,28 @@ void server_destroy(scr_server *s) {
         s->stop_builder = true;
         s->cv_build.notify_all();
     }
-    if (s->builder.joinable())
-        s->builder.join();
+    for (auto &bd : s->builders)
+        if (bd.th.joinable())
+            bd.th.join();
     scr_ctx *c = s->ctx;
     DeviceGuard dg(c->device);
     cudaStreamSynchronize(s->st);
-    cudaStreamSynchronize(s->bst);
+    for (auto &bd : s->builders)
+        cudaStreamSynchronize(bd.st);
+    std::vector<std::pair<size_t, void *>> blocks;
     for (auto &kv : s->images) {
         if (kv.second->t)
-            free_tables_on(s, kv.second->t, s->bst);
+            retire_tables(s, kv.second, &blocks);
         delete kv.second;
     }
     for (SrvImage *im : s->dropped) {
         if (im->t)
-            free_tables_on(s, im->t, s->bst);
+            retire_tables(s, im, &blocks);
         delete im;
     }
+    free_blocks(s, blocks, s->st);
+    if (s->arena)
+        dev_free(c, s->arena, s->arena_bytes, s->st);
     for (auto &kv : s->reqs)
         delete kv.second;
     for (DevBuf *b : {&s->mask_dev, &s->list_dev, &s->small_dev})
@@ -1080,9 +1244,13 @@ void server_destroy(scr_server *s) {
     for (auto &sl : s->slots)
         for (DevBuf *b : {&sl.mask_dev, &sl.segs_dev, &sl.scratch_dev})
             dev_free(c, b->p, b->bytes, s->st);
-    dev_free(c, s->img_dev.p, s->img_dev.bytes, s->bst);
+    for (auto &bd : s->builders) {
+        dev_free(c, bd.img.p, bd.img.bytes, bd.st);
+        dev_free(c, bd.scratch.p, bd.scratch.bytes, bd.st);
+    }
     cudaStreamSynchronize(s->st);
-    cudaStreamSynchronize(s->bst);
+    for (auto &bd : s->builders)
+        cudaStreamSynchronize(bd.st);
     for (DevBuf *b : {&s->keys_host, &s->small_host})
         if (b->p)
             cudaFreeHost(b->p);
@@ -1093,7 +1261,12 @@ void server_destroy(scr_server *s) {
         cudaEventDestroy(sl.done);
     }
     cudaStreamDestroy(s->st);
-    cudaStreamDestroy(s->bst);
+    for (auto &bd : s->builders) {
+        cudaStreamDestroy(bd.st);
+        for (cudaEvent_t e : bd.ev)
+            if (e)
+                cudaEventDestroy(e);
+    }
     {
         std::lock_guard<std::mutex> lk(c->mu);
         c->servers.erase(s);

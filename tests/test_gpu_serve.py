@@ -187,9 +187,42 @@ def test_forget_overflow_and_budget_errors(ctx, work):
 
 
 def scr_table_bytes(shape, sum_bits=32, sq_bits=64):
-    """Device bytes of one image's four tables: (H + 1) rows at the padded pitch
-    per u32 plane, one plane per 32 bits (the library's layout)."""
+    """Device bytes the server charges for one image's four tables: (H + 1) rows
+    at the padded pitch per u32 plane, one plane per 32 bits (the library's
+    layout; a multiple of 256 bytes)."""
     H, W = shape
     pitch = ((W + 16 + 31) // 32) * 32
     plane = (((H + 1) * pitch + 63) // 64) * 64
     return plane * 4 * (2 * (sum_bits // 32) + 2 * (sq_bits // 32))
+
+
+def test_completion_queue_returns_each_request_once(ctx, work):
+    bw, tmpls, params, want = work
+    s = scr.server_create(ctx, max_batch=3)
+    try:
+        ids = []
+        for im in bw.images:
+            iid, rid = scr.server_upload(s, im)
+            ids.append(iid)
+        reqs, bufs = {}, {}
+        for k in range(12):
+            i, t = k % 4, (2 * k) % 5
+            buf = np.zeros(1 << 16, np.uint64)
+            rid = scr.server_screen(s, ids[i], tmpls[t], params[t], buf)
+            reqs[rid], bufs[rid] = (i, t), buf
+        seen = []
+        for _ in range(len(reqs) + len(bw.images)):
+            rid, r = scr.server_next(s, 60_000_000)
+            seen.append(rid)
+            if rid in reqs:
+                i, t = reqs[rid]
+                assert r["status"] == scr.SCR_OK and r["kind"] == 1
+                assert np.array_equal(bufs[rid][:r["count"]], want[(i, t)])
+            else:
+                assert r["kind"] == 0                       # the uploads
+        assert len(set(seen)) == len(seen) and set(reqs) <= set(seen)
+        with pytest.raises(scr.ScreenError) as e:
+            scr.server_next(s, 1000)
+        assert e.value.code == scr.SCR_ETIMEOUT
+    finally:
+        scr.server_destroy(s)
