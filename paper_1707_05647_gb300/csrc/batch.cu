@@ -80,8 +80,11 @@ struct StarCorners {
 
 constexpr int kBatchWarps = kBatchWarpsPerBlock;
 
+// Register budget per variant: 3 resident blocks (80 registers) with 8 words
+// per warp, 4 (64 registers) with fewer, neither spilling; more warps per SM
+// hide the L2 latency of the corner loads.
 template <int WPW>
-__global__ void __launch_bounds__(32 * kBatchWarps) k_batch(const BatchArgs a) {
+__global__ void __launch_bounds__(32 * kBatchWarps, (WPW >= 8 ? 3 : 4)) k_batch(const BatchArgs a) {
     pdl_begin();
     const int lane = threadIdx.x & 31;
     const uint32_t lt_mask = (1u << lane) - 1u;
