@@ -185,6 +185,38 @@ int screen_bounds(const scr_tmpl *tm, const scr_params *p, scr_bounds *out);
 int screen_features(scr_ctx *ctx, const scr_tables *t, const scr_tmpl *tm, const scr_params *p,
                     uint32_t *mask_dev, uint64_t mask_words, scr_stream stream);
 
+/* ---- joint-vector membership over nested central areas ------------------ */
+
+/* The exact test of Sec. 5 (Algorithm 1 with the feature set F_n of Eq. F_n)
+ * in place of per-feature intervals, for up to three central areas of every
+ * candidate (the closing paragraphs of Sec. 5).  Each enabled feature of a star
+ * (mean S/A, standard deviation sqrt(V)/A with V = A*Q - S^2, contrast
+ * N/(A_in*A_ring)) is quantised with Q(f) = floor(f/q + 1/2) (q per feature,
+ * in grey levels); area j's set F_j marks, for every template central radius t
+ * in band[j], the cell vectors whose every component is Q(f_t - q/2) or
+ * Q(f_t + q/2) (= floor(f_t/q) or floor(f_t/q) + 1); a candidate survives iff
+ * the quantised vector of each of its areas is in that area's set. */
+typedef struct {
+    int32_t n_areas;            /* 1..3 */
+    const int32_t *area_radii;  /* host [n_scales][n_areas]: star radius of area j at scale s,
+                                   2 <= area_radii[s][j] <= radii[s] (area 0 is normally radii[s]) */
+    int32_t band[3][2];         /* inclusive template central-radius band of each area, inside the
+                                   template's [t_min, r] */
+    scr_rat q[3];               /* quantisation factors (mean, std, contrast): 1 <= num <= 65536,
+                                   1 <= den <= 16 */
+} scr_joint;
+
+/* Write the candidate mask (layout as screen_features) of the joint membership
+ * screen.  p supplies radii and features (its tolerances are not used); the
+ * template must cover every band and carry SCR_F_GRAD when contrast is on.
+ * The sets are bit arrays over the cell ranges they span; SCR_EINVAL if they
+ * would exceed 2^26 bits (quantisation too fine for the spread of the band).
+ * Device memory for the sets comes from the context's pool.  Returns when the
+ * mask is written (it synchronises the stream: the host copy of the sets is
+ * released on return). */
+int screen_joint(scr_ctx *ctx, const scr_tables *t, const scr_tmpl *tm, const scr_params *p,
+                 const scr_joint *j, uint32_t *mask_dev, uint64_t mask_words, scr_stream stream);
+
 /* ---- a5: compaction ----------------------------------------------------- */
 
 /* Ascending keys (s << 48) | (y << 24) | x of the set bits of a mask laid out

@@ -64,6 +64,11 @@ class _BatchInfo(ctypes.Structure):
 
 _lib = None
 
+class _Joint(ctypes.Structure):
+    _fields_ = [("n_areas", ctypes.c_int32), ("area_radii", ctypes.POINTER(ctypes.c_int32)),
+                ("band", (ctypes.c_int32 * 2) * 3), ("q", _Rat * 3)]
+
+
 class _ServerConfig(ctypes.Structure):
     _fields_ = [("table_budget_bytes", ctypes.c_uint64), ("sum_bits", ctypes.c_int32), ("sq_bits", ctypes.c_int32),
                 ("mode", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("start_held", ctypes.c_int32),
@@ -113,6 +118,7 @@ def load(build_if_missing: bool = True):
         "template_release": ([vp, vp], None),
         "screen_bounds": ([vp, ctypes.POINTER(_Params), ctypes.POINTER(_Bounds)], ctypes.c_int),
         "screen_features": ([vp, vp, vp, ctypes.POINTER(_Params), vp, u64, vp], ctypes.c_int),
+        "screen_joint": ([vp, vp, vp, ctypes.POINTER(_Params), ctypes.POINTER(_Joint), vp, u64, vp], ctypes.c_int),
         "compact_mask": ([vp, vp, i32, i32, i32, vp, u64, vp, vp], ctypes.c_int),
         "compact_mask_noalloc": ([vp, i32, i32, i32, vp, u64, vp, vp], ctypes.c_int),
         "compact_mask_noalloc_error": ([], ctypes.c_char_p),
@@ -151,7 +157,8 @@ def load(build_if_missing: bool = True):
 def exported_symbols():
     return ["screen_init", "screen_shutdown", "screen_last_error", "screen_stats", "build_tables",
             "tables_view", "tables_copy_to_host", "tables_release", "template_features", "template_sums",
-            "template_release", "screen_bounds", "screen_features", "compact_mask", "compact_mask_noalloc",
+            "template_release", "screen_bounds", "screen_features", "screen_joint", "compact_mask",
+            "compact_mask_noalloc",
             "compact_mask_noalloc_error", "screen_positions",
             "screen_positions_async", "screen_host", "screen_batch_create", "screen_batch_run",
             "screen_batch_info", "screen_batch_release", "server_clock_ns", "server_create", "server_upload",
@@ -290,6 +297,23 @@ def mask_words(n_scales: int, H: int, W: int) -> int:
 def screen_features(ctx, tables, tm, params: Params, mask, stream=None) -> None:
     _check(load().screen_features(ctx, tables, tm, ctypes.byref(params.c), _ptr(mask), mask.numel(),
                                   _stream(stream)))
+
+
+def screen_joint(ctx, tables, tm, params: Params, area_radii, bands, q, mask, stream=None) -> None:
+    """Joint membership screen: area_radii [n_scales][n_areas] ints, bands
+    [(t_lo, t_hi)] per area, q (mean, std, contrast) quantisation factors."""
+    ar = np.ascontiguousarray(area_radii, dtype=np.int32)
+    n_areas = len(bands)
+    assert ar.shape == (params.n_scales, n_areas)
+    j = _Joint()
+    j.n_areas = n_areas
+    j.area_radii = ar.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    for k, (lo, hi) in enumerate(bands):
+        j.band[k][0], j.band[k][1] = int(lo), int(hi)
+    for k in range(3):
+        j.q[k] = _rat(q[k])
+    _check(load().screen_joint(ctx, tables, tm, ctypes.byref(params.c), ctypes.byref(j), _ptr(mask), mask.numel(),
+                               _stream(stream)))
 
 
 def compact_mask(ctx, mask, n_scales, H, W, lst, count, stream=None) -> None:

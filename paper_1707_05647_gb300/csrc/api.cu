@@ -15,6 +15,9 @@
 #include <string>
 #include <vector>
 
+#include <array>
+#include <cmath>
+
 #include "runtime.h"
 
 using namespace scr;
@@ -639,6 +642,201 @@ int screen_features(scr_ctx *c, const scr_tables *t, const scr_tmpl *tm, const s
     c->launches += n;
     CUDA_TRY(e);
     const_cast<scr_tables *>(t)->stream = (cudaStream_t)stream;
+    return SCR_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+uint64_t isqrt_u64(uint64_t z) {   // floor(sqrt(z)), exact
+    uint64_t w = (uint64_t)std::sqrt((long double)z);
+    while (w > 0 && w * w > z)
+        --w;
+    while ((w + 1) * (w + 1) <= z)
+        ++w;
+    return w;
+}
+
+// floor(f/q) of the template's central star of radius t for the enabled
+// features (mean, std, contrast order); exact (128-bit where needed)
+void template_cells(const scr_tmpl *tm, int t, uint32_t features, const scr_rat q[3], int64_t out[3]) {
+    const Geo g = geometry(t);
+    const i128 S = tm->S[t - tm->t_min], Q = tm->Q[t - tm->t_min], Si = tm->Si[t - tm->t_min];
+    int k = 0;
+    if (features & SCR_F_MEAN)
+        out[k++] = (int64_t)floor_div(S * q[0].den, (i128)g.A * q[0].num);
+    if (features & SCR_F_VAR) {
+        const i128 V = (i128)g.A * Q - S * S;
+        const uint64_t w = isqrt_u64((uint64_t)(V * q[1].den * q[1].den));
+        out[k++] = (int64_t)floor_div((i128)w, (i128)g.A * q[1].num);
+    }
+    if (features & SCR_F_GRAD) {
+        const i128 N = Si * g.Aring - (S - Si) * g.Ain;
+        out[k++] = (int64_t)floor_div(N * q[2].den, (i128)g.Ain * g.Aring * q[2].num);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int screen_joint(scr_ctx *c, const scr_tables *t, const scr_tmpl *tm, const scr_params *p, const scr_joint *jt,
+                 uint32_t *mask_dev, uint64_t mask_words, scr_stream stream) {
+    int rc;
+    if ((rc = check_ctx(c)) || (rc = check_screen_inputs(t, tm, p)))
+        return rc;
+    if (!jt || !mask_dev || jt->n_areas < 1 || jt->n_areas > 3 || !jt->area_radii)
+        return fail(SCR_EINVAL, "joint screen needs 1..3 areas, their radii and a mask");
+    const uint32_t feats = p->features & 7u;
+    if (!feats)
+        return fail(SCR_EINVAL, "no feature enabled");
+    const int S = p->n_scales, NA = jt->n_areas;
+    const uint64_t need = (uint64_t)S * t->H * ((t->W + 31) / 32);
+    if (mask_words < need)
+        return fail(SCR_EINVAL, "mask has %llu words, needs %llu", (unsigned long long)mask_words,
+                    (unsigned long long)need);
+    for (int k = 0; k < 3; ++k)
+        if (jt->q[k].num < 1 || jt->q[k].num > 65536 || jt->q[k].den < 1 || jt->q[k].den > 16)
+            return fail(SCR_EINVAL, "q[%d] = %lld/%lld: need 1 <= num <= 65536, 1 <= den <= 16", k,
+                        (long long)jt->q[k].num, (long long)jt->q[k].den);
+    for (int j = 0; j < NA; ++j)
+        if (jt->band[j][0] > jt->band[j][1] || jt->band[j][0] < tm->t_min || jt->band[j][1] > tm->r ||
+            jt->band[j][0] < 2)
+            return fail(SCR_EINVAL, "band %d [%d, %d] outside the template's central radii [%d, %d]", j,
+                        jt->band[j][0], jt->band[j][1], std::max(tm->t_min, 2), tm->r);
+    for (int s = 0; s < S; ++s)
+        for (int j = 0; j < NA; ++j) {
+            const int rho = jt->area_radii[s * NA + j];
+            if (rho < 2 || rho > p->radii[s])
+                return fail(SCR_EINVAL, "area radius %d at scale %d, area %d: need 2 <= radius <= %d", rho, s, j,
+                            p->radii[s]);
+        }
+    // membership sets: bit arrays over the cell ranges each area's band spans
+    const int nf = __builtin_popcount(feats);
+    std::vector<JointSet> sets(NA);
+    std::vector<uint32_t> bits;
+    uint64_t nbits = 0;
+    for (int j = 0; j < NA; ++j) {
+        std::vector<std::array<int64_t, 3>> base;
+        int64_t lo[3] = {INT64_MAX, INT64_MAX, INT64_MAX}, hi[3] = {INT64_MIN, INT64_MIN, INT64_MIN};
+        for (int tt = jt->band[j][0]; tt <= jt->band[j][1]; ++tt) {
+            std::array<int64_t, 3> cb = {0, 0, 0};
+            template_cells(tm, tt, feats, jt->q, cb.data());
+            for (int k = 0; k < nf; ++k) {
+                lo[k] = std::min(lo[k], cb[k]);
+                hi[k] = std::max(hi[k], cb[k] + 1);
+            }
+            base.push_back(cb);
+        }
+        JointSet &st = sets[j];
+        uint64_t total = 1;
+        for (int k = 0; k < 3; ++k) {
+            st.cmin[k] = 0;
+            st.dim[k] = 1;
+            if (k < nf) {
+                if (hi[k] - lo[k] + 1 > (1 << 26) || lo[k] < INT32_MIN || lo[k] > INT32_MAX)
+                    return fail(SCR_EINVAL, "area %d: quantisation too fine for the spread of its band", j);
+                st.cmin[k] = (int32_t)lo[k];
+                st.dim[k] = (uint32_t)(hi[k] - lo[k] + 1);
+                total *= st.dim[k];
+            }
+        }
+        if (total > (1ull << 26) || nbits + total > (1ull << 28))
+            return fail(SCR_EINVAL, "area %d: its membership array would hold %llu bits (at most 2^26)", j,
+                        (unsigned long long)total);
+        st.bit0 = nbits;
+        nbits += (total + 31) & ~uint64_t(31);
+        bits.resize((size_t)(nbits / 32), 0u);
+        for (const auto &cb : base)
+            for (int m = 0; m < (1 << nf); ++m) {
+                uint64_t idx = 0, stride = 1;
+                for (int k = 0; k < nf; ++k) {
+                    idx += (uint64_t)(cb[k] + ((m >> k) & 1) - st.cmin[k]) * stride;
+                    stride *= st.dim[k];
+                }
+                const uint64_t b = st.bit0 + idx;
+                bits[b >> 5] |= 1u << (b & 31);
+            }
+    }
+    // per scale and area: star corner offsets for this pitch
+    const int64_t P = t->t[0].pitch;
+    std::vector<JointScale> scales(S);
+    std::vector<JointArea> areas((size_t)S * NA);
+    for (int s = 0; s < S; ++s) {
+        const Geo g = geometry(p->radii[s]);
+        JointScale &sc = scales[s];
+        memset(&sc, 0, sizeof sc);
+        sc.y_lo = std::max(g.n, g.h) - 1;
+        sc.y_hi = t->H - 1 - std::max(g.n, g.h);
+        sc.x_lo = std::max(g.n, g.h) - 1;
+        sc.x_hi = std::min(t->W - 1 - g.n, t->W - g.h);
+        sc.empty = (sc.x_hi < sc.x_lo || sc.y_hi < sc.y_lo) ? 1u : 0u;
+        for (int j = 0; j < NA; ++j) {
+            const Geo ga = geometry(jt->area_radii[s * NA + j]);
+            JointArea &ar = areas[(size_t)s * NA + j];
+            memset(&ar, 0, sizeof ar);
+            const int64_t n = ga.n, h = ga.h, ni = ga.ni, hi = ga.hi;
+            const int64_t oL[4] = {(n + 1) * P + (n + 1), (1 - n) * P + (n + 1), (n + 1) * P + (1 - n),
+                                   (1 - n) * P + (1 - n)};
+            const int64_t oT[4] = {(h + 1) * P + 1, P + (1 - h), P + (h + 1), (1 - h) * P + 1};
+            const int64_t oLi[4] = {(ni + 1) * P + (ni + 1), (1 - ni) * P + (ni + 1), (ni + 1) * P + (1 - ni),
+                                    (1 - ni) * P + (1 - ni)};
+            const int64_t oTi[4] = {(hi + 1) * P + 1, P + (1 - hi), P + (hi + 1), (1 - hi) * P + 1};
+            for (int k = 0; k < 4; ++k) {
+                ar.oL[k] = (int32_t)oL[k];
+                ar.oT[k] = (int32_t)oT[k];
+                ar.oLi[k] = (int32_t)oLi[k];
+                ar.oTi[k] = (int32_t)oTi[k];
+            }
+            ar.A = (uint32_t)ga.A;
+            ar.Ain = (uint32_t)ga.Ain;
+            ar.Aring = (uint32_t)ga.Aring;
+        }
+    }
+    // one device buffer: scales | areas | sets | bits
+    const size_t o_areas = (S * sizeof(JointScale) + 255) & ~size_t(255);
+    const size_t o_sets = o_areas + ((areas.size() * sizeof(JointArea) + 255) & ~size_t(255));
+    const size_t o_bits = o_sets + ((sets.size() * sizeof(JointSet) + 255) & ~size_t(255));
+    const size_t total = o_bits + bits.size() * 4 + 4;
+    std::vector<char> host(total, 0);
+    memcpy(host.data(), scales.data(), S * sizeof(JointScale));
+    memcpy(host.data() + o_areas, areas.data(), areas.size() * sizeof(JointArea));
+    memcpy(host.data() + o_sets, sets.data(), sets.size() * sizeof(JointSet));
+    memcpy(host.data() + o_bits, bits.data(), bits.size() * 4);
+    DeviceGuard dg(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    Scoped buf(c, st);
+    if ((rc = buf.take(total)))
+        return rc;
+    CUDA_TRY(cudaMemcpyAsync(buf.p, host.data(), total, cudaMemcpyHostToDevice, st));
+    JointArgs a;
+    memset(&a, 0, sizeof a);
+    a.L1 = t->t[0].lo;
+    a.L2 = t->t[1].lo;
+    a.T1 = t->t[2].lo;
+    a.T2 = t->t[3].lo;
+    a.pitch = P;
+    a.H = t->H;
+    a.W = t->W;
+    a.Wwords = (t->W + 31) / 32;
+    a.n_scales = S;
+    a.n_areas = NA;
+    a.features = feats;
+    for (int k = 0; k < 3; ++k) {
+        a.qn[k] = (uint64_t)jt->q[k].num;
+        a.qd[k] = (uint64_t)jt->q[k].den;
+    }
+    a.scales = (const JointScale *)buf.p;
+    a.areas = (const JointArea *)((char *)buf.p + o_areas);
+    a.sets = (const JointSet *)((char *)buf.p + o_sets);
+    a.bits = (const uint32_t *)((char *)buf.p + o_bits);
+    a.mask = mask_dev;
+    uint64_t n = 0;
+    cudaError_t e = launch_screen_joint(a, st, &n);
+    c->launches += n;
+    CUDA_TRY(e);
+    CUDA_TRY(cudaStreamSynchronize(st));   // the host copy of the sets must outlive the upload
     return SCR_OK;
 }
 

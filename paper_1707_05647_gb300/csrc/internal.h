@@ -120,6 +120,34 @@ cudaError_t launch_template_sums(const TableDesc &L1, const TableDesc &L2, const
 
 cudaError_t launch_screen(const ScreenArgs &args, cudaStream_t st, uint64_t *launches);
 
+// Joint-vector membership screen (joint.cu).
+struct JointScale {                   // per scale: valid rectangle of the outermost area
+    int32_t y_lo, y_hi, x_lo, x_hi;
+    uint32_t empty, pad[3];
+};
+struct JointArea {                    // per (scale, area): corner offsets and areas of its star
+    int32_t oL[4], oT[4], oLi[4], oTi[4];
+    uint32_t A, Ain, Aring, pad;
+};
+struct JointSet {                     // per area: the membership bit array over cell vectors
+    uint64_t bit0;                    // first bit in the shared bit array
+    int32_t cmin[3];                  // lowest cell of each enabled feature (in mean, std, contrast order)
+    uint32_t dim[3];                  // cells per enabled feature (index = sum (c - cmin) * stride)
+};
+struct JointArgs {
+    const uint32_t *L1, *L2, *T1, *T2;   // low planes
+    int64_t pitch;
+    int32_t H, W, Wwords, n_scales, n_areas;
+    uint32_t features;
+    uint64_t qn[3], qd[3];                // quantisation factors q = qn / qd: mean, std, contrast
+    const JointScale *scales;             // [n_scales]
+    const JointArea *areas;               // [n_scales][n_areas]
+    const JointSet *sets;                 // [n_areas]
+    const uint32_t *bits;
+    uint32_t *mask;
+};
+cudaError_t launch_screen_joint(const JointArgs &a, cudaStream_t st, uint64_t *launches);
+
 // One mask in a buffer of several (segmented compaction): S planes of H rows of
 // Wwords words starting at word0, a multiple of kCompactChunk; the words up to
 // the next chunk boundary are zero.  Its first `cap` keys go to out[out0 ..].

@@ -413,3 +413,18 @@ def serve_workload(seed: int = BASE_SEED + 4, duration: float = 2.0, rate: float
             events.append(ServeEvent(t, "screen", int(rng.integers(0, n_up)), int(rng.integers(0, n_templates)),
                                      feats))
     return ServeWorkload(pool, templates, warm, events, Tolerances(), rate, duration, table_budget)
+
+
+def joint_areas(r: int, scales: list[float], n_areas: int):
+    """Nested central areas for the joint membership screen: at scale s the
+    star radii of areas j = 0..n_areas-1 are floor(R_s / lambda^j + 1/2)
+    (area 0 is R_s itself), and area j's band of template central radii is
+    [ceil(r / lambda^(j+1)), floor(r / lambda^j)], lambda the ratio of
+    consecutive scales (area 0's band is [t_min, r]).  A single scale uses
+    lambda = 2^(1/4)."""
+    lam = scales[1] / scales[0] if len(scales) > 1 else 2 ** 0.25
+    radii = radii_for(r, scales)
+    area_radii = [[int(math.floor(R / lam ** j + 0.5)) for j in range(n_areas)] for R in radii]
+    bands = [(int(math.ceil(r / lam ** (j + 1) - 1e-9)), int(math.floor(r / lam ** j + 1e-9)))
+             for j in range(n_areas)]
+    return area_radii, bands
