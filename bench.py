@@ -413,6 +413,68 @@ def run_batched(args):
     scr.screen_shutdown(ctx)
 
 
+def run_joint(args):
+    """The joint-vector membership screen (three nested central areas, q = 4, 2,
+    4 grey levels) on the 4096^2 workload, beside the interval screen on the
+    same tables: device time per screen with CUDA events, survivors of each."""
+    import torch
+    import synth
+    from fractions import Fraction
+    import paper_1707_05647_gb300 as scr
+
+    torch.cuda.set_device(0)
+    wl = synth.config2()
+    H, W = wl.image.shape
+    S = len(wl.radii)
+    area_radii, bands = synth.joint_areas(wl.r, wl.scales, 3)
+    t_min = max(2, min(b[0] for b in bands))
+    q = (Fraction(4), Fraction(2), Fraction(4))
+    ctx = scr.screen_init(0, 0)
+    st = torch.cuda.current_stream()
+    tab = scr.build_tables(ctx, torch.from_numpy(wl.image).cuda(), wl.sum_bits, wl.sq_bits, st)
+    tm = scr.template_features(ctx, wl.template, wl.r, t_min, wl.features)
+    pj = scr.Params(wl.radii, wl.features)
+    pi = scr.Params(wl.radii, wl.features, wl.tol.mean_rel, wl.tol.std_rel, wl.tol.grad_rel, wl.tol.grad_abs)
+    tmi = scr.template_features(ctx, wl.template, wl.r, wl.t_min, wl.features)
+    mask = torch.empty(scr.mask_words(S, H, W), dtype=torch.int32, device="cuda")
+    lst = torch.empty(1 << 24, dtype=torch.int64, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.steps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / args.steps
+
+    joint_s = timed(lambda: scr.screen_joint(ctx, tab, tm, pj, area_radii, bands, q, mask, st))
+    scr.compact_mask(ctx, mask, S, H, W, lst, cnt, st)
+    torch.cuda.synchronize()
+    n_joint = int(cnt.item())
+    py, px = wl.planted
+    m = mask.cpu().numpy().view(np.uint32).reshape(S, H, (W + 31) // 32)
+    planted = any((int(m[s, py, px >> 5]) >> (px & 31)) & 1 for s in range(S))
+    int_s = timed(lambda: scr.screen_features(ctx, tab, tmi, pi, mask, st))
+    scr.compact_mask(ctx, mask, S, H, W, lst, cnt, st)
+    torch.cuda.synchronize()
+    n_int = int(cnt.item())
+    cand = 127458510
+    print(json.dumps({
+        "metric": "candidate (position x scale) evaluations/s", "workload":
+            "joint membership: 4096x4096, r 48, 8 scales, 3 nested central areas, q = (4, 2, 4) grey levels",
+        "value": cand / joint_s, "unit": "evals/s", "ms_per_screen": 1e3 * joint_s, "steps": args.steps,
+        "survivors": n_joint, "pruned": 1 - n_joint / cand, "planted_survives": bool(planted),
+        "interval_screen": {"ms_per_screen": 1e3 * int_s, "value": cand / int_s, "survivors": n_int,
+                            "pruned": 1 - n_int / cand},
+        "data": "synthetic"}), flush=True)
+    scr.screen_shutdown(ctx)
+
+
 def run_serve(args):
     """Configuration 5: replay one seeded Poisson stream of uploads and screens
     through the serving loop, batched (continuous batching) and plain (one
@@ -613,7 +675,7 @@ def main():
     ap.add_argument("--size", type=int, default=4096,
                     help="crop the 4096x4096 image to size x size (smaller ncu captures)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "serve"])
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "serve", "joint"])
     ap.add_argument("--duration", type=float, default=2.0, help="seconds of arrivals (serve workload)")
     ap.add_argument("--rates", default="2000,8000,16000",
                     help="arrival rates (req/s) of the serve workload; the first is the headline")
@@ -622,6 +684,9 @@ def main():
     args = ap.parse_args()
     if args.workload == "serve":
         run_serve(args)
+        return
+    if args.workload == "joint":
+        run_joint(args)
         return
     if args.workload == "batched":
         run_batched(args)

@@ -792,6 +792,26 @@ int screen_joint(scr_ctx *c, const scr_tables *t, const scr_tmpl *tm, const scr_
             ar.A = (uint32_t)ga.A;
             ar.Ain = (uint32_t)ga.Ain;
             ar.Aring = (uint32_t)ga.Aring;
+            // the sums S whose mean cell floor((2 S qd + A qn) / (2 A qn)) lies in
+            // [cmin, cmin + dim - 1]: S >= ceil(A qn (2 cmin - 1) / (2 qd)) and
+            // S <= ceil(A qn (2 cmax + 1) / (2 qd)) - 1 (the cell grows with S)
+            ar.S_lo = 0;
+            ar.S_rng = UINT32_MAX;
+            if (feats & SCR_F_MEAN) {
+                const i128 Aq = (i128)ga.A * jt->q[0].num, d2 = 2 * (i128)jt->q[0].den;
+                const i128 cmin = sets[j].cmin[0], cmax = cmin + sets[j].dim[0] - 1;
+                const i128 lo = std::max<i128>(ceil_div(Aq * (2 * cmin - 1), d2), 0);
+                const i128 hi = std::min<i128>(ceil_div(Aq * (2 * cmax + 1), d2) - 1, (i128)UINT32_MAX);
+                if (lo > hi) {
+                    ar.S_lo = 1;   // no sum qualifies
+                    ar.S_rng = 0;
+                } else {
+                    ar.S_lo = (uint32_t)lo;
+                    ar.S_rng = (uint32_t)(hi - lo);
+                }
+                if (lo > hi)
+                    sc.empty = 1u;   // this area rejects every candidate of the scale
+            }
         }
     }
     // one device buffer: scales | areas | sets | bits

@@ -128,6 +128,7 @@ struct JointScale {                   // per scale: valid rectangle of the outer
 struct JointArea {                    // per (scale, area): corner offsets and areas of its star
     int32_t oL[4], oT[4], oLi[4], oTi[4];
     uint32_t A, Ain, Aring, pad;
+    uint32_t S_lo, S_rng;             // star sums whose mean cell lies in the set's range
 };
 struct JointSet {                     // per area: the membership bit array over cell vectors
     uint64_t bit0;                    // first bit in the shared bit array

@@ -49,6 +49,8 @@ __device__ __forceinline__ int64_t floor_div(int64_t a, int64_t b) {   // b > 0
 __device__ __forceinline__ bool member(const JointArgs &a, const JointArea &ar, const JointSet &st, int64_t e) {
     const uint32_t *L1 = a.L1 + e, *T1 = a.T1 + e;
     const uint32_t S = sum8(L1, T1, ar.oL, ar.oT);
+    if (S - ar.S_lo > ar.S_rng)   // its mean cell is outside the set's range (exact)
+        return false;
     const uint64_t A = ar.A;
     uint64_t idx = 0, stride = 1;
     int k = 0;
