@@ -72,7 +72,7 @@ enum {
     SCR_EUNSUPPORTED = -8 /* valid request outside what this build implements */
 };
 
-enum { SCR_F_MEAN = 1, SCR_F_VAR = 2, SCR_F_GRAD = 4 };
+enum { SCR_F_MEAN = 1, SCR_F_VAR = 2, SCR_F_GRAD = 4, SCR_F_PREWITT = 8 };
 
 /* Exact rational num/den, den > 0, |num| and den <= 2^20. */
 typedef struct {
@@ -88,12 +88,21 @@ typedef struct {
  *     std      sqrt(V)/A in [(1-ts) sd_lo, (1+ts) sd_hi]         (compared squared)
  *     contrast N/(A_in A_ring) in [g_lo - tg|g_lo| - dg, g_hi + tg|g_hi| + dg]
  *   where [mu_lo, mu_hi], ... are the template's feature hulls over its central
- *   radii t in [t_min, r] (Sec. 5, Eq. F_n; see template_features). */
+ *   radii t in [t_min, r] (Sec. 5, Eq. F_n; see template_features).
+ *   prewitt_rel tp (in [0, 1)), prewitt_abs dp (>= 0), used with SCR_F_PREWITT:
+ *     the Prewitt gradient of the star's 2n x 2n square (Sec. 3, Eq. S_y and
+ *     Eq. T_x; magnitude of Sec. 4) about the square's centre (y + 1/2, x + 1/2),
+ *     Gx2 = sum (2x' - 2x - 1) I, Gy2 = sum (2y' - 2y - 1) I, J2 = (2n)^2 (4n^2 - 1)/3,
+ *     phi^2 = 4 n^2 (Gx2^2 + Gy2^2) / J2^2 (slope times half-side, squared), and
+ *     phi^2 in [max(0, (1-tp)^2 p_lo - dp^2), (1+tp)^2 p_hi + dp^2] with [p_lo, p_hi]
+ *     the hull of the template's central squares' phi^2.  Needs moment tables
+ *     (build_moment_tables) and a template computed with SCR_F_PREWITT. */
 typedef struct {
     int32_t n_scales;
     const int32_t *radii;
     uint32_t features;
     scr_rat mean_rel, std_rel, grad_rel, grad_abs;
+    scr_rat prewitt_rel, prewitt_abs;
 } scr_params;
 
 /* Inclusive integer bounds of one scale (INT64_MIN / INT64_MAX when the
@@ -152,7 +161,8 @@ int tables_view(const scr_tables *t, int which, const void **dev_ptr, int64_t *r
                 int32_t *bits);
 
 /* Copy table `which` into a dense rows x cols uint64 host array (values zero-
- * extended from 32-bit tables).  Synchronous. */
+ * extended from 32-bit tables); which 4 and 5 are the moment tables Mx and My
+ * ((H + 1) x (W + 1), after build_moment_tables).  Synchronous. */
 int tables_copy_to_host(scr_ctx *ctx, const scr_tables *t, int which, uint64_t *dst_host);
 
 void tables_release(scr_ctx *ctx, scr_tables *t);
@@ -163,7 +173,9 @@ void tables_release(scr_ctx *ctx, scr_tables *t);
  * 2 <= r <= 181): star sums S_t, Q_t, S_in,t of the central star of radius t at
  * the template centre (r, r) for every t in [t_min, r] (t_min >= 2 when
  * SCR_F_GRAD is used), and the hulls of mean, variance and contrast over t.
- * Computed on the device with the same table kernels; synchronous. */
+ * Computed on the device with the same table kernels; synchronous.  With
+ * SCR_F_PREWITT also the doubled Prewitt moments of each central square and the
+ * hull of their phi^2 (see scr_params), summed on the host from the pixels. */
 int template_features(scr_ctx *ctx, const uint8_t *tmpl_host, int32_t side, int32_t r,
                       int32_t t_min, uint32_t features, scr_tmpl **out);
 
@@ -175,6 +187,14 @@ void template_release(scr_ctx *ctx, scr_tmpl *tm);
 /* Per-scale inclusive integer bounds (host computation, exact 128-bit
  * rationals).  out has p->n_scales entries. */
 int screen_bounds(const scr_tmpl *tm, const scr_params *p, scr_bounds *out);
+
+/* Add the moment tables of the Prewitt gradient to t: Mx(a, b) = sum_{y<a, x<b}
+ * x I and My(a, b) = sum_{y<a, x<b} y I (Sec. 3, Eq. T_x), 64-bit, same rows,
+ * pitch and column offset as the upright tables; img_dev is the image the
+ * tables were built from.  Charged to the HBM budget; freed with the tables.
+ * Stream-ordered. */
+int build_moment_tables(scr_ctx *ctx, const uint8_t *img_dev, int32_t H, int32_t W, int64_t pitch,
+                        scr_tables *t, scr_stream stream);
 
 /* ---- a3, a4: features and threshold ------------------------------------ */
 

@@ -16,7 +16,7 @@ import numpy as np
 
 from . import _build
 
-F_MEAN, F_VAR, F_GRAD = 1, 2, 4
+F_MEAN, F_VAR, F_GRAD, F_PREWITT = 1, 2, 4, 8
 SCR_OK, SCR_EINVAL, SCR_ENOMEM, SCR_EBUDGET, SCR_ECUDA, SCR_ETIMEOUT, SCR_EOVERFLOW = 0, -1, -2, -3, -4, -5, -6
 SCR_EEVICTED, SCR_EUNSUPPORTED = -7, -8
 SERVE_BATCHED, SERVE_PLAIN = 0, 1
@@ -36,7 +36,7 @@ class _Rat(ctypes.Structure):
 class _Params(ctypes.Structure):
     _fields_ = [("n_scales", ctypes.c_int32), ("radii", ctypes.POINTER(ctypes.c_int32)),
                 ("features", ctypes.c_uint32), ("mean_rel", _Rat), ("std_rel", _Rat),
-                ("grad_rel", _Rat), ("grad_abs", _Rat)]
+                ("grad_rel", _Rat), ("grad_abs", _Rat), ("prewitt_rel", _Rat), ("prewitt_abs", _Rat)]
 
 
 class _Bounds(ctypes.Structure):
@@ -112,6 +112,7 @@ def load(build_if_missing: bool = True):
         "build_tables": ([vp, vp, i32, i32, i64, i32, i32, vp, pp], ctypes.c_int),
         "tables_view": ([vp, ctypes.c_int, pp] + [ctypes.POINTER(i64)] * 5 + [ctypes.POINTER(i32)], ctypes.c_int),
         "tables_copy_to_host": ([vp, vp, ctypes.c_int, vp], ctypes.c_int),
+        "build_moment_tables": ([vp, vp, i32, i32, i64, vp, vp], ctypes.c_int),
         "tables_release": ([vp, vp], None),
         "template_features": ([vp, vp, i32, i32, i32, u32, pp], ctypes.c_int),
         "template_sums": ([vp, i32, ctypes.POINTER(i64)], ctypes.c_int),
@@ -156,7 +157,8 @@ def load(build_if_missing: bool = True):
 
 def exported_symbols():
     return ["screen_init", "screen_shutdown", "screen_last_error", "screen_stats", "build_tables",
-            "tables_view", "tables_copy_to_host", "tables_release", "template_features", "template_sums",
+            "tables_view", "tables_copy_to_host", "build_moment_tables", "tables_release", "template_features",
+            "template_sums",
             "template_release", "screen_bounds", "screen_features", "screen_joint", "compact_mask",
             "compact_mask_noalloc",
             "compact_mask_noalloc_error", "screen_positions",
@@ -199,10 +201,12 @@ class Params:
     """scr_params: radii per scale, feature bits and the four tolerances."""
 
     def __init__(self, radii, features, mean_rel=Fraction(1, 20), std_rel=Fraction(1, 10),
-                 grad_rel=Fraction(1, 10), grad_abs=Fraction(4)):
+                 grad_rel=Fraction(1, 10), grad_abs=Fraction(4), prewitt_rel=Fraction(1, 10),
+                 prewitt_abs=Fraction(2)):
         self.radii = np.ascontiguousarray(radii, dtype=np.int32)
         self.c = _Params(len(self.radii), self.radii.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                         int(features), _rat(mean_rel), _rat(std_rel), _rat(grad_rel), _rat(grad_abs))
+                         int(features), _rat(mean_rel), _rat(std_rel), _rat(grad_rel), _rat(grad_abs),
+                         _rat(prewitt_rel), _rat(prewitt_abs))
 
     @property
     def n_scales(self):
@@ -252,7 +256,19 @@ def tables_view(tables, which: int) -> dict:
                 plane_stride=v[4].value, bits=bits.value)
 
 
+def build_moment_tables(ctx, tables, img, stream=None) -> None:
+    """Add the Prewitt moment tables to `tables` (img: the same 2-D uint8 CUDA tensor)."""
+    H, W = img.shape
+    _check(load().build_moment_tables(ctx, _ptr(img), H, W, img.stride(0), tables, _stream(stream)))
+
+
 def tables_copy_to_host(ctx, tables, which: int) -> np.ndarray:
+    """which 0..3: L1, L2, T1, T2; 4, 5: the moment tables Mx, My ((H+1) x (W+1))."""
+    if which >= 4:
+        v = tables_view(tables, 0)            # the upright table's (H + 1) x (W + 1)
+        out = np.empty((v["rows"], v["cols"]), np.uint64)
+        _check(load().tables_copy_to_host(ctx, tables, which, _ptr(out)))
+        return out
     v = tables_view(tables, which)
     out = np.empty((v["rows"], v["cols"]), np.uint64)
     _check(load().tables_copy_to_host(ctx, tables, which, _ptr(out)))

@@ -11,7 +11,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libscreen.so")
-SOURCES = ["api.cu", "tables.cu", "features.cu", "compact.cu", "batch.cu", "serve.cu", "joint.cu"]
+SOURCES = ["api.cu", "tables.cu", "features.cu", "compact.cu", "batch.cu", "serve.cu", "joint.cu", "moments.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", "-diag-suppress", "68"]

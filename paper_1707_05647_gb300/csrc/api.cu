@@ -131,7 +131,7 @@ int validate_params(const scr_params *p) {
         return fail(SCR_EINVAL, "null params");
     if (p->n_scales < 1 || p->n_scales > kMaxScales || !p->radii)
         return fail(SCR_EINVAL, "n_scales must be in [1, %d] with a radii array", kMaxScales);
-    if (p->features & ~7u)
+    if (p->features & ~15u)
         return fail(SCR_EINVAL, "unknown feature bits 0x%x", p->features);
     for (int s = 0; s < p->n_scales; ++s) {
         const int R = p->radii[s];
@@ -141,6 +141,9 @@ int validate_params(const scr_params *p) {
     int rc;
     if ((rc = check_rat(p->mean_rel, true, "mean_rel")) || (rc = check_rat(p->std_rel, true, "std_rel")) ||
         (rc = check_rat(p->grad_rel, true, "grad_rel")) || (rc = check_rat(p->grad_abs, false, "grad_abs")))
+        return rc;
+    if ((p->features & SCR_F_PREWITT) &&
+        ((rc = check_rat(p->prewitt_rel, true, "prewitt_rel")) || (rc = check_rat(p->prewitt_abs, false, "prewitt_abs"))))
         return rc;
     return SCR_OK;
 }
@@ -258,7 +261,168 @@ int run_build(scr_ctx *c, const uint8_t *img, int H, int W, int64_t pitch, scr_t
 
 void free_tables(scr_ctx *c, scr_tables *t) {
     dev_free(c, t->base, t->bytes, t->stream);
+    if (t->mom)
+        dev_free(c, t->mom, t->mom_bytes, t->stream);
     delete t;
+}
+
+// ---- exact wide integers for the Prewitt bounds ----------------------------
+// Non-negative integers as base-2^32 limbs (little end first): enough for the
+// products of the Prewitt bound rationals, which outgrow 128 bits.
+struct Big {
+    std::vector<uint32_t> d;
+    Big() {}
+    explicit Big(unsigned __int128 v) {
+        while (v) {
+            d.push_back((uint32_t)v);
+            v >>= 32;
+        }
+    }
+};
+
+int big_cmp(const Big &a, const Big &b) {
+    if (a.d.size() != b.d.size())
+        return a.d.size() < b.d.size() ? -1 : 1;
+    for (size_t i = a.d.size(); i-- > 0;)
+        if (a.d[i] != b.d[i])
+            return a.d[i] < b.d[i] ? -1 : 1;
+    return 0;
+}
+
+void big_trim(Big &a) {
+    while (!a.d.empty() && a.d.back() == 0)
+        a.d.pop_back();
+}
+
+Big big_mul(const Big &a, const Big &b) {
+    Big r;
+    if (a.d.empty() || b.d.empty())
+        return r;
+    r.d.assign(a.d.size() + b.d.size(), 0);
+    for (size_t i = 0; i < a.d.size(); ++i) {
+        uint64_t carry = 0;
+        for (size_t j = 0; j < b.d.size(); ++j) {
+            const uint64_t cur = (uint64_t)a.d[i] * b.d[j] + r.d[i + j] + carry;
+            r.d[i + j] = (uint32_t)cur;
+            carry = cur >> 32;
+        }
+        size_t k = i + b.d.size();
+        while (carry) {
+            const uint64_t cur = (uint64_t)r.d[k] + carry;
+            r.d[k++] = (uint32_t)cur;
+            carry = cur >> 32;
+        }
+    }
+    big_trim(r);
+    return r;
+}
+
+Big big_add(const Big &a, const Big &b) {
+    Big r;
+    uint64_t carry = 0;
+    for (size_t i = 0; i < std::max(a.d.size(), b.d.size()) || carry; ++i) {
+        const uint64_t cur = carry + (i < a.d.size() ? a.d[i] : 0) + (i < b.d.size() ? b.d[i] : 0);
+        r.d.push_back((uint32_t)cur);
+        carry = cur >> 32;
+    }
+    big_trim(r);
+    return r;
+}
+
+Big big_sub(const Big &a, const Big &b) {   // a >= b
+    Big r = a;
+    int64_t borrow = 0;
+    for (size_t i = 0; i < r.d.size(); ++i) {
+        int64_t cur = (int64_t)r.d[i] - borrow - (i < b.d.size() ? (int64_t)b.d[i] : 0);
+        borrow = cur < 0;
+        if (cur < 0)
+            cur += (int64_t)1 << 32;
+        r.d[i] = (uint32_t)cur;
+    }
+    big_trim(r);
+    return r;
+}
+
+size_t big_bits(const Big &a) {
+    if (a.d.empty())
+        return 0;
+    return 32 * (a.d.size() - 1) + (32 - __builtin_clz(a.d.back()));
+}
+
+bool big_bit(const Big &a, size_t i) { return (a.d[i / 32] >> (i % 32)) & 1u; }
+
+// floor(a / b) (b > 0) by shift and subtract; also whether the division was exact
+Big big_div(const Big &a, const Big &b, bool *exact) {
+    Big q, r;
+    const size_t n = big_bits(a);
+    q.d.assign((n + 31) / 32 + 1, 0);
+    for (size_t i = n; i-- > 0;) {
+        r = big_add(r, r);
+        if (big_bit(a, i))
+            r = big_add(r, Big(1));
+        if (big_cmp(r, b) >= 0) {
+            r = big_sub(r, b);
+            q.d[i / 32] |= 1u << (i % 32);
+        }
+    }
+    big_trim(q);
+    if (exact)
+        *exact = r.d.empty();
+    return q;
+}
+
+unsigned __int128 big_u128_sat(const Big &a) {
+    if (a.d.size() > 4)
+        return ~(unsigned __int128)0;
+    unsigned __int128 v = 0;
+    for (size_t i = a.d.size(); i-- > 0;)
+        v = (v << 32) | a.d[i];
+    return v;
+}
+
+// doubled Prewitt normaliser of a 2n x 2n square: sum (2x' - 2x - 1)^2 = (2n)^2 (4n^2 - 1) / 3
+uint64_t prewitt_j2(int64_t n) { return (uint64_t)((2 * n) * (2 * n) * (4 * n * n - 1) / 3); }
+
+// Inclusive bounds on Gx2^2 + Gy2^2 at star radius R (scr_params: phi^2 in
+// [max(0, (1-tp)^2 p_lo - dp^2), (1+tp)^2 p_hi + dp^2], phi^2 = 4 n^2 G2 / J2^2),
+// exact: L = ceil(lo J2^2 / (4 n^2)), U = floor(hi J2^2 / (4 n^2)), U saturated.
+void prewitt_bounds(const scr_tmpl *tm, const scr_params *p, int R, unsigned __int128 *L, unsigned __int128 *U) {
+    const int64_t n = geometry(R).n;
+    const Big J2(prewitt_j2(n)), J2sq = big_mul(J2, J2);
+    const uint64_t tn = (uint64_t)p->prewitt_rel.num, td = (uint64_t)p->prewitt_rel.den;
+    const uint64_t dn = (uint64_t)p->prewitt_abs.num, dd = (uint64_t)p->prewitt_abs.den;
+    // lo = ((td - tn)^2 A_lo dd^2 - dn^2 td^2 B_lo) / (td^2 B_lo dd^2); hi likewise with +
+    auto part = [&](unsigned __int128 A, unsigned __int128 B, uint64_t tf, bool minus, Big *num, Big *den, bool *neg) {
+        const Big a = big_mul(big_mul(Big(A), Big((unsigned __int128)tf * tf)), Big((unsigned __int128)dd * dd));
+        const Big b = big_mul(Big((unsigned __int128)dn * dn * td * td), Big(B));
+        *neg = false;
+        if (minus) {
+            if (big_cmp(a, b) <= 0) {
+                *neg = true;
+                *num = Big();
+            } else {
+                *num = big_sub(a, b);
+            }
+        } else {
+            *num = big_add(a, b);
+        }
+        *den = big_mul(big_mul(Big((unsigned __int128)td * td), Big(B)), Big((unsigned __int128)dd * dd));
+    };
+    Big num, den;
+    bool neg;
+    part(tm->p_lo_n, tm->p_lo_d, td - tn, true, &num, &den, &neg);
+    const Big fden = big_mul(den, Big((unsigned __int128)(4 * n * n)));
+    if (neg) {
+        *L = 0;
+    } else {
+        bool exact = false;
+        Big q = big_div(big_mul(num, J2sq), fden, &exact);
+        if (!exact)
+            q = big_add(q, Big(1));
+        *L = big_u128_sat(q);
+    }
+    part(tm->p_hi_n, tm->p_hi_d, td + tn, false, &num, &den, &neg);
+    *U = big_u128_sat(big_div(big_mul(num, J2sq), big_mul(den, Big((unsigned __int128)(4 * n * n))), nullptr));
 }
 
 int fill_screen_args(const scr_tables *t, const scr_tmpl *tm, const scr_params *p, ScreenArgs *a) {
@@ -324,7 +488,21 @@ int fill_screen_args(const scr_tables *t, const scr_tmpl *tm, const scr_params *
             sp.N_lo = b.N_lo;
             sp.N_rng = (uint64_t)((i128)b.N_hi - (i128)b.N_lo);
         }
+        sp.P_lo = 0;
+        sp.P_rng = ~(unsigned __int128)0;
+        if (p->features & SCR_F_PREWITT) {
+            unsigned __int128 L, U;
+            prewitt_bounds(tm, p, R, &L, &U);
+            if (L > U)
+                sp.empty = 1;
+            else {
+                sp.P_lo = L;
+                sp.P_rng = U - L;
+            }
+        }
     }
+    a->Mx = t->Mx;
+    a->My = t->My;
     return SCR_OK;
 }
 
@@ -336,6 +514,10 @@ int check_screen_inputs(const scr_tables *t, const scr_tmpl *tm, const scr_param
         return rc;
     if ((p->features & SCR_F_GRAD) && !(tm->features & SCR_F_GRAD))
         return fail(SCR_EINVAL, "template features were computed without SCR_F_GRAD");
+    if ((p->features & SCR_F_PREWITT) && !(tm->features & SCR_F_PREWITT))
+        return fail(SCR_EINVAL, "template features were computed without SCR_F_PREWITT");
+    if ((p->features & SCR_F_PREWITT) && !t->Mx)
+        return fail(SCR_EINVAL, "SCR_F_PREWITT needs the moment tables (build_moment_tables)");
     return SCR_OK;
 }
 
@@ -407,6 +589,8 @@ void screen_shutdown(scr_ctx *c) {
         std::lock_guard<std::mutex> lk(c->mu);
         for (auto *t : c->tables) {
             cudaFreeAsync(t->base, nullptr);
+            if (t->mom)
+                cudaFreeAsync(t->mom, nullptr);
             delete t;
         }
         c->tables.clear();
@@ -482,9 +666,17 @@ int tables_copy_to_host(scr_ctx *c, const scr_tables *t, int which, uint64_t *ds
     int rc;
     if ((rc = check_ctx(c)))
         return rc;
-    if (!t || which < 0 || which > 3 || !dst)
+    if (!t || which < 0 || which > 5 || !dst || (which >= 4 && !t->Mx))
         return fail(SCR_EINVAL, "bad arguments");
     DeviceGuard dg(c->device);
+    if (which >= 4) {   // moment tables: (H + 1) x (W + 1) 64-bit values
+        const uint64_t *src = which == 4 ? t->Mx : t->My;
+        const int64_t P = t->t[0].pitch;
+        CUDA_TRY(cudaStreamSynchronize(t->stream));
+        CUDA_TRY(cudaMemcpy2D(dst, (size_t)(t->W + 1) * 8, src + kColOffset, (size_t)P * 8, (size_t)(t->W + 1) * 8,
+                              t->H + 1, cudaMemcpyDeviceToHost));
+        return SCR_OK;
+    }
     const TableDesc &d = t->t[which];
     std::vector<uint32_t> lo((size_t)d.rows * d.cols), hi;
     CUDA_TRY(cudaStreamSynchronize(t->stream));
@@ -520,7 +712,7 @@ int template_features(scr_ctx *c, const uint8_t *tmpl_host, int32_t side, int32_
         return fail(SCR_EINVAL, "template side %d must be 2r+1 with 2 <= r <= 181 (r = %d)", side, r);
     if (t_min < 1 || t_min > r || ((features & SCR_F_GRAD) && t_min < 2))
         return fail(SCR_EINVAL, "t_min %d outside [%d, r]", t_min, (features & SCR_F_GRAD) ? 2 : 1);
-    if (features & ~7u)
+    if (features & ~15u)
         return fail(SCR_EINVAL, "unknown feature bits");
     *out = nullptr;
     DeviceGuard dg(c->device);
@@ -590,8 +782,77 @@ int template_features(scr_ctx *c, const uint8_t *tmpl_host, int32_t side, int32_
             if ((i128)g_n * tm->g_hi_d > (i128)tm->g_hi_n * g_d) { tm->g_hi_n = g_n; tm->g_hi_d = g_d; }
         }
     }
+    if (features & SCR_F_PREWITT) {
+        // doubled moments of each central square about the template centre
+        // (r + 1/2, r + 1/2): Gx2 = sum (2x - 2r - 1) I, Gy2 = sum (2y - 2r - 1) I;
+        // and the hull of phi^2 = 4 n^2 (Gx2^2 + Gy2^2) / J2^2 (Sec. 3-4)
+        bool firstp = true;
+        for (int tt = t_min; tt <= r; ++tt) {
+            const int64_t n = geometry(tt).n;
+            int64_t gx = 0, gy = 0;
+            for (int64_t y = r - n + 1; y <= r + n; ++y)
+                for (int64_t x = r - n + 1; x <= r + n; ++x) {
+                    const int64_t v = tmpl_host[y * side + x];
+                    gx += (2 * x - 2 * r - 1) * v;
+                    gy += (2 * y - 2 * r - 1) * v;
+                }
+            tm->Gx2.push_back(gx);
+            tm->Gy2.push_back(gy);
+            const unsigned __int128 num = (unsigned __int128)(4 * n * n) *
+                                          ((unsigned __int128)((i128)gx * gx) + (unsigned __int128)((i128)gy * gy));
+            const unsigned __int128 j = prewitt_j2(n), den = j * j;
+            if (firstp) {
+                tm->p_lo_n = tm->p_hi_n = num;
+                tm->p_lo_d = tm->p_hi_d = den;
+                firstp = false;
+                continue;
+            }
+            if (big_cmp(big_mul(Big(num), Big(tm->p_lo_d)), big_mul(Big(tm->p_lo_n), Big(den))) < 0) {
+                tm->p_lo_n = num;
+                tm->p_lo_d = den;
+            }
+            if (big_cmp(big_mul(Big(num), Big(tm->p_hi_d)), big_mul(Big(tm->p_hi_n), Big(den))) > 0) {
+                tm->p_hi_n = num;
+                tm->p_hi_d = den;
+            }
+        }
+    }
     c->tmpls.insert(tm);
     *out = tm;
+    return SCR_OK;
+}
+
+int build_moment_tables(scr_ctx *c, const uint8_t *img_dev, int32_t H, int32_t W, int64_t pitch, scr_tables *t,
+                        scr_stream stream) {
+    int rc;
+    if ((rc = check_ctx(c)))
+        return rc;
+    if (!img_dev || !t)
+        return fail(SCR_EINVAL, "null image or tables");
+    if (H != t->H || W != t->W || pitch < W)
+        return fail(SCR_EINVAL, "image %d x %d (pitch %lld) does not match the tables (%d x %d)", H, W,
+                    (long long)pitch, t->H, t->W);
+    DeviceGuard dg(c->device);
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!t->mom) {
+        const int64_t P = t->t[0].pitch;
+        const size_t one = (size_t)(H + 1) * P * 8;
+        const size_t bytes = 2 * ((one + 255) & ~size_t(255));
+        if ((rc = dev_alloc(c, bytes, st, &t->mom)))
+            return rc;
+        t->mom_bytes = bytes;
+        t->Mx = (uint64_t *)t->mom;
+        t->My = (uint64_t *)((char *)t->mom + ((one + 255) & ~size_t(255)));
+    }
+    Scoped scratch(c, st);
+    if ((rc = scratch.take(moment_scratch_bytes(H, W))))
+        return rc;
+    uint64_t n = 0;
+    cudaError_t e = launch_moment_tables(img_dev, pitch, H, W, t->t[0].pitch, t->Mx, t->My, scratch.p, st, &n);
+    c->launches += n;
+    CUDA_TRY(e);
+    t->stream = st;
     return SCR_OK;
 }
 
@@ -688,6 +949,8 @@ int screen_joint(scr_ctx *c, const scr_tables *t, const scr_tmpl *tm, const scr_
         return rc;
     if (!jt || !mask_dev || jt->n_areas < 1 || jt->n_areas > 3 || !jt->area_radii)
         return fail(SCR_EINVAL, "joint screen needs 1..3 areas, their radii and a mask");
+    if (p->features & SCR_F_PREWITT)
+        return fail(SCR_EUNSUPPORTED, "the joint membership screen has no Prewitt feature");
     const uint32_t feats = p->features & 7u;
     if (!feats)
         return fail(SCR_EINVAL, "no feature enabled");
@@ -1317,6 +1580,8 @@ int screen_batch_create(scr_ctx *c, const scr_tables *const *tables, int32_t n_i
             return fail(rc, "template %d: %s", t, g_last_error.c_str());
         if (params[t].n_scales > 32)
             return fail(SCR_EINVAL, "template %d: more than 32 scales", t);
+        if (params[t].features & SCR_F_PREWITT)
+            return fail(SCR_EUNSUPPORTED, "template %d: the batched screen has no Prewitt test", t);
     }
     for (int p = 0; p < n_pairs; ++p)
         if (pairs[p].image < 0 || pairs[p].image >= n_images || pairs[p].tmpl < 0 || pairs[p].tmpl >= n_tmpls)

@@ -28,6 +28,7 @@
 #include <stdint.h>
 
 #include "internal.h"
+#include "screen.h"
 
 namespace scr {
 namespace {
@@ -66,6 +67,10 @@ struct Corners {
 // still alive (a warp-uniform vote), and only for the live words.
 constexpr int WPW = 8;
 
+// PW: the Prewitt gradient test of the star's square (Sec. 3, Eq. S_y with
+// the moment tables of Eq. T_x; magnitude of Sec. 4) runs after the others,
+// compared squared in 128 bits.  The default kernel has no Prewitt code.
+template <bool PW>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock)
 k_screen(const __grid_constant__ ScreenArgs a) {
     pdl_begin();
@@ -144,6 +149,29 @@ k_screen(const __grid_constant__ ScreenArgs a) {
                         keep &= ~(1u << j);
                 }
             }
+            if (PW && __any_sync(0xffffffffu, keep != 0)) {
+                // moments about the square's centre (y + 1/2, x + 1/2), doubled:
+                // Gx2 = 2 [Mx window] - (2x + 1) S_sq, Gy2 = 2 [My window] - (2y + 1) S_sq
+                const uint64_t *MX = a.Mx + e, *MY = a.My + e;
+#pragma unroll
+                for (int j = 0; j < WPW; ++j) {
+                    if (!((keep >> j) & 1u))
+                        continue;
+                    const int d = 32 * j;
+                    const uint32_t Ssq = ld(L1 + p.oL[0] + d) - ld(L1 + p.oL[1] + d) - ld(L1 + p.oL[2] + d) +
+                                         ld(L1 + p.oL[3] + d);
+                    const uint64_t mx = __ldg(MX + p.oL[0] + d) - __ldg(MX + p.oL[1] + d) -
+                                        __ldg(MX + p.oL[2] + d) + __ldg(MX + p.oL[3] + d);
+                    const uint64_t my = __ldg(MY + p.oL[0] + d) - __ldg(MY + p.oL[1] + d) -
+                                        __ldg(MY + p.oL[2] + d) + __ldg(MY + p.oL[3] + d);
+                    const int64_t gx = (int64_t)(2 * mx - (uint64_t)(2 * (x0 + d) + 1) * Ssq);
+                    const int64_t gy = (int64_t)(2 * my - (uint64_t)(2 * y + 1) * Ssq);
+                    const uint64_t ax = (uint64_t)(gx < 0 ? -gx : gx), ay = (uint64_t)(gy < 0 ? -gy : gy);
+                    const unsigned __int128 g2 = (unsigned __int128)ax * ax + (unsigned __int128)ay * ay;
+                    if (g2 - p.P_lo > p.P_rng)
+                        keep &= ~(1u << j);
+                }
+            }
         }
         uint32_t mine = 0;
 #pragma unroll
@@ -213,7 +241,9 @@ __global__ void k_template_sums(const TmplArgs a) {
 cudaError_t launch_screen(const ScreenArgs &args, cudaStream_t st, uint64_t *launches) {
     const int warps = (args.Wwords + WPW - 1) / WPW;
     dim3 grid((warps + kWarpsPerBlock - 1) / kWarpsPerBlock, args.H);
-    const cudaError_t e = launch_pdl(k_screen, grid, dim3(32 * kWarpsPerBlock), st, args);
+    const cudaError_t e = (args.features & SCR_F_PREWITT)
+                              ? launch_pdl(k_screen<true>, grid, dim3(32 * kWarpsPerBlock), st, args)
+                              : launch_pdl(k_screen<false>, grid, dim3(32 * kWarpsPerBlock), st, args);
     if (launches)
         *launches += 1;
     return e;

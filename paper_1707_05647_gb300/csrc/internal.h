@@ -60,10 +60,12 @@ struct ScaleParam {
     uint64_t V_rng;                   // variance: (V - V_lo) <= V_rng       (64-bit)
     int64_t N_lo;
     uint64_t N_rng;                   // contrast: (N - N_lo) <= N_rng       (64-bit)
+    unsigned __int128 P_lo, P_rng;    // Prewitt:  (Gx2^2 + Gy2^2 - P_lo) <= P_rng (128-bit)
 };
 
 struct ScreenArgs {
     const uint32_t *L1, *L2, *T1, *T2;   // low planes (window sums read mod 2^32)
+    const uint64_t *Mx, *My;             // Prewitt moment tables (with SCR_F_PREWITT)
     int64_t pitch;                       // words per row (all four tables)
     int32_t H, W, Wwords, n_scales;
     uint32_t features;
@@ -148,6 +150,11 @@ struct JointArgs {
     uint32_t *mask;
 };
 cudaError_t launch_screen_joint(const JointArgs &a, cudaStream_t st, uint64_t *launches);
+
+// Prewitt moment tables (moments.cu)
+size_t moment_scratch_bytes(int H, int W);
+cudaError_t launch_moment_tables(const uint8_t *img, int64_t ipitch, int H, int W, int64_t pitch, uint64_t *Mx,
+                                 uint64_t *My, void *scratch, cudaStream_t st, uint64_t *launches);
 
 // One mask in a buffer of several (segmented compaction): S planes of H rows of
 // Wwords words starting at word0, a multiple of kCompactChunk; the words up to

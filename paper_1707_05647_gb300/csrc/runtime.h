@@ -43,6 +43,11 @@ struct scr_tables {
     void *base = nullptr;
     size_t bytes = 0;
     int H = 0, W = 0;
+    // Prewitt moment tables (build_moment_tables): 64-bit, same rows, pitch and
+    // column offset as the upright tables (pitch in 64-bit words)
+    void *mom = nullptr;
+    size_t mom_bytes = 0;
+    uint64_t *Mx = nullptr, *My = nullptr;
     cudaStream_t stream = nullptr;   // stream of the last use (frees are ordered on it)
 };
 
@@ -54,6 +59,10 @@ struct scr_tmpl {
     int64_t mu_lo_n = 0, mu_lo_d = 1, mu_hi_n = 0, mu_hi_d = 1;
     int64_t v_lo_n = 0, v_lo_d = 1, v_hi_n = 0, v_hi_d = 1;
     int64_t g_lo_n = 0, g_lo_d = 1, g_hi_n = 0, g_hi_d = 1;
+    // Prewitt (SCR_F_PREWITT): doubled moments of each central square, and the
+    // hull of phi^2 = 4 n^2 (Gx2^2 + Gy2^2) / J2^2 as num/den
+    std::vector<int64_t> Gx2, Gy2;
+    unsigned __int128 p_lo_n = 0, p_lo_d = 1, p_hi_n = 0, p_hi_d = 1;
 };
 
 struct scr_batch;

@@ -1061,6 +1061,8 @@ int server_screen(scr_server *s, int64_t image_id, const scr_tmpl *tm, const scr
         return rc;
     if ((p->features & SCR_F_GRAD) && !(tm->features & SCR_F_GRAD))
         return fail(SCR_EINVAL, "template features were computed without SCR_F_GRAD");
+    if (p->features & SCR_F_PREWITT)
+        return fail(SCR_EUNSUPPORTED, "the serving loop has no Prewitt test");
     auto *r = new (std::nothrow) SrvRequest();
     if (!r)
         return fail(SCR_ENOMEM, "host allocation failed");
