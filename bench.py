@@ -416,7 +416,9 @@ def run_batched(args):
 def run_joint(args):
     """The joint-vector membership screen (three nested central areas, q = 4, 2,
     4 grey levels) on the 4096^2 workload, beside the interval screen on the
-    same tables: device time per screen with CUDA events, survivors of each."""
+    same tables and the interval screen with the Prewitt test added (plus the
+    moment-table build): device time per screen with CUDA events, survivors of
+    each."""
     import torch
     import synth
     from fractions import Fraction
@@ -459,6 +461,19 @@ def run_joint(args):
     py, px = wl.planted
     m = mask.cpu().numpy().view(np.uint32).reshape(S, H, (W + 31) // 32)
     planted = any((int(m[s, py, px >> 5]) >> (px & 31)) & 1 for s in range(S))
+    # the interval screen with the Prewitt test of the star's square added
+    dimg = torch.from_numpy(wl.image).cuda()
+    scr.build_moment_tables(ctx, tab, dimg, st)
+    tmp = scr.template_features(ctx, wl.template, wl.r, wl.t_min, wl.features | scr.F_PREWITT)
+    pp = scr.Params(wl.radii, wl.features | scr.F_PREWITT, wl.tol.mean_rel, wl.tol.std_rel, wl.tol.grad_rel,
+                    wl.tol.grad_abs, Fraction(1, 10), Fraction(2))
+    pw_s = timed(lambda: scr.screen_features(ctx, tab, tmp, pp, mask, st))
+    scr.compact_mask(ctx, mask, S, H, W, lst, cnt, st)
+    torch.cuda.synchronize()
+    n_pw = int(cnt.item())
+    m = mask.cpu().numpy().view(np.uint32).reshape(S, H, (W + 31) // 32)
+    planted_pw = any((int(m[s, py, px >> 5]) >> (px & 31)) & 1 for s in range(S))
+    mom_s = timed(lambda: scr.build_moment_tables(ctx, tab, dimg, st))
     int_s = timed(lambda: scr.screen_features(ctx, tab, tmi, pi, mask, st))
     scr.compact_mask(ctx, mask, S, H, W, lst, cnt, st)
     torch.cuda.synchronize()
@@ -471,6 +486,9 @@ def run_joint(args):
         "survivors": n_joint, "pruned": 1 - n_joint / cand, "planted_survives": bool(planted),
         "interval_screen": {"ms_per_screen": 1e3 * int_s, "value": cand / int_s, "survivors": n_int,
                             "pruned": 1 - n_int / cand},
+        "interval_with_prewitt": {"ms_per_screen": 1e3 * pw_s, "value": cand / pw_s, "survivors": n_pw,
+                                  "planted_survives": bool(planted_pw), "moment_tables_ms": 1e3 * mom_s,
+                                  "moment_tables_GBps": 2 * (H + 1) * (W + 1) * 8 / mom_s / 1e9},
         "data": "synthetic"}), flush=True)
     scr.screen_shutdown(ctx)
 
