@@ -138,17 +138,29 @@ def measured_peak_gbs():
         return 6800.0, "fallback"
 
 
-def oracle_baseline(wl, max_rows=None):
-    """CPU oracle (tables + screen) on the host cores; returns (evals/s, sample, cores, seconds)."""
+def oracle_baseline(wl, max_rows=None, threads=0, split=None):
+    """CPU oracle on the host cores (threads = 0: all, OpenMP over rows in the
+    screen); returns (evals/s, sample, threads used, seconds).  split, a dict,
+    receives the table-build and screen seconds separately."""
     import oracle
     img = wl.image if max_rows is None else wl.image[:max_rows]
     H, W = img.shape
+    used = oracle.threads(threads if threads > 0 else (os.cpu_count() or 1))
     t0 = time.perf_counter()
-    oracle.screen_workload(img, wl.template, wl.r, wl.t_min, wl.radii, wl.features, wl.tol)
+    tb = oracle.Tables(img)
+    t1 = time.perf_counter()
+    oracle.screen_workload(img, wl.template, wl.r, wl.t_min, wl.radii, wl.features, wl.tol, tables=tb)
     dt = time.perf_counter() - t0
+    if split is not None:
+        split["tables_s"] = t1 - t0
+        split["screen_s"] = dt - (t1 - t0)
     n = candidates(H, W, wl.radii)
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return n / dt, f"{H}x{W} rows of the same image, all {len(wl.radii)} scales, tables + screen", cores, dt
+    return n / dt, f"{H}x{W} rows of the same image, all {len(wl.radii)} scales, tables + screen", used, dt
+
+
+def oracle_threads(n):
+    import oracle
+    oracle.threads(n)
 
 
 def run_reference(args):
@@ -294,9 +306,15 @@ def emit(args, wl, world, total_s, value, k3_ms, step_ms, launches, clk, n_surv,
     traffic = recorded_traffic(H, W)
     cpu = None
     if not args.no_cpu_baseline:
-        v, sample, cores, dt = oracle_baseline(wl)
+        split, split1 = {}, {}
+        v, sample, cores, dt = oracle_baseline(wl, split=split)
+        v1, sample1, _, dt1 = oracle_baseline(wl, 1024, threads=1, split=split1)
+        oracle_threads(cores)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
-               "seconds": round(dt, 2)}
+               "seconds": round(dt, 2), "tables_s": round(split["tables_s"], 3),
+               "screen_s": round(split["screen_s"], 3),
+               "single_thread": {"value": v1, "sample": sample1, "seconds": round(dt1, 2),
+                                 "tables_s": round(split1["tables_s"], 3), "screen_s": round(split1["screen_s"], 3)}}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,

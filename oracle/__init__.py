@@ -66,12 +66,19 @@ def lib():
                                      ctypes.c_int, i32p, i64p, ctypes.c_uint, u32p, u64p,
                                      ctypes.c_int64]
             L.orc_screen.restype = ctypes.c_int64
+            L.orc_threads.argtypes = [ctypes.c_int]
+            L.orc_threads.restype = ctypes.c_int
             _lib = L
     return _lib
 
 
 def _p(a: np.ndarray, ct):
     return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def threads(n: int = 0) -> int:
+    """Set the screening loop's OpenMP thread count (n > 0); returns the count in effect."""
+    return int(lib().orc_threads(int(n)))
 
 
 def square_half(R: int) -> int:

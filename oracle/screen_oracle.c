@@ -33,6 +33,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define PX(img, pitch, y, x) ((uint64_t)(img)[(int64_t)(y) * (pitch) + (x)])
 
@@ -245,4 +248,18 @@ int64_t orc_screen(const uint64_t *L1, const uint64_t *L2, const uint64_t *T1,
                 }
             }
     return count;
+}
+
+
+/* Threads the screening loop uses (OpenMP over rows); n <= 0 leaves it as is.
+ * Returns the count in effect. */
+int orc_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0)
+        omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
