@@ -226,3 +226,48 @@ def test_completion_queue_returns_each_request_once(ctx, work):
         assert e.value.code == scr.SCR_ETIMEOUT
     finally:
         scr.server_destroy(s)
+
+
+def test_concurrent_clients(ctx, work):
+    """Four client threads upload and screen at once, one collector drains the
+    completion queue; every list equals the oracle's."""
+    import threading
+    bw, tmpls, params, want = work
+    s = scr.server_create(ctx, max_batch=5)
+    try:
+        ids = {}
+        for i, im in enumerate(bw.images):
+            iid, rid = scr.server_upload(s, im)
+            assert scr.server_wait(s, rid)["status"] == scr.SCR_OK
+            ids[i] = iid
+        lock = threading.Lock()
+        submitted, errors = {}, []
+
+        def client(c):
+            try:
+                for k in range(15):
+                    i, t = (c + k) % 4, (c * 3 + k) % 5
+                    buf = np.zeros(1 << 16, np.uint64)
+                    rid = scr.server_screen(s, ids[i], tmpls[t], params[t], buf)
+                    with lock:
+                        submitted[rid] = (i, t, buf)
+            except Exception as e:   # surfaced below
+                errors.append(e)
+
+        threads = [threading.Thread(target=client, args=(c,)) for c in range(4)]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join()
+        assert not errors
+        got = {}
+        for _ in range(len(submitted)):
+            rid, r = scr.server_next(s, 60_000_000)
+            got[rid] = r
+        assert set(got) == set(submitted)
+        for rid, (i, t, buf) in submitted.items():
+            r = got[rid]
+            assert r["status"] == scr.SCR_OK
+            assert np.array_equal(buf[:r["count"]], want[(i, t)])
+    finally:
+        scr.server_destroy(s)
