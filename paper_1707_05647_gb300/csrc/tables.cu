@@ -44,19 +44,25 @@ constexpr int CW = kTileCols;
 constexpr int HALO = kHalo;
 constexpr int SLOTS = kTileSlots;            // 1024 accumulator columns per tile
 constexpr int NT = 256;                      // threads of k_tab_reduce
-constexpr int WT = 256;                      // threads of k_tab_write (4 columns each)
-constexpr int K = SLOTS / WT;                // columns per k_tab_write thread
+constexpr int WK = 8;                        // columns per k_tab_write lane
+constexpr int WS = 32 * WK;                  // 256 slots per warp tile
+constexpr int WCW = WS - 2 * HALO;           // 192 core columns per warp tile
+constexpr int WPR = CW / WCW;                // warp tiles per reduce tile (5)
 constexpr int CL = kWinLo;                   // first carry column
+static_assert(CW % WCW == 0, "a reduce tile holds whole warp-tile chunks");
+static_assert(B == 32, "row carries are held one per lane");
 
 struct Geometry {
-    int H, W, n, m;          // bands, tiles
+    int H, W, n, m;          // bands, reduce tiles (CW core columns each)
+    int mw;                  // warp tiles per band (WCW core columns each)
     int XW;                  // carry columns c in [CL, W+1]
     int XWp;                 // row pitch of the carry arrays (XW rounded up to 4)
     int DMIN, DN;            // anti-diagonal lanes d in [DMIN, DMIN+DN)
     int FMIN, FN;            // diagonal lanes f in [FMIN, FMIN+FN)
     Geometry(int H_, int W_) : H(H_), W(W_) {
         n = (H + B - 1) / B;
-        m = (W + CW - 1) / CW;
+        m = W / CW + 1;      // the core columns of the tiles reach past column W
+        mw = W / WCW + 1;
         XW = W + 1 - CL + 1;
         XWp = (XW + 3) & ~3;
         DMIN = CL - 1;
@@ -71,12 +77,12 @@ struct Scratch {
     uint32_t *cs1, *cs2;     // [n][W]        column sums of the band
     uint32_t *ad1, *ad2;     // [n][W+B-1]    anti-diagonal sums, x' + B-1
     uint32_t *md1, *md2;     // [n][W+B-1]    diagonal sums, x''
-    uint32_t *rs1, *rs2;     // [n][m][B]     row sums over the tile's shifted chunk
+    uint32_t *rs1, *rs2;     // [n][mw][B]    row sums over each warp tile's shifted chunk
     uint32_t *csx1, *csx2;   // [n][XWp]      exclusive band prefix of cs at x = c (0 outside the image)
     uint32_t *adx1, *adx2;   // [n][XWp]      AD_i(r0-1+c)
     uint32_t *mdx1, *mdx2;   // [n][XWp]      MD_i(c-r0)
     uint32_t *adf1, *adf2;   // [DN]          full anti-diagonal sums, index d - DMIN
-    uint32_t *rc1, *rc2;     // [n][m][B]     row carries P(r, c0-HALO-1)
+    uint32_t *rc1, *rc2;     // [n][mw][B]    row carries P(r, c0-HALO-1) of each warp tile
     void *xl1, *xl2, *x11, *x12, *x21, *x22;   // [n][XWp] carry rows, table width
 };
 
@@ -89,7 +95,7 @@ size_t carve(const Geometry &g, int sb, int qb, Scratch *s, char *base) {
         off += align256(bytes);
         return p;
     };
-    const size_t n = g.n, W = g.W, m = g.m, XW = g.XWp;
+    const size_t n = g.n, W = g.W, m = g.mw, XW = g.XWp;
     s->cs1 = (uint32_t *)take(n * W * 4);
     s->cs2 = (uint32_t *)take(n * W * 4);
     s->ad1 = (uint32_t *)take(n * (W + B - 1) * 4);
@@ -170,32 +176,38 @@ __global__ void __launch_bounds__(NT) k_tab_reduce(const ReduceArgs a) {
             *reinterpret_cast<uint2 *>(&tile[rb + k][8 * (t & 127)]) = w[k];
     }
     __syncthreads();
-    // row sums over the shifted chunk [c0-HALO, c0-HALO+CW): NT/B threads per row
+    // row sums over the warp tiles' shifted chunks [c0w-HALO, c0w-HALO+WCW),
+    // c0w = (j*WPR + q)*WCW: 8 threads per (row, chunk), 6 words each
     {
-        constexpr int TPR = NT / B;                  // threads per row (16)
-        constexpr int WPT = CW / 4 / TPR;            // 32-bit words per thread (15)
-        const int rr = t / TPR, part = t % TPR;
-        const uint32_t *row = reinterpret_cast<const uint32_t *>(&tile[rr][0]) + part * WPT;
-        uint32_t s1 = 0, s2 = 0;
+        constexpr int TPI = 8;
+        constexpr int WPI = WCW / 4 / TPI;
+        const int sub = t % TPI;
+#pragma unroll 1
+        for (int u = t / TPI; u < B * WPR; u += NT / TPI) {
+            const int rr = u / WPR, q = u % WPR;
+            const uint32_t *row = reinterpret_cast<const uint32_t *>(&tile[rr][0]) + q * (WCW / 4) + sub * WPI;
+            uint32_t s1 = 0, s2 = 0;
 #pragma unroll
-        for (int q = 0; q < WPT; ++q) {
-            const uint32_t w4 = row[q];
+            for (int w4i = 0; w4i < WPI; ++w4i) {
+                const uint32_t w4 = row[w4i];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const uint32_t v = (w4 >> (8 * k)) & 0xffu;
-                s1 += v;
-                s2 += v * v;
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t v = (w4 >> (8 * k)) & 0xffu;
+                    s1 += v;
+                    s2 += v * v;
+                }
             }
-        }
 #pragma unroll
-        for (int o = 1; o < TPR; o <<= 1) {
-            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-        }
-        if (part == 0) {
-            const size_t o = ((size_t)i * g.m + j) * B + rr;
-            a.s.rs1[o] = s1;
-            a.s.rs2[o] = s2;
+            for (int o = 1; o < TPI; o <<= 1) {
+                s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+                s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            }
+            const int jw = j * WPR + q;
+            if (sub == 0 && jw < g.mw) {
+                const size_t o = ((size_t)i * g.mw + jw) * B + rr;
+                a.s.rs1[o] = s1;
+                a.s.rs2[o] = s2;
+            }
         }
     }
     const size_t W = g.W, WD = g.W + B - 1;
@@ -409,16 +421,32 @@ __global__ void __launch_bounds__(PT) k_tab_prefix(const PrefixArgs a) {
     const int i = blockIdx.x, q = blockIdx.y, t = threadIdx.x, lane = t & 31, w = t >> 5;
     const int r0 = i * B;
     const int XW = g.XW;
-    if (q == 6) {   // row carries per tile: sum of the row sums of the tiles to the left
-        if (t < B) {
-            uint32_t c1 = 0, c2 = 0;
-            for (int j = 0; j < g.m; ++j) {
-                const size_t o = ((size_t)i * g.m + j) * B + t;
-                a.s.rc1[o] = c1;
-                a.s.rc2[o] = c2;
-                c1 += a.s.rs1[o];
-                c2 += a.s.rs2[o];
-            }
+    if (q == 6) {   // row carries per warp tile: sum of the row sums of the chunks to the left
+        // lane = row of the band; warp w takes a contiguous run of chunks
+        __shared__ uint32_t tot1[PT / 32][B], tot2[PT / 32][B];
+        const int seg = (g.mw + PT / 32 - 1) / (PT / 32);
+        const int j0 = w * seg, j1 = min(g.mw, j0 + seg);
+        uint32_t s1 = 0, s2 = 0;
+        for (int j = j0; j < j1; ++j) {
+            const size_t o = ((size_t)i * g.mw + j) * B + lane;
+            s1 += a.s.rs1[o];
+            s2 += a.s.rs2[o];
+        }
+        tot1[w][lane] = s1;
+        tot2[w][lane] = s2;
+        __syncthreads();
+        uint32_t c1 = 0, c2 = 0;
+        for (int u = 0; u < w; ++u) {
+            c1 += tot1[u][lane];
+            c2 += tot2[u][lane];
+        }
+        for (int j = j0; j < j1; ++j) {
+            const size_t o = ((size_t)i * g.mw + j) * B + lane;
+            const uint32_t v1 = a.s.rs1[o], v2 = a.s.rs2[o];
+            a.s.rc1[o] = c1;
+            a.s.rc2[o] = c2;
+            c1 += v1;
+            c2 += v2;
         }
         return;
     }
@@ -523,7 +551,7 @@ __global__ void __launch_bounds__(PT) k_tab_prefix(const PrefixArgs a) {
 }
 
 // ----------------------------------------------------------------------------
-// Stage 4: per tile, walk the band's rows and write L1, L2, T1, T2.
+// Stage 4: per warp tile, walk the band's rows and write L1, L2, T1, T2.
 // ----------------------------------------------------------------------------
 struct WriteArgs {
     const uint8_t *img;
@@ -535,14 +563,35 @@ struct WriteArgs {
     int aligned8;
 };
 
+// WK consecutive values at a 16-byte aligned word: two 16-byte stores per plane
 template <typename T>
-__device__ __forceinline__ void store4(uint32_t *lo, uint32_t *hi, int64_t word, const T (&v)[K]) {
-    *reinterpret_cast<uint4 *>(lo + word) =
-        make_uint4((uint32_t)v[0], (uint32_t)v[1], (uint32_t)v[2], (uint32_t)v[3]);
-    if (sizeof(T) == 8)
-        *reinterpret_cast<uint4 *>(hi + word) =
-            make_uint4((uint32_t)((uint64_t)v[0] >> 32), (uint32_t)((uint64_t)v[1] >> 32),
-                       (uint32_t)((uint64_t)v[2] >> 32), (uint32_t)((uint64_t)v[3] >> 32));
+__device__ __forceinline__ void store8(uint32_t *lo, uint32_t *hi, int64_t word, const T (&v)[WK]) {
+    uint4 *pl = reinterpret_cast<uint4 *>(lo + word);
+    pl[0] = make_uint4((uint32_t)v[0], (uint32_t)v[1], (uint32_t)v[2], (uint32_t)v[3]);
+    pl[1] = make_uint4((uint32_t)v[4], (uint32_t)v[5], (uint32_t)v[6], (uint32_t)v[7]);
+    if (sizeof(T) == 8) {
+        uint4 *ph = reinterpret_cast<uint4 *>(hi + word);
+        ph[0] = make_uint4((uint32_t)((uint64_t)v[0] >> 32), (uint32_t)((uint64_t)v[1] >> 32),
+                           (uint32_t)((uint64_t)v[2] >> 32), (uint32_t)((uint64_t)v[3] >> 32));
+        ph[1] = make_uint4((uint32_t)((uint64_t)v[4] >> 32), (uint32_t)((uint64_t)v[5] >> 32),
+                           (uint32_t)((uint64_t)v[6] >> 32), (uint32_t)((uint64_t)v[7] >> 32));
+    }
+}
+
+// WK consecutive values into a shared-memory row (low words; high words into hi
+// when the table is 64-bit; hi aliases lo otherwise and is not written)
+template <typename T>
+__device__ __forceinline__ void put8(uint32_t *lo, uint32_t *hi, int at, const T (&v)[WK]) {
+    uint4 *pl = reinterpret_cast<uint4 *>(lo + at);
+    pl[0] = make_uint4((uint32_t)v[0], (uint32_t)v[1], (uint32_t)v[2], (uint32_t)v[3]);
+    pl[1] = make_uint4((uint32_t)v[4], (uint32_t)v[5], (uint32_t)v[6], (uint32_t)v[7]);
+    if (sizeof(T) == 8) {
+        uint4 *ph = reinterpret_cast<uint4 *>(hi + at);
+        ph[0] = make_uint4((uint32_t)((uint64_t)v[0] >> 32), (uint32_t)((uint64_t)v[1] >> 32),
+                           (uint32_t)((uint64_t)v[2] >> 32), (uint32_t)((uint64_t)v[3] >> 32));
+        ph[1] = make_uint4((uint32_t)((uint64_t)v[4] >> 32), (uint32_t)((uint64_t)v[5] >> 32),
+                           (uint32_t)((uint64_t)v[6] >> 32), (uint32_t)((uint64_t)v[7] >> 32));
+    }
 }
 
 template <typename T>
@@ -552,53 +601,45 @@ __device__ __forceinline__ void store1(uint32_t *lo, uint32_t *hi, int64_t word,
         hi[word] = (uint32_t)((uint64_t)v >> 32);
 }
 
-__device__ __forceinline__ uint32_t load4(const uint8_t *img, int64_t pitch, int H, int W, int aligned4, int y,
-                                          int cs) {
-    if (y < H && aligned4 && cs >= 0 && cs + 4 <= W)
-        return __ldg(reinterpret_cast<const uint32_t *>(img + (int64_t)y * pitch + cs));
-    uint32_t w = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int x = cs + k;
-        const uint32_t b = (y < H && x >= 0 && x < W) ? (uint32_t)__ldg(img + (int64_t)y * pitch + x) : 0u;
-        w |= b << (8 * k);
-    }
-    return w;
-}
-
-// Each thread owns K = 4 adjacent columns, so every warp store writes 512
-// contiguous bytes of one plane.
+// One warp per (band, warp tile); lane l owns the WK adjacent columns
+// cs = c0 - HALO + WK*l .. cs + WK - 1 of the tile's WS slots.  Per row the
+// lane scans its pixels, a warp scan plus the tile's row carry gives P, D1
+// moves one column left and D2 one column right (register moves plus one
+// neighbour shuffle), and the core lanes store L and T = D1 - D2.  The warp
+// needs no other warp: D1 and D2 values that flow in from outside the tile are
+// taken as the tile's own edge value (right) or 0 (left); an error entering at
+// an edge moves one column per row, so after the band's B rows it has crossed
+// at most B = HALO columns and never reaches the core.  At the right end of the
+// image D1 is constant in the column, so there the edge value is exact.
 template <typename TS, typename TQ>
-__global__ void __launch_bounds__(WT) k_tab_write(const WriteArgs a) {
+__global__ void __launch_bounds__(32) k_tab_write(const WriteArgs a) {
+    // planes of a row in obuf: L1 (lo[, hi]), L2 (lo[, hi]), T1 (lo[, hi]), T2 (lo[, hi])
+    constexpr int HS = sizeof(TS) == 8 ? 1 : 0, HQ = sizeof(TQ) == 8 ? 1 : 0;
+    constexpr int PL1 = 0, PL2 = PL1 + 1 + HS, PT1 = PL2 + 1 + HQ, PT2 = PT1 + 1 + HS;
+    constexpr int NPL = PT2 + 1 + HQ;
     pdl_begin();
-    constexpr int NW = WT / 32;
-    __shared__ uint32_t wt1[2][NW], wt2[2][NW];                // warp totals
-    __shared__ TS nb_d1a[2][NW], nb_d2a[2][NW];                // warp-edge neighbours
-    __shared__ TQ nb_d1b[2][NW], nb_d2b[2][NW];
-    __shared__ uint32_t rc1[B], rc2[B];
     const Geometry &g = a.g;
-    const int j = blockIdx.x, i = blockIdx.y, t = threadIdx.x;
-    const int lane = t & 31, w = t >> 5;
+    const int j = blockIdx.x, i = blockIdx.y, lane = threadIdx.x;
     const int r0 = i * B;
     const int rows = min(B, g.H - r0);
-    const int c0 = j * CW;
-    const bool last = (j == g.m - 1);
-    const int cs = c0 - HALO + K * t;
-    const int cTmax = last ? g.W : c0 + CW - 1;     // last T column this tile writes
-    const int cLmax = last ? g.W - 1 : c0 + CW - 1; // last L column (b = c+1 <= W)
+    const int c0 = j * WCW;
+    const bool last = (j == g.mw - 1);
+    const int cs = c0 - HALO + WK * lane;
+    const int cTmax = last ? g.W : c0 + WCW - 1;     // last T column this tile writes
+    const int cLmax = last ? g.W - 1 : c0 + WCW - 1; // last L column (b = c+1 <= W)
     const bool wT = cs >= c0 && cs <= cTmax;
     const bool wL = cs >= c0 && cs <= cLmax;
-    const bool wEdge = (j == 0) && (cs == -K);      // holds column c = -1 (b = 0)
+    const bool wEdge = (j == 0) && (cs == -WK);     // holds column c = -1 (b = 0)
 
     // carries from the row above the band
-    TS L1a[K], D1a[K], D2a[K];
-    TQ L2a[K], D1b[K], D2b[K];
+    TS L1a[WK], D1a[WK], D2a[WK];
+    TQ L2a[WK], D1b[WK], D2b[WK];
     {
         const size_t XW = g.XWp;
         const TS *xl1 = (const TS *)a.s.xl1, *x11 = (const TS *)a.s.x11, *x21 = (const TS *)a.s.x21;
         const TQ *xl2 = (const TQ *)a.s.xl2, *x12 = (const TQ *)a.s.x12, *x22 = (const TQ *)a.s.x22;
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
+        for (int k = 0; k < WK; ++k) {
             int c = cs + k;
             c = c < CL ? CL : (c > g.W + 1 ? g.W + 1 : c);
             const size_t o = (size_t)i * XW + (size_t)(c - CL);
@@ -610,17 +651,29 @@ __global__ void __launch_bounds__(WT) k_tab_write(const WriteArgs a) {
             D2b[k] = x22[o];
         }
     }
+    // row carries P(r0 + lane, c0 - HALO - 1), one row per lane
+    uint32_t rcv1 = 0, rcv2 = 0;
+    if (lane < rows) {
+        const size_t o = ((size_t)i * g.mw + j) * B + lane;
+        rcv1 = a.s.rc1[o];
+        rcv2 = a.s.rc2[o];
+    }
     // row 0 of every table is zero
     if (i == 0) {
-        TS z1[K] = {0, 0, 0, 0};
-        TQ z2[K] = {0, 0, 0, 0};
+        TS z1[WK];
+        TQ z2[WK];
+#pragma unroll
+        for (int k = 0; k < WK; ++k) {
+            z1[k] = 0;
+            z2[k] = 0;
+        }
         if (wL) {
-            store4(a.L1lo, a.L1hi, cs + 1 + kColOffset, z1);
-            store4(a.L2lo, a.L2hi, cs + 1 + kColOffset, z2);
+            store8(a.L1lo, a.L1hi, cs + 1 + kColOffset, z1);
+            store8(a.L2lo, a.L2hi, cs + 1 + kColOffset, z2);
         }
         if (wT) {
-            store4(a.T1lo, a.T1hi, cs + 1 + kColOffset, z1);
-            store4(a.T2lo, a.T2hi, cs + 1 + kColOffset, z2);
+            store8(a.T1lo, a.T1hi, cs + 1 + kColOffset, z1);
+            store8(a.T2lo, a.T2hi, cs + 1 + kColOffset, z2);
         }
         if (wEdge) {
             store1(a.L1lo, a.L1hi, kColOffset, (TS)0);
@@ -629,32 +682,33 @@ __global__ void __launch_bounds__(WT) k_tab_write(const WriteArgs a) {
             store1(a.T2lo, a.T2hi, kColOffset, (TQ)0);
         }
     }
-    if (t < B) {
-        rc1[t] = a.s.rc1[((size_t)i * g.m + j) * B + t];
-        rc2[t] = a.s.rc2[((size_t)i * g.m + j) * B + t];
-    }
-    __syncthreads();
-    const int aligned4 = a.aligned8;
     // pixel rows are prefetched two rows ahead
-    uint32_t nxt0 = load4(a.img, a.pitch, g.H, g.W, aligned4, r0, cs);
-    uint32_t nxt1 = load4(a.img, a.pitch, g.H, g.W, aligned4, r0 + 1, cs);
+    uint2 nxt0 = load8(a.img, a.pitch, g.H, g.W, a.aligned8, r0, cs);
+    uint2 nxt1 = load8(a.img, a.pitch, g.H, g.W, a.aligned8, r0 + 1, cs);
+    // core columns of the current row, one 192-word row per plane, two rows in flight
+    __shared__ __align__(128) uint32_t obuf[2][NPL][WCW];
+    const int ob = cs - c0;                              // this lane's first word in an obuf row
+    // columns of the L and T rows this tile stores, rounded up to 16-byte multiples
+    const uint32_t bytesL = (uint32_t)((max(0, min(WCW, cLmax - c0 + 1)) + 3) / 4 * 16);
+    const uint32_t bytesT = (uint32_t)((min(WCW, cTmax - c0 + 1) + 3) / 4 * 16);
 
+#pragma unroll 1
     for (int rr = 0; rr < rows; ++rr) {
         const int y = r0 + rr;
         const int par = rr & 1;
-        const uint32_t q = nxt0;
+        const uint2 q = nxt0;
         nxt0 = nxt1;
         if (rr + 2 < rows)
-            nxt1 = load4(a.img, a.pitch, g.H, g.W, aligned4, y + 2, cs);
-        uint32_t p1[K], p2[K];
+            nxt1 = load8(a.img, a.pitch, g.H, g.W, a.aligned8, y + 2, cs);
+        uint32_t p1[WK], p2[WK];
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const uint32_t v = (q >> (8 * k)) & 0xffu;
+        for (int k = 0; k < WK; ++k) {
+            const uint32_t v = ((k < 4 ? q.x : q.y) >> (8 * (k & 3))) & 0xffu;
             p1[k] = (k ? p1[k - 1] : 0u) + v;
             p2[k] = (k ? p2[k - 1] : 0u) + v * v;
         }
-        // warp inclusive scan of the thread totals
-        uint32_t s1 = p1[K - 1], s2 = p2[K - 1];
+        // warp inclusive scan of the lane totals
+        uint32_t s1 = p1[WK - 1], s2 = p2[WK - 1];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t u1 = __shfl_up_sync(0xffffffffu, s1, o);
@@ -664,61 +718,31 @@ __global__ void __launch_bounds__(WT) k_tab_write(const WriteArgs a) {
                 s2 += u2;
             }
         }
-        if (lane == 31) {
-            wt1[par][w] = s1;
-            wt2[par][w] = s2;
-        }
-        // old D1[0] and D2[K-1] of warp-edge threads for the neighbouring warps
-        if (lane == 0) {
-            nb_d1a[par][w] = D1a[0];
-            nb_d1b[par][w] = D1b[0];
-        }
-        if (lane == 31) {
-            nb_d2a[par][w] = D2a[K - 1];
-            nb_d2b[par][w] = D2b[K - 1];
-        }
-        // in-warp neighbours (before the update)
+        // e = P(y, cs - 1)
+        const uint32_t e1 = __shfl_sync(0xffffffffu, rcv1, rr) + s1 - p1[WK - 1];
+        const uint32_t e2 = __shfl_sync(0xffffffffu, rcv2, rr) + s2 - p2[WK - 1];
+        // neighbours before the update
         TS n1a = __shfl_down_sync(0xffffffffu, D1a[0], 1);
         TQ n1b = __shfl_down_sync(0xffffffffu, D1b[0], 1);
-        TS n2a = __shfl_up_sync(0xffffffffu, D2a[K - 1], 1);
-        TQ n2b = __shfl_up_sync(0xffffffffu, D2b[K - 1], 1);
-        __syncthreads();
-        uint32_t e1 = rc1[rr] + s1 - p1[K - 1], e2 = rc2[rr] + s2 - p2[K - 1];
-#pragma unroll
-        for (int qq = 0; qq < NW; ++qq) {
-            if (qq < w) {
-                e1 += wt1[par][qq];
-                e2 += wt2[par][qq];
-            }
-        }
+        TS n2a = __shfl_up_sync(0xffffffffu, D2a[WK - 1], 1);
+        TQ n2b = __shfl_up_sync(0xffffffffu, D2b[WK - 1], 1);
         if (lane == 31) {
-            if (w + 1 < NW) {
-                n1a = nb_d1a[par][w + 1];
-                n1b = nb_d1b[par][w + 1];
-            } else {            // rightmost column of the tile: D1 is constant there
-                n1a = D1a[K - 1];   // (exact for the last tile, whose right end is past W)
-                n1b = D1b[K - 1];
-            }
+            n1a = D1a[WK - 1];
+            n1b = D1b[WK - 1];
         }
         if (lane == 0) {
-            if (w > 0) {
-                n2a = nb_d2a[par][w - 1];
-                n2b = nb_d2b[par][w - 1];
-            } else {            // leftmost column: D2 = 0 left of the image (tile 0)
-                n2a = 0;
-                n2b = 0;
-            }
+            n2a = 0;
+            n2b = 0;
         }
-        // P(y, c) for this thread's columns; e = P(y, cs-1)
-        uint32_t P1[K], P2[K];
+        uint32_t P1[WK], P2[WK];
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
+        for (int k = 0; k < WK; ++k) {
             P1[k] = e1 + p1[k];
             P2[k] = e2 + p2[k];
         }
         // D2 moves one column right: D2(y, c) = P(y, c-1) + D2(y-1, c-1)
 #pragma unroll
-        for (int k = K - 1; k >= 1; --k) {
+        for (int k = WK - 1; k >= 1; --k) {
             D2a[k] = (TS)P1[k - 1] + D2a[k - 1];
             D2b[k] = (TQ)P2[k - 1] + D2b[k - 1];
         }
@@ -726,16 +750,16 @@ __global__ void __launch_bounds__(WT) k_tab_write(const WriteArgs a) {
         D2b[0] = (TQ)e2 + n2b;
         // D1 moves one column left: D1(y, c) = P(y, c) + D1(y-1, c+1)
 #pragma unroll
-        for (int k = 0; k < K - 1; ++k) {
+        for (int k = 0; k < WK - 1; ++k) {
             D1a[k] = (TS)P1[k] + D1a[k + 1];
             D1b[k] = (TQ)P2[k] + D1b[k + 1];
         }
-        D1a[K - 1] = (TS)P1[K - 1] + n1a;
-        D1b[K - 1] = (TQ)P2[K - 1] + n1b;
-        TS T1v[K];
-        TQ T2v[K];
+        D1a[WK - 1] = (TS)P1[WK - 1] + n1a;
+        D1b[WK - 1] = (TQ)P2[WK - 1] + n1b;
+        TS T1v[WK];
+        TQ T2v[WK];
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
+        for (int k = 0; k < WK; ++k) {
             L1a[k] += (TS)P1[k];
             L2a[k] += (TQ)P2[k];
             T1v[k] = D1a[k] - D2a[k];
@@ -743,21 +767,52 @@ __global__ void __launch_bounds__(WT) k_tab_write(const WriteArgs a) {
         }
         const int64_t rowL = (int64_t)(y + 1) * a.pL + kColOffset;
         const int64_t rowT = (int64_t)(y + 1) * a.pT + kColOffset;
+        // the buffer of row rr - 2 is free once its copies have read it
+        if (rr >= 2 && lane == 0)
+            asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+        __syncwarp();
         if (wL) {
-            store4(a.L1lo, a.L1hi, rowL + cs + 1, L1a);
-            store4(a.L2lo, a.L2hi, rowL + cs + 1, L2a);
+            put8(obuf[par][PL1], obuf[par][PL1 + HS], ob, L1a);
+            put8(obuf[par][PL2], obuf[par][PL2 + HQ], ob, L2a);
         }
         if (wT) {
-            store4(a.T1lo, a.T1hi, rowT + cs + 1, T1v);
-            store4(a.T2lo, a.T2hi, rowT + cs + 1, T2v);
+            put8(obuf[par][PT1], obuf[par][PT1 + HS], ob, T1v);
+            put8(obuf[par][PT2], obuf[par][PT2 + HQ], ob, T2v);
         }
         if (wEdge) {   // b = 0: L is zero, T is cone(y, -1) = D1(y, -1)
             store1(a.L1lo, a.L1hi, rowL, (TS)0);
             store1(a.L2lo, a.L2hi, rowL, (TQ)0);
-            store1(a.T1lo, a.T1hi, rowT, T1v[K - 1]);
-            store1(a.T2lo, a.T2hi, rowT, T2v[K - 1]);
+            store1(a.T1lo, a.T1hi, rowT, T1v[WK - 1]);
+            store1(a.T2lo, a.T2hi, rowT, T2v[WK - 1]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {   // row (y + 1), columns b = c0 + 1 .. : 16-byte aligned in every plane
+            uint32_t *dst[NPL];
+            int k = 0;
+            dst[k++] = a.L1lo + rowL + c0 + 1;
+            if (HS) dst[k++] = a.L1hi + rowL + c0 + 1;
+            dst[k++] = a.L2lo + rowL + c0 + 1;
+            if (HQ) dst[k++] = a.L2hi + rowL + c0 + 1;
+            dst[k++] = a.T1lo + rowT + c0 + 1;
+            if (HS) dst[k++] = a.T1hi + rowT + c0 + 1;
+            dst[k++] = a.T2lo + rowT + c0 + 1;
+            if (HQ) dst[k++] = a.T2hi + rowT + c0 + 1;
+#pragma unroll
+            for (int pl = 0; pl < NPL; ++pl) {
+                const uint32_t nb = pl < PT1 ? bytesL : bytesT;
+                if (nb)
+                    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst[pl]),
+                                 "r"((uint32_t)__cvta_generic_to_shared(&obuf[par][pl][0])), "r"(nb)
+                                 : "memory");
+            }
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
         }
     }
+    // the copies read shared memory until they complete
+    if (lane == 0)
+        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    __syncwarp();
 }
 
 template <typename TS, typename TQ>
@@ -777,7 +832,7 @@ cudaError_t launch_all(const Geometry &g, const Scratch &s, const uint8_t *img, 
         return e;
     WriteArgs wa{img, pitch, g, s, L1.lo, L1.hi, L2.lo, L2.hi, T1.lo, T1.hi, T2.lo, T2.hi,
                  L1.pitch, T1.pitch, aligned8};
-    return launch_pdl(k_tab_write<TS, TQ>, dim3(g.m, g.n), dim3(WT), st, wa);
+    return launch_pdl(k_tab_write<TS, TQ>, dim3(g.mw, g.n), dim3(32), st, wa);
 }
 
 }  // namespace
