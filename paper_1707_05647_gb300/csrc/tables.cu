@@ -152,15 +152,60 @@ __device__ __forceinline__ uint2 load8(const uint8_t *img, int64_t pitch, int H,
     return make_uint2(lo, hi);
 }
 
+constexpr int TROW = SLOTS + 32;   // smem bytes per tile row: word reads past the last slot stay inside
+
+// Rows r..r+3 (one 32-bit word each, byte k = column k) -> c[k] = column k's four rows.
+__device__ __forceinline__ void transpose4(uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3, uint32_t (&c)[4]) {
+    const uint32_t t0 = __byte_perm(r0, r1, 0x5140), t1 = __byte_perm(r0, r1, 0x7362);
+    const uint32_t t2 = __byte_perm(r2, r3, 0x5140), t3 = __byte_perm(r2, r3, 0x7362);
+    c[0] = __byte_perm(t0, t2, 0x5410);
+    c[1] = __byte_perm(t0, t2, 0x7632);
+    c[2] = __byte_perm(t1, t3, 0x5410);
+    c[3] = __byte_perm(t1, t3, 0x7632);
+}
+
+// Sums of I and I^2 over the band's B rows along four adjacent lines whose
+// pixels in row rr start at smem byte O + off(rr), O a multiple of 4:
+// MODE 0 columns (off = 0), MODE 1 anti-diagonals (off = B-1-rr: the line
+// through (r_end - k, x' + k)), MODE 2 diagonals (off = rr-(B-1): through
+// (r_end - k, x'' - k)).  One 32-bit window per row (a funnel shift of two
+// aligned words), 4x4 byte transposes, dp4a for both sums.
+template <int MODE>
+__device__ __forceinline__ void line_sums(const uint32_t *t32, int O, uint32_t (&s1)[4], uint32_t (&s2)[4]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        s1[k] = s2[k] = 0;
+    const int Ow = O >> 2;
+#pragma unroll
+    for (int r = 0; r < B; r += 4) {
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int rr = r + q;
+            const int off = MODE == 0 ? 0 : (MODE == 1 ? B - 1 - rr : rr - (B - 1));
+            const int sh = off & 3;                       // O is a multiple of 4
+            const uint32_t *row = t32 + rr * (TROW / 4) + Ow + (off - sh) / 4;
+            w[q] = sh ? __funnelshift_r(row[0], row[1], 8 * sh) : row[0];
+        }
+        uint32_t c[4];
+        transpose4(w[0], w[1], w[2], w[3], c);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            s1[k] = __dp4a(c[k], 0x01010101u, s1[k]);
+            s2[k] = __dp4a(c[k], c[k], s2[k]);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(NT) k_tab_reduce(const ReduceArgs a) {
     pdl_begin();
-    __shared__ __align__(16) uint8_t tile[B][SLOTS];
+    __shared__ __align__(16) uint8_t tile[B][TROW];
     const Geometry &g = a.g;
     const int j = blockIdx.x, i = blockIdx.y, t = threadIdx.x;
     const int r0 = i * B;
     const int c0 = j * CW;
     const int c1 = min(c0 + CW, g.W);
-    const int base = c0 - HALO;                  // smem column 0
+    const int base = c0 - HALO;                  // smem column 0 (a multiple of 4)
     // load the band (zero outside the image): thread t covers 8 columns of
     // B / (NT / 128) rows, all loads in flight
     {
@@ -174,8 +219,11 @@ __global__ void __launch_bounds__(NT) k_tab_reduce(const ReduceArgs a) {
 #pragma unroll
         for (int k = 0; k < RPT; ++k)
             *reinterpret_cast<uint2 *>(&tile[rb + k][8 * (t & 127)]) = w[k];
+        if (t < B)   // the row pads are read only for lines past the tile, whose sums are dropped
+            *reinterpret_cast<uint4 *>(&tile[t][SLOTS]) = make_uint4(0, 0, 0, 0);
     }
     __syncthreads();
+    const uint32_t *t32 = reinterpret_cast<const uint32_t *>(&tile[0][0]);
     // row sums over the warp tiles' shifted chunks [c0w-HALO, c0w-HALO+WCW),
     // c0w = (j*WPR + q)*WCW: 8 threads per (row, chunk), 6 words each
     {
@@ -185,17 +233,13 @@ __global__ void __launch_bounds__(NT) k_tab_reduce(const ReduceArgs a) {
 #pragma unroll 1
         for (int u = t / TPI; u < B * WPR; u += NT / TPI) {
             const int rr = u / WPR, q = u % WPR;
-            const uint32_t *row = reinterpret_cast<const uint32_t *>(&tile[rr][0]) + q * (WCW / 4) + sub * WPI;
+            const uint32_t *row = t32 + rr * (TROW / 4) + q * (WCW / 4) + sub * WPI;
             uint32_t s1 = 0, s2 = 0;
 #pragma unroll
             for (int w4i = 0; w4i < WPI; ++w4i) {
                 const uint32_t w4 = row[w4i];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const uint32_t v = (w4 >> (8 * k)) & 0xffu;
-                    s1 += v;
-                    s2 += v * v;
-                }
+                s1 = __dp4a(w4, 0x01010101u, s1);
+                s2 = __dp4a(w4, w4, s2);
             }
 #pragma unroll
             for (int o = 1; o < TPI; o <<= 1) {
@@ -211,43 +255,42 @@ __global__ void __launch_bounds__(NT) k_tab_reduce(const ReduceArgs a) {
         }
     }
     const size_t W = g.W, WD = g.W + B - 1;
-    // column sums
-    for (int x = c0 + t; x < c1; x += NT) {
-        uint32_t s1 = 0, s2 = 0;
-#pragma unroll 8
-        for (int rr = 0; rr < B; ++rr) {
-            const uint32_t v = tile[rr][x - base];
-            s1 += v;
-            s2 += v * v;
-        }
-        a.s.cs1[(size_t)i * W + x] = s1;
-        a.s.cs2[(size_t)i * W + x] = s2;
+    uint32_t s1[4], s2[4];
+    // column sums, four columns per step
+    for (int x0 = c0 + 4 * t; x0 < c1; x0 += 4 * NT) {
+        line_sums<0>(t32, x0 - base, s1, s2);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (x0 + k < c1) {
+                a.s.cs1[(size_t)i * W + x0 + k] = s1[k];
+                a.s.cs2[(size_t)i * W + x0 + k] = s2[k];
+            }
     }
-    // anti-diagonal sums through (r_end, x'): sum_k I(r_end-k, x'+k)
+    // anti-diagonal sums through (r_end, x'): sum_k I(r_end-k, x'+k), x' in [xa0, c1)
     const int xa0 = (j == 0) ? -(B - 1) : c0;
-    for (int xp = xa0 + t; xp < c1; xp += NT) {
-        uint32_t s1 = 0, s2 = 0;
-#pragma unroll 8
-        for (int k = 0; k < B; ++k) {
-            const uint32_t v = tile[B - 1 - k][xp + k - base];
-            s1 += v;
-            s2 += v * v;
+    for (int xp0 = (j == 0 ? -B : c0) + 4 * t; xp0 < c1; xp0 += 4 * NT) {
+        line_sums<1>(t32, xp0 - base, s1, s2);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int xp = xp0 + k;
+            if (xp >= xa0 && xp < c1) {
+                a.s.ad1[(size_t)i * WD + xp + B - 1] = s1[k];
+                a.s.ad2[(size_t)i * WD + xp + B - 1] = s2[k];
+            }
         }
-        a.s.ad1[(size_t)i * WD + xp + B - 1] = s1;
-        a.s.ad2[(size_t)i * WD + xp + B - 1] = s2;
     }
-    // diagonal sums through (r_end, x''): sum_k I(r_end-k, x''-k)
+    // diagonal sums through (r_end, x''): sum_k I(r_end-k, x''-k), x'' in [c0, xm1)
     const int xm1 = (j == g.m - 1) ? g.W + B - 1 : c1;
-    for (int xpp = c0 + t; xpp < xm1; xpp += NT) {
-        uint32_t s1 = 0, s2 = 0;
-#pragma unroll 8
-        for (int k = 0; k < B; ++k) {
-            const uint32_t v = tile[B - 1 - k][xpp - k - base];
-            s1 += v;
-            s2 += v * v;
+    for (int xpp0 = c0 + 4 * t; xpp0 < xm1; xpp0 += 4 * NT) {
+        line_sums<2>(t32, xpp0 - base, s1, s2);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int xpp = xpp0 + k;
+            if (xpp < xm1) {
+                a.s.md1[(size_t)i * WD + xpp] = s1[k];
+                a.s.md2[(size_t)i * WD + xpp] = s2[k];
+            }
         }
-        a.s.md1[(size_t)i * WD + xpp] = s1;
-        a.s.md2[(size_t)i * WD + xpp] = s2;
     }
 }
 
