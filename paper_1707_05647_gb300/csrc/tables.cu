@@ -337,7 +337,7 @@ __device__ __forceinline__ void carry_contrib(const CarryArgs &a, int part, int 
 constexpr int CG = 8;   // band groups per carry block
 constexpr int CQ = 16;  // bands per group kept in registers (more bands: reloaded)
 
-__global__ void __launch_bounds__(32 * CG) k_tab_carry(const CarryArgs a) {
+__global__ void __launch_bounds__(32 * CG, 5) k_tab_carry(const CarryArgs a) {
     pdl_begin();
     __shared__ uint32_t sum1[CG][33], sum2[CG][33];
     const Geometry &g = a.g;
@@ -457,7 +457,7 @@ __device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v, int lane) {
 constexpr int PT = 256;
 
 template <typename TS, typename TQ>
-__global__ void __launch_bounds__(PT) k_tab_prefix(const PrefixArgs a) {
+__global__ void __launch_bounds__(PT, 4) k_tab_prefix(const PrefixArgs a) {
     pdl_begin();
     __shared__ uint64_t wsum[PT / 32], red[PT / 32];
     const Geometry &g = a.g;
