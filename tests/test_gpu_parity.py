@@ -51,6 +51,25 @@ def test_tables_bit_exact(ctx, H, W, bits):
         scr.tables_release(ctx, tb)
 
 
+# widths around the table writer's 192-column warp tiles and the band
+# reduction's 960-column tiles (one column short, exact, one past), heights
+# around the 32-row bands
+EDGE_SIZES = [(33, 191), (32, 192), (65, 193), (40, 383), (31, 384), (35, 385), (96, 959), (33, 960),
+              (64, 1152), (1, 192), (32, 1)]
+
+
+@pytest.mark.parametrize("H,W", EDGE_SIZES)
+@pytest.mark.parametrize("bits", [(32, 64), (64, 64)])
+@pytest.mark.parametrize("kind", ["uniform", "max"])
+def test_tables_tile_edges(ctx, H, W, bits, kind):
+    img = synth.random_image(H * 7 + W, H, W, kind)
+    tb = scr.build_tables(ctx, torch.from_numpy(img).cuda(), bits[0], bits[1])
+    try:
+        _tables_equal(ctx, tb, img, bits)
+    finally:
+        scr.tables_release(ctx, tb)
+
+
 @pytest.mark.parametrize("kind", ["max", "zero", "blobs"])
 def test_tables_special_images(ctx, kind):
     H, W = 257, 1100
