@@ -478,10 +478,13 @@ int server_lru_victims(const uint64_t *bytes, const uint64_t *last_use, const in
 /* ---- whole path from host memory ----------------------------------------- */
 
 /* End-to-end call for host-resident data: copy the image (host, pitch bytes per
- * row) to the device, build its tables, screen it against the template, copy
- * the count and the first list_cap keys back to list_host.  Device buffers come
- * from the context's pool and are returned before the call ends.  Synchronous;
- * returns SCR_EOVERFLOW like screen_positions. */
+ * row) to the device, build its tables, screen it against the template, and
+ * return the count and the first list_cap keys in list_host.  When list_host
+ * is pinned, mapped host memory (cudaHostAlloc / cudaMallocHost), the device
+ * writes the keys into it directly and the call synchronises once; otherwise
+ * the count and the keys are copied back.  Device buffers come from the
+ * context's pool and are returned before the call ends.  Synchronous; returns
+ * SCR_EOVERFLOW like screen_positions. */
 int screen_host(scr_ctx *ctx, const uint8_t *img_host, int32_t H, int32_t W, int64_t pitch,
                 int32_t sum_bits, int32_t sq_bits, const scr_tmpl *tm, const scr_params *p,
                 uint64_t *list_host, uint64_t list_cap, uint64_t *n_survivors,

@@ -569,6 +569,10 @@ int screen_init(scr_ctx **ctx, int device, uint64_t hbm_budget_bytes) {
     }
     if (e == cudaSuccess)
         e = cudaMallocHost((void **)&c->pinned, 64);
+    if (e == cudaSuccess && cudaHostGetDevicePointer((void **)&c->pinned_dev, c->pinned, 0) != cudaSuccess) {
+        c->pinned_dev = nullptr;   // screen_host then reads the count back with a copy
+        cudaGetLastError();
+    }
     if (e != cudaSuccess) {
         if (c->pool)
             cudaMemPoolDestroy(c->pool);
@@ -1197,33 +1201,60 @@ int screen_host(scr_ctx *c, const uint8_t *img_host, int32_t H, int32_t W, int64
     DeviceGuard dg(c->device);
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t dpitch = (W + 15) / 16 * 16;
+    // A pinned, mapped list buffer (cudaHostAlloc / cudaMallocHost memory) is
+    // written by the compaction directly, with the count going to the
+    // context's pinned slot: one synchronisation instead of a count read, a
+    // list copy and two.
+    uint64_t *list_map = nullptr;
+    if (list_cap && c->pinned_dev) {
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, list_host) == cudaSuccess) {
+            if (pa.type == cudaMemoryTypeHost && pa.devicePointer)
+                list_map = (uint64_t *)pa.devicePointer;
+        } else {
+            cudaGetLastError();
+        }
+    }
     Scoped img(c, st), mask(c, st), list(c, st);
     const uint64_t words = (uint64_t)p->n_scales * H * ((W + 31) / 32);
     if ((rc = img.take((size_t)dpitch * H)) || (rc = mask.take(words * 4)) ||
-        (rc = list.take(std::max<uint64_t>(list_cap, 1) * 8 + 64)))
+        (!list_map && (rc = list.take(std::max<uint64_t>(list_cap, 1) * 8 + 64))))
         return rc;
     CUDA_TRY(cudaMemcpy2DAsync(img.p, dpitch, img_host, pitch, W, H, cudaMemcpyHostToDevice, st));
     scr_tables *t = nullptr;
     if ((rc = build_tables(c, (const uint8_t *)img.p, H, W, dpitch, sum_bits, sq_bits, stream, &t)))
         return rc;
-    uint64_t *cnt_dev = (uint64_t *)((char *)list.p + std::max<uint64_t>(list_cap, 1) * 8);
-    rc = screen_positions_async(c, t, tm, p, (uint32_t *)mask.p, words, list_cap ? (uint64_t *)list.p : nullptr,
-                                list_cap, cnt_dev, stream);
-    if (!rc) {
-        std::lock_guard<std::mutex> lk(c->mu);
-        cudaError_t e = cudaMemcpyAsync(c->pinned, cnt_dev, 8, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess)
-            e = cudaStreamSynchronize(st);
-        if (e == cudaSuccess) {
-            *n_survivors = c->pinned[0];
-            const uint64_t k = std::min<uint64_t>(*n_survivors, list_cap);
-            if (k)
-                e = cudaMemcpyAsync(list_host, list.p, k * 8, cudaMemcpyDeviceToHost, st);
+    if (list_map) {
+        std::lock_guard<std::mutex> lk(c->mu);   // the pinned count slot
+        rc = screen_positions_async(c, t, tm, p, (uint32_t *)mask.p, words, list_map, list_cap, c->pinned_dev,
+                                    stream);
+        if (!rc) {
+            const cudaError_t e = cudaStreamSynchronize(st);
+            if (e == cudaSuccess)
+                *n_survivors = c->pinned[0];
+            else
+                rc = fail(SCR_ECUDA, "screen_host: %s", cudaGetErrorString(e));
+        }
+    } else {
+        uint64_t *cnt_dev = (uint64_t *)((char *)list.p + std::max<uint64_t>(list_cap, 1) * 8);
+        rc = screen_positions_async(c, t, tm, p, (uint32_t *)mask.p, words, list_cap ? (uint64_t *)list.p : nullptr,
+                                    list_cap, cnt_dev, stream);
+        if (!rc) {
+            std::lock_guard<std::mutex> lk(c->mu);
+            cudaError_t e = cudaMemcpyAsync(c->pinned, cnt_dev, 8, cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess)
                 e = cudaStreamSynchronize(st);
+            if (e == cudaSuccess) {
+                *n_survivors = c->pinned[0];
+                const uint64_t k = std::min<uint64_t>(*n_survivors, list_cap);
+                if (k)
+                    e = cudaMemcpyAsync(list_host, list.p, k * 8, cudaMemcpyDeviceToHost, st);
+                if (e == cudaSuccess)
+                    e = cudaStreamSynchronize(st);
+            }
+            if (e != cudaSuccess)
+                rc = fail(SCR_ECUDA, "screen_host: %s", cudaGetErrorString(e));
         }
-        if (e != cudaSuccess)
-            rc = fail(SCR_ECUDA, "screen_host: %s", cudaGetErrorString(e));
     }
     tables_release(c, t);
     if (!rc && *n_survivors > list_cap)

@@ -80,6 +80,7 @@ struct scr_ctx {
     std::set<scr_server *> servers;
     std::map<std::string, std::pair<int, int>> tuned;   // batch shape -> (words per warp, blocks per SM)
     uint64_t *pinned = nullptr;      // 8-byte pinned slot for counts
+    uint64_t *pinned_dev = nullptr;  // the same slot as the device sees it (null if not mapped)
 };
 
 struct scr_batch {

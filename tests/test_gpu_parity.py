@@ -183,6 +183,29 @@ def test_screen_host_matches_oracle(ctx):
     assert np.array_equal(lst[:n], o["list"])
 
 
+@pytest.mark.parametrize("pinned_list", [False, True])
+@pytest.mark.parametrize("short", [False, True])
+def test_screen_host_list_buffers(ctx, pinned_list, short):
+    """A pinned list buffer takes the one-synchronisation path (keys written by
+    the device into host memory); a pageable one the copy-back path.  Both give
+    the oracle's list, and a short buffer its first keys with the exact count."""
+    wl = synth.small_planted(2003)
+    o = oracle_run(wl)
+    assert o["count"] > 4
+    tm = scr.template_features(ctx, wl.template, wl.r, wl.t_min, wl.features)
+    cap = o["count"] - 3 if short else o["count"] + 10
+    if pinned_list:
+        lst = torch.full((cap,), -1, dtype=torch.int64).pin_memory().numpy().view(np.uint64)
+    else:
+        lst = np.full(cap, np.uint64(2**64 - 1), np.uint64)
+    img = torch.from_numpy(wl.image).pin_memory().numpy() if pinned_list else wl.image
+    n, over = scr.screen_host(ctx, img, wl.sum_bits, wl.sq_bits, tm, params_of(wl), lst)
+    assert n == o["count"] and over == short
+    k = min(n, cap)
+    assert np.array_equal(lst[:k], o["list"][:k])
+    assert np.all(lst[k:] == np.uint64(2**64 - 1))
+
+
 def test_budget_is_enforced(ctx):
     small = scr.screen_init(0, 1 << 20)
     try:
