@@ -1208,12 +1208,13 @@ int screen_host(scr_ctx *c, const uint8_t *img_host, int32_t H, int32_t W, int64
     uint64_t *list_map = nullptr;
     if (list_cap && c->pinned_dev) {
         cudaPointerAttributes pa;
-        if (cudaPointerGetAttributes(&pa, list_host) == cudaSuccess) {
-            if (pa.type == cudaMemoryTypeHost && pa.devicePointer)
-                list_map = (uint64_t *)pa.devicePointer;
-        } else {
-            cudaGetLastError();
-        }
+        void *d = nullptr;
+        // pinned host memory that this device can address (asked with the
+        // context's device current); anything else takes the copy-back path
+        if (cudaPointerGetAttributes(&pa, list_host) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+            cudaHostGetDevicePointer(&d, list_host, 0) == cudaSuccess && d)
+            list_map = (uint64_t *)d;
+        cudaGetLastError();
     }
     Scoped img(c, st), mask(c, st), list(c, st);
     const uint64_t words = (uint64_t)p->n_scales * H * ((W + 31) / 32);
