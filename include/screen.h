@@ -69,7 +69,7 @@ enum {
     SCR_ETIMEOUT = -5,    /* reserved: a bounded device-side wait gave up */
     SCR_EOVERFLOW = -6,   /* more survivors than list capacity (mask still complete) */
     SCR_EEVICTED = -7,    /* the image's tables and host copy were dropped (server_forget) */
-    SCR_EUNSUPPORTED = -8 /* valid request outside what this build implements */
+    SCR_EUNSUPPORTED = -8 /* valid request outside what the library implements */
 };
 
 enum { SCR_F_MEAN = 1, SCR_F_VAR = 2, SCR_F_GRAD = 4, SCR_F_PREWITT = 8 };
