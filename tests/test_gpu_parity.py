@@ -161,6 +161,28 @@ def test_ragged_sizes_and_large_radii(ctx, H, W):
     scr.tables_release(ctx, g["tables"])
 
 
+@pytest.mark.parametrize("H,W", [(40, 65535), (65535, 40)])
+def test_maximum_dimension(ctx, H, W):
+    """The largest side the boundary accepts (65535), on a thin image: 2048
+    bands or 342 writer tiles, keys with y or x near 2^16; tables and the
+    screen against the oracle."""
+    img = synth.random_image(H ^ W, H, W, "uniform")
+    tb = scr.build_tables(ctx, torch.from_numpy(img).cuda(), 32, 64)
+    try:
+        _tables_equal(ctx, tb, img, (32, 64))
+    finally:
+        scr.tables_release(ctx, tb)
+    r = 10
+    tm = img[:2 * r + 1, :2 * r + 1].copy()
+    wl = synth.Workload("max side", img, tm, r, [6, 9, 13, 17], 7, 7,
+                        synth.Tolerances(synth.Fraction(1, 50), synth.Fraction(1, 20), synth.Fraction(1, 5),
+                                         synth.Fraction(4)), 32, 64, (0, 0), 1.0, 0.0)
+    g, o = gpu_run(ctx, wl), oracle_run(wl)
+    assert o["count"] > 0
+    _compare(g, o)
+    scr.tables_release(ctx, g["tables"])
+
+
 def test_list_overflow_reports_true_count(ctx):
     wl = synth.config1(1000)
     wl.tol = synth.Tolerances(synth.Fraction(1, 2), synth.Fraction(9, 10))
