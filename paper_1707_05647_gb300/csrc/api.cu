@@ -1201,6 +1201,11 @@ int screen_host(scr_ctx *c, const uint8_t *img_host, int32_t H, int32_t W, int64
     DeviceGuard dg(c->device);
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t dpitch = (W + 15) / 16 * 16;
+    // the image copy goes first, so the host work below overlaps it
+    Scoped img(c, st), mask(c, st), list(c, st);
+    if ((rc = img.take((size_t)dpitch * H)))
+        return rc;
+    CUDA_TRY(cudaMemcpy2DAsync(img.p, dpitch, img_host, pitch, W, H, cudaMemcpyHostToDevice, st));
     // A pinned, mapped list buffer (cudaHostAlloc / cudaMallocHost memory) is
     // written by the compaction directly, with the count going to the
     // context's pinned slot: one synchronisation instead of a count read, a
@@ -1216,15 +1221,17 @@ int screen_host(scr_ctx *c, const uint8_t *img_host, int32_t H, int32_t W, int64
             list_map = (uint64_t *)d;
         cudaGetLastError();
     }
-    Scoped img(c, st), mask(c, st), list(c, st);
     const uint64_t words = (uint64_t)p->n_scales * H * ((W + 31) / 32);
-    if ((rc = img.take((size_t)dpitch * H)) || (rc = mask.take(words * 4)) ||
-        (!list_map && (rc = list.take(std::max<uint64_t>(list_cap, 1) * 8 + 64))))
+    // an error from here on returns only after the copy has stopped reading img_host
+    if ((rc = mask.take(words * 4)) || (!list_map && (rc = list.take(std::max<uint64_t>(list_cap, 1) * 8 + 64)))) {
+        cudaStreamSynchronize(st);
         return rc;
-    CUDA_TRY(cudaMemcpy2DAsync(img.p, dpitch, img_host, pitch, W, H, cudaMemcpyHostToDevice, st));
+    }
     scr_tables *t = nullptr;
-    if ((rc = build_tables(c, (const uint8_t *)img.p, H, W, dpitch, sum_bits, sq_bits, stream, &t)))
+    if ((rc = build_tables(c, (const uint8_t *)img.p, H, W, dpitch, sum_bits, sq_bits, stream, &t))) {
+        cudaStreamSynchronize(st);
         return rc;
+    }
     if (list_map) {
         std::lock_guard<std::mutex> lk(c->mu);   // the pinned count slot
         rc = screen_positions_async(c, t, tm, p, (uint32_t *)mask.p, words, list_map, list_cap, c->pinned_dev,
@@ -1257,6 +1264,8 @@ int screen_host(scr_ctx *c, const uint8_t *img_host, int32_t H, int32_t W, int64
                 rc = fail(SCR_ECUDA, "screen_host: %s", cudaGetErrorString(e));
         }
     }
+    if (rc)   // nothing queued may still read img_host or write list_host
+        cudaStreamSynchronize(st);
     tables_release(c, t);
     if (!rc && *n_survivors > list_cap)
         return fail(SCR_EOVERFLOW, "%llu survivors exceed list capacity %llu", (unsigned long long)*n_survivors,
