@@ -63,10 +63,13 @@ def test_joint_matches_oracle(ctx, features, n_areas, qs):
 
 
 @pytest.mark.parametrize("bits", [(32, 32), (64, 64)])
-def test_joint_ragged_sizes_and_table_widths(ctx, bits):
+@pytest.mark.parametrize("H,W", [(161, 97), (200, 300), (97, 520)])
+def test_joint_ragged_sizes_and_table_widths(ctx, bits, H, W):
+    """Widths with a partial last warp of 8 mask words (97: 4 words; 300: 10;
+    520: 17), heights off the 32-row bands."""
     rng = np.random.default_rng(77)
-    wl = synth.small_planted(seed=4100, H=256, r=12, n_scales=3)
-    img = np.ascontiguousarray(wl.image[:161, :97])
+    wl = synth.small_planted(seed=4100, H=max(256, H, W), r=12, n_scales=3)
+    img = np.ascontiguousarray(wl.image[:H, :W])
     area_radii, bands = synth.joint_areas(wl.r, wl.scales, 3)
     t_min = max(2, min(b[0] for b in bands))
     q = (Fraction(9, 2), Fraction(5, 2), Fraction(11, 2))

@@ -35,7 +35,8 @@ def _tables(ctx, img, bits=(32, 64)):
 
 
 @pytest.mark.parametrize("H,W", [(1, 1), (7, 300), (300, 7), (257, 1031), (1200, 900),
-                                 (32, 256), (33, 255), (31, 257), (64, 1024), (65, 2049), (96, 513)])
+                                 (32, 256), (33, 255), (31, 257), (64, 1024), (65, 2049), (96, 513),
+                                 (65535, 40), (40, 65535)])
 def test_moment_tables_bit_exact(ctx, H, W):
     img = synth.random_image(H * 7 + W, H, W)
     tab = _tables(ctx, img)
