@@ -288,7 +288,7 @@ def run_e2e(scr, torch, ctx, wl, tm, p, cap, ncand, args):
         scr.screen_host(ctx, img_host.numpy(), wl.sum_bits, wl.sq_bits, tm, p, lst_host.numpy())
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    e2e_steps = max(3, min(args.steps, 10))
+    e2e_steps = max(10, min(args.steps, 100))
     for _ in range(e2e_steps):
         n_e2e, _ = scr.screen_host(ctx, img_host.numpy(), wl.sum_bits, wl.sq_bits, tm, p, lst_host.numpy())
     e2e_s = (time.perf_counter() - t0) / e2e_steps
