@@ -97,9 +97,18 @@ k_screen(const __grid_constant__ ScreenArgs a) {
             // star sum: square (upright table) + diamond (cone table), Sec. 4
             const Corners c(L1, T1, p.oL, p.oT);
             if (xw_lo >= p.x_lo && xw_hi <= p.x_hi) {   // warp-uniform: every word valid
+                // all 8 x WPW corner reads are written before any sum, which lets
+                // the scheduler issue them back to back (measured ~4% faster than
+                // summing word by word)
+                uint32_t v[WPW][8];
 #pragma unroll
                 for (int j = 0; j < WPW; ++j)
-                    S[j] = c.sum(j);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        v[j][k] = ld(c.p[k] + 32 * j);
+#pragma unroll
+                for (int j = 0; j < WPW; ++j)
+                    S[j] = v[j][0] - v[j][1] - v[j][2] + v[j][3] + v[j][4] - v[j][5] - v[j][6] + v[j][7];
                 keep = (1u << WPW) - 1;
             } else {
                 const uint32_t span = (uint32_t)(p.x_hi - p.x_lo);
