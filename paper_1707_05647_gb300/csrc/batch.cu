@@ -159,9 +159,16 @@ __global__ void __launch_bounds__(32 * kBatchWarps, (WPW >= 8 ? 3 : 4)) k_batch(
             const StarCorners c(L1 + e, T1 + e, oL, oT);
             uint32_t S[WPW], live = 0;
             if (xs >= x_lo && xs + 32 * WPW - 1 <= x_hi) {   // warp-uniform: every position valid
+                // all corner reads written before any sum: issued back to back
+                uint32_t v[WPW][8];
 #pragma unroll
                 for (int j = 0; j < WPW; ++j)
-                    S[j] = c.sum(j);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        v[j][k] = ldb(c.p[k] + 32 * j);
+#pragma unroll
+                for (int j = 0; j < WPW; ++j)
+                    S[j] = v[j][0] - v[j][1] - v[j][2] + v[j][3] + v[j][4] - v[j][5] - v[j][6] + v[j][7];
                 live = (1u << WPW) - 1;
             } else {
                 const uint32_t span = (uint32_t)(x_hi - x_lo);

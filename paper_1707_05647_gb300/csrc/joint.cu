@@ -149,14 +149,31 @@ __global__ void __launch_bounds__(32 * kJointWarps) k_screen_joint(const JointAr
             const uint32_t *q0 = T + ar0.oT[0], *q1 = T + ar0.oT[1], *q2 = T + ar0.oT[2], *q3 = T + ar0.oT[3];
             const uint32_t span = (uint32_t)(sc.x_hi - sc.x_lo);
             uint32_t S[kJointWPW];
+            const int xw_lo = w0 * 32, xw_hi = xw_lo + 32 * kJointWPW - 1;
+            if (xw_lo >= sc.x_lo && xw_hi <= sc.x_hi) {   // warp-uniform: every word valid
+                // all corner reads written before any sum: issued back to back
+                uint32_t v[kJointWPW][8];
 #pragma unroll
-            for (int j = 0; j < kJointWPW; ++j) {
-                const int d = 32 * j;
-                S[j] = 0;
-                if ((uint32_t)(x0 + d - sc.x_lo) <= span) {
-                    S[j] = ldj(p0 + d) - ldj(p1 + d) - ldj(p2 + d) + ldj(p3 + d) + ldj(q0 + d) - ldj(q1 + d) -
-                           ldj(q2 + d) + ldj(q3 + d);
+                for (int j = 0; j < kJointWPW; ++j) {
+                    const int d = 32 * j;
+                    v[j][0] = ldj(p0 + d), v[j][1] = ldj(p1 + d), v[j][2] = ldj(p2 + d), v[j][3] = ldj(p3 + d);
+                    v[j][4] = ldj(q0 + d), v[j][5] = ldj(q1 + d), v[j][6] = ldj(q2 + d), v[j][7] = ldj(q3 + d);
+                }
+#pragma unroll
+                for (int j = 0; j < kJointWPW; ++j) {
+                    S[j] = v[j][0] - v[j][1] - v[j][2] + v[j][3] + v[j][4] - v[j][5] - v[j][6] + v[j][7];
                     keep |= (S[j] - ar0.S_lo <= ar0.S_rng ? 1u : 0u) << j;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < kJointWPW; ++j) {
+                    const int d = 32 * j;
+                    S[j] = 0;
+                    if ((uint32_t)(x0 + d - sc.x_lo) <= span) {
+                        S[j] = ldj(p0 + d) - ldj(p1 + d) - ldj(p2 + d) + ldj(p3 + d) + ldj(q0 + d) - ldj(q1 + d) -
+                               ldj(q2 + d) + ldj(q3 + d);
+                        keep |= (S[j] - ar0.S_lo <= ar0.S_rng ? 1u : 0u) << j;
+                    }
                 }
             }
             if (__any_sync(0xffffffffu, keep != 0)) {
