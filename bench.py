@@ -312,8 +312,8 @@ def emit(args, wl, world, total_s, value, k3_ms, step_ms, launches, clk, n_surv,
                   "model": f"compulsory (tables once across scales + mask + list): {alg} B/launch, "
                            f"{alg / ncand:.2f} B/candidate"}
     binding = ("on-chip: L1/L2 load latency and the L1 data pipe; DRAM traffic is the low "
-               "planes of L1 and T1 once (ncu: L1 LSU wavefronts 66%, L1/TEX 70%, ALU pipe 49%, "
-               "issue 61%, L2 49% of peak on the 3072^2 case)")
+               "planes of L1 and T1 once (ncu: L1 LSU wavefronts 66%, L1/TEX 72%, ALU pipe 52%, "
+               "issue 62%, L2 48% of peak on the 3072^2 case)")
     if alg1 <= peak:
         # Algorithm 1's per-scale traffic, served partly from L2: the fraction of the HBM roof
         # that model implies (kept only while it stays below 1)
