@@ -112,10 +112,21 @@ class Clocks:
                 if any(r[2].replace(".", "").isdigit() for r in rows) else None}
 
 
+def kernel_code_sha256(path):
+    """SHA-256 of a CUDA source with its comments and whitespace removed, so a
+    comment edit does not invalidate counters taken on the same code."""
+    import hashlib
+    import re
+    text = open(path, encoding="utf-8").read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    text = " ".join(text.split())
+    return hashlib.sha256(text.encode()).hexdigest()
+
+
 def recorded_traffic(H, W):
     """DRAM bytes per k_screen launch from the committed ncu capture of the
-    4096x4096 workload, or None if the kernel source changed since."""
-    import hashlib
+    4096x4096 workload, or None if the kernel's code changed since."""
     path = os.path.join(ROOT, "profiles", "k_screen_4096_traffic.txt")
     if (H, W) != (4096, 4096) or not os.path.exists(path):
         return None
@@ -125,7 +136,7 @@ def recorded_traffic(H, W):
             k, v = line.split(":", 1)
             rec[k.strip()] = v.strip()
     src = os.path.join(ROOT, "paper_1707_05647_gb300", "csrc", "features.cu")
-    if rec.get("kernel_source_sha256") != hashlib.sha256(open(src, "rb").read()).hexdigest():
+    if rec.get("kernel_code_sha256") != kernel_code_sha256(src):
         return None
     return int(rec["dram_bytes_per_launch"])
 

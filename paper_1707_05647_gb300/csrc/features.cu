@@ -16,14 +16,15 @@
 // kernel reads only the low 32-bit plane of every table and subtracts modulo
 // 2^32: the result is the exact sum.  Products are formed in 64 bits.
 //
-// Mapping: one warp evaluates one mask word -- 32 consecutive x of one row --
-// for every scale, so each corner read is a coalesced 128-byte row segment and
-// the word is formed with one warp ballot.  The tests run in order mean,
+// Mapping: one warp evaluates WPW consecutive mask words (32 x each) of one
+// row for every scale, so each corner read is a coalesced 128-byte row segment
+// and each word is formed with one warp ballot.  The tests run in order mean,
 // variance, contrast and each later test's corner reads are issued only for
 // lanes still alive, so a warp whose candidates all fail the mean test reads
-// 8 of the 24 corners.  The kernel is bound by instruction issue; corner
-// offsets are precomputed per scale so each read costs one multiply-add and
-// one load.
+// 8 of the 24 corners.  Corner offsets are precomputed per scale, so a read is
+// one load at an immediate offset.  The tables are served from L2 across
+// scales; the kernel is bound by the L1 data pipe and by the latency of those
+// L2-served reads, which is why a scale's reads are issued together.
 #include <cuda_runtime.h>
 #include <stdint.h>
 

@@ -56,3 +56,15 @@ def test_per_scale_fraction_never_quoted_above_one():
     assert r["frac"] <= 1.0
     assert r["model"].startswith("compulsory")
     assert r["per_scale_above_peak"]["achieved"] > r["peak"]
+
+
+def test_traffic_record_follows_kernel_code_not_comments(tmp_path):
+    base = "// a comment\n__global__ void k(int *p) { /* note */ p[0] = 1; }\n"
+    a, b, c = tmp_path / "a.cu", tmp_path / "b.cu", tmp_path / "c.cu"
+    a.write_text(base)
+    b.write_text(base.replace("a comment", "another comment").replace("note", "other"))
+    c.write_text(base.replace("p[0] = 1", "p[0] = 2"))
+    assert bench.kernel_code_sha256(str(a)) == bench.kernel_code_sha256(str(b))
+    assert bench.kernel_code_sha256(str(a)) != bench.kernel_code_sha256(str(c))
+    # the committed record matches the committed kernel
+    assert bench.recorded_traffic(4096, 4096) is not None
