@@ -149,24 +149,33 @@ def measured_peak_gbs():
         return 6800.0, "fallback"
 
 
-def oracle_baseline(wl, max_rows=None, threads=0, split=None):
+def oracle_baseline(wl, max_rows=None, threads=0, split=None, min_seconds=0.0):
     """CPU oracle on the host cores (threads = 0: all, OpenMP over rows in the
-    screen); returns (evals/s, sample, threads used, seconds).  split, a dict,
-    receives the table-build and screen seconds separately."""
+    screen); the sample (tables + screen of the first max_rows rows) is repeated
+    until min_seconds have passed.  Returns (evals/s, sample, threads used,
+    seconds).  split, a dict, receives the mean table-build and screen seconds."""
     import oracle
     img = wl.image if max_rows is None else wl.image[:max_rows]
     H, W = img.shape
     used = oracle.threads(threads if threads > 0 else (os.cpu_count() or 1))
-    t0 = time.perf_counter()
-    tb = oracle.Tables(img)
-    t1 = time.perf_counter()
-    oracle.screen_workload(img, wl.template, wl.r, wl.t_min, wl.radii, wl.features, wl.tol, tables=tb)
-    dt = time.perf_counter() - t0
+    t_tab = t_all = 0.0
+    reps = 0
+    while reps == 0 or t_all < min_seconds:
+        t0 = time.perf_counter()
+        tb = oracle.Tables(img)
+        t1 = time.perf_counter()
+        oracle.screen_workload(img, wl.template, wl.r, wl.t_min, wl.radii, wl.features, wl.tol, tables=tb)
+        t_all += time.perf_counter() - t0
+        t_tab += t1 - t0
+        reps += 1
     if split is not None:
-        split["tables_s"] = t1 - t0
-        split["screen_s"] = dt - (t1 - t0)
+        split["tables_s"] = t_tab / reps
+        split["screen_s"] = (t_all - t_tab) / reps
     n = candidates(H, W, wl.radii)
-    return n / dt, f"{H}x{W} rows of the same image, all {len(wl.radii)} scales, tables + screen", used, dt
+    sample = f"{H}x{W} rows of the same image, all {len(wl.radii)} scales, tables + screen"
+    if reps > 1:
+        sample += f", repeated {reps} times"
+    return n * reps / t_all, sample, used, t_all
 
 
 def oracle_threads(n):
@@ -346,8 +355,8 @@ def emit(args, wl, world, total_s, value, k3_ms, step_ms, launches, clk, n_surv,
     cpu = None
     if not args.no_cpu_baseline:
         split, split1 = {}, {}
-        v, sample, cores, dt = oracle_baseline(wl, split=split)
-        v1, sample1, _, dt1 = oracle_baseline(wl, 1024, threads=1, split=split1)
+        v, sample, cores, dt = oracle_baseline(wl, split=split, min_seconds=10.0)
+        v1, sample1, _, dt1 = oracle_baseline(wl, 1024, threads=1, split=split1, min_seconds=10.0)
         oracle_threads(cores)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
                "seconds": round(dt, 2), "tables_s": round(split["tables_s"], 3),
