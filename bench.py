@@ -1,28 +1,36 @@
 """Benchmark of the screening hot path on GB300.
 
-One step = the whole path on one synthetic 4096x4096 image (the single-large-
-image workload: 8 scales 0.5..2 of a radius-48 template, mean + variance +
-contrast, uint32 sum / uint64 sum^2 tables):
+One step = the whole path on one synthetic image, image already in HBM:
   build_tables (upright + cone tables)  ->  screen_features (star features and
   thresholds -> bitmask)  ->  compact_mask (bitmask -> sorted survivor list).
-`value` = candidate (position x scale) evaluations per second with the image
-already resident in HBM; `e2e` = the same metric through screen_host() with the
-image in pinned host memory and the count + list copied back every step.
+The default workload is the very large single image: 8192x8192 u8 with a
+planted r=64 template and 8 distractor copies at +-3% gain, 16 scales
+0.35..2.8 (R = 22..179), mean + variance + contrast, uint64 sum and sum^2
+tables.  --config 2 runs the 4096x4096 image (r=48, 8 scales 0.5..2, uint32
+sum / uint64 sum^2), --config 1 the 512x512 one.  The default line also carries
+a shorter run of the 4096x4096 workload under "config2".
+
+`value` = candidate (position x scale) evaluations per second; `e2e` = the same
+metric through screen_host() with the image in pinned host memory and the
+count + list copied back every step.  The line reports whether the planted
+match (and each distractor copy) survives, from the mask of the last step.
 
 --impl reference times the CPU oracle (the slow plain implementation the GPU
-path is checked against) on the host cores instead.
-Under torchrun each rank screens its own image (weak scaling, no collective on
-the data path); rank 0 prints one JSON line.
+path is checked against) on the host cores instead, on a row sample of the
+same workload.  Under torchrun each rank screens its own image (weak scaling,
+no collective on the data path); rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import math
 import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -32,16 +40,20 @@ sys.path.insert(0, ROOT)
 
 METRIC = "candidate (position x scale) evaluations/s"
 UNIT = "evals/s"
+FEATURE_NAMES = ((1, "mean"), (2, "variance"), (4, "contrast"))
+
+
+def square_half(R: int) -> int:
+    """n with (2n-1)^2 < 2R^2 < (2n+1)^2, for counting valid positions in reports."""
+    m = math.isqrt(2 * R * R)
+    return (m + 1) // 2
 
 
 def candidates(H, W, radii):
     """Number of valid (scale, y, x) candidates: the star lies inside the image."""
     tot = 0
     for R in radii:
-        n = 0
-        while (2 * n + 1) ** 2 < 2 * R * R:
-            n += 1
-        h = R
+        n, h = square_half(R), R
         ylo, yhi = max(n, h) - 1, H - 1 - max(n, h)
         xlo, xhi = max(n, h) - 1, min(W - 1 - n, W - h)
         if yhi >= ylo and xhi >= xlo:
@@ -49,94 +61,160 @@ def candidates(H, W, radii):
     return tot
 
 
+def table_bytes(H, W, sum_bits, sq_bits):
+    """Bytes of the four tables at full width: L1, L2 are (H+1) x (W+1), T1, T2 (H+1) x (W+2)."""
+    return ((H + 1) * (W + 1) + (H + 1) * (W + 2)) * (sum_bits + sq_bits) // 8
+
+
 def compulsory_bytes(H, W, n_scales, sum_bits, sq_bits, survivors):
     """Compulsory traffic of one screening pass with tables reused across scales:
     the four tables read once (full width), the mask written, the list written."""
-    tables = ((H + 1) * (W + 1) + (H + 1) * (W + 2)) * (sum_bits + sq_bits) // 8
-    return tables + n_scales * H * ((W + 31) // 32) * 4 + 8 * survivors
+    return table_bytes(H, W, sum_bits, sq_bits) + n_scales * H * ((W + 31) // 32) * 4 + 8 * survivors
 
 
 def per_scale_bytes(H, W, n_scales, sum_bits, sq_bits):
     """Algorithmic bytes of one screening launch under the per-scale model of
     Algorithm 1: every scale pass reads the four tables once and writes its mask."""
-    tables = ((H + 1) * (W + 1) + (H + 1) * (W + 2)) * (sum_bits + sq_bits) // 8
     mask = n_scales * H * ((W + 31) // 32) * 4
-    return n_scales * tables + mask
+    return n_scales * table_bytes(H, W, sum_bits, sq_bits) + mask
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi sampling of SM clocks and throttle reasons.  Started before the
+    warm-up; samples carry nvidia-smi's own timestamp, so the summary can keep
+    only those taken inside a window [t0, t1] of host wall-clock time."""
 
-    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 50
 
     def __init__(self, index: int):
         self.index = index
         self.p = None
+        self.f = None
+        self.error = None
 
-    def __enter__(self):
+    def start(self, wait_s: float = 5.0):
         try:
+            self.f = tempfile.TemporaryFile(mode="w+")
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "100"],
-                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-        except OSError:
-            self.p = None
+                                       "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
+                                      stdout=self.f, stderr=subprocess.DEVNULL, text=True)
+        except OSError as e:
+            self.p, self.error = None, f"nvidia-smi not started: {e}"
+            return self
+        t_end = time.time() + wait_s          # wait for the first sample, so the sampler is live
+        while time.time() < t_end and not self.rows():
+            if self.p.poll() is not None:
+                self.error = f"nvidia-smi exited with {self.p.returncode}"
+                break
+            time.sleep(0.05)
         return self
 
-    def __exit__(self, *a):
-        self.out = ""
-        if self.p is not None:
+    def stop(self):
+        if self.p is not None and self.p.poll() is None:
             self.p.terminate()
             try:
-                self.out, _ = self.p.communicate(timeout=5)
+                self.p.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.p.kill()
-                self.out = ""
 
-    def summary(self):
-        rows = []
-        for line in (self.out or "").strip().splitlines():
+    def rows(self):
+        """[(unix time, fields...)] of every complete sample so far."""
+        if self.f is None:
+            return []
+        self.f.flush()
+        self.f.seek(0)
+        out = []
+        for line in self.f.read().splitlines():
             f = [v.strip() for v in line.split(",")]
-            if len(f) >= 8:
-                rows.append(f)
+            if len(f) < 9:
+                continue
+            try:
+                t = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                continue
+            out.append((t, *f[1:]))
+        return out
+
+    def __enter__(self):            # sample around a block: start, then summary_all() after exit
+        self.start()
+        self.t0 = time.time()
+        return self
+
+    def __exit__(self, *exc):
+        self.t1 = time.time()
+        self.stop()
+
+    def summary_all(self, note="timed region"):
+        return self.summary(self.t0, self.t1 + 0.1, note)
+
+    def count_between(self, t0, t1=None):
+        return sum(1 for r in self.rows() if r[0] >= t0 and (t1 is None or r[0] <= t1))
+
+    def summary(self, t0, t1, note):
+        rows = [r for r in self.rows() if t0 <= r[0] <= t1]
         if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+            why = self.error or "no nvidia-smi sample fell inside the window"
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [why], "samples": 0, "window": note}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [v for v in (num(r[1]) for r in rows) if v is not None]
+        mx = [v for v in (num(r[2]) for r in rows) if v is not None]
+        pw = [v for v in (num(r[3]) for r in rows) if v is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if r[4 + k].lower().startswith("active")})
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows),
-                "power_w_max": max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
-                if any(r[2].replace(".", "").isdigit() for r in rows) else None}
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None,
+                "window": note}
 
 
-def kernel_code_sha256(path):
-    """SHA-256 of a CUDA source with its comments and whitespace removed, so a
-    comment edit does not invalidate counters taken on the same code."""
+def code_sha256(paths):
+    """SHA-256 over source files with C/C++ and Python comments and whitespace
+    removed, so a comment edit does not invalidate counters taken on the same code."""
     import hashlib
     import re
-    text = open(path, encoding="utf-8").read()
-    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
-    text = re.sub(r"//[^\n]*", " ", text)
-    text = " ".join(text.split())
-    return hashlib.sha256(text.encode()).hexdigest()
+    h = hashlib.sha256()
+    for path in paths:
+        text = open(path, encoding="utf-8").read()
+        if path.endswith(".py"):
+            text = re.sub(r"#[^\n]*", " ", text)
+        else:
+            text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+            text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
+        h.update(b"\0")
+    return h.hexdigest()
 
 
-def recorded_traffic(H, W):
-    """DRAM bytes per k_screen launch from the committed ncu capture of the
-    4096x4096 workload, or None if the kernel's code changed since."""
-    path = os.path.join(ROOT, "profiles", "k_screen_4096_traffic.txt")
-    if (H, W) != (4096, 4096) or not os.path.exists(path):
+# what the screening kernel's DRAM traffic depends on: its source, the shared
+# launch/argument header, and the compiler flags
+SCREEN_CODE = [os.path.join(ROOT, "paper_1707_05647_gb300", "csrc", f) for f in ("features.cu", "internal.h")] + \
+    [os.path.join(ROOT, "paper_1707_05647_gb300", "_build.py")]
+
+
+def kernel_code_sha256(path=None):
+    return code_sha256([path] if path else SCREEN_CODE)
+
+
+def recorded_traffic(H, W, root=ROOT):
+    """DRAM bytes per k_screen launch from the committed one-pass ncu capture of
+    this workload (profiles/k_screen_<H>_traffic.txt), or None when there is
+    none or the kernel's code changed since it was taken."""
+    path = os.path.join(root, "profiles", f"k_screen_{H}_traffic.txt")
+    if H != W or not os.path.exists(path):
         return None
     rec = {}
     for line in open(path):
         if ":" in line and not line.startswith(("#", " ", "`")):
             k, v = line.split(":", 1)
             rec[k.strip()] = v.strip()
-    src = os.path.join(ROOT, "paper_1707_05647_gb300", "csrc", "features.cu")
-    if rec.get("kernel_code_sha256") != kernel_code_sha256(src):
+    if rec.get("kernel_code_sha256") != kernel_code_sha256():
         return None
     return int(rec["dram_bytes_per_launch"])
 
@@ -147,6 +225,71 @@ def measured_peak_gbs():
             return float(json.load(f)["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def workload(cfg, seed_offset=0, size=None):
+    import synth
+    wl = synth.CONFIGS[cfg](synth.BASE_SEED + cfg - 1 + seed_offset)
+    if size and size < wl.image.shape[0]:     # smaller case of the same recipe (profiling captures)
+        wl.image = np.ascontiguousarray(wl.image[:size, :size])
+    return wl
+
+
+def feature_str(f):
+    return "+".join(n for b, n in FEATURE_NAMES if f & b)
+
+
+def config_dict(wl, cfg):
+    H, W = wl.image.shape
+    S = len(wl.radii)
+    sc = f"{S} scale{'s' if S > 1 else ''}"
+    if S > 1:
+        sc += f" {wl.scales[0]:.2f}-{wl.scales[-1]:.2f}"
+    extra = ""
+    if wl.distractors:
+        gains = sorted({round(abs(d[2] - 1) * 100) for d in wl.distractors})
+        extra = f" + {len(wl.distractors)} distractor copies (gain 1 +- {'/'.join(map(str, gains))}%)"
+    planted = "template cut from the image, rotated" if cfg == 1 else "planted template, rotated and scaled"
+    tb = table_bytes(H, W, wl.sum_bits, wl.sq_bits)
+    return {"workload": f"config {cfg}: single image {H}x{W} u8, r={wl.r} {planted}{extra}, {sc} "
+                        f"(R {wl.radii[0]}..{wl.radii[-1]}), {feature_str(wl.features)}, "
+                        f"u{wl.sum_bits} sum / u{wl.sq_bits} sum^2 tables",
+            "config": cfg, "image": f"{H}x{W}", "r": wl.r, "radii": wl.radii, "t_min": wl.t_min,
+            "features": feature_str(wl.features), "tables": f"u{wl.sum_bits} sum / u{wl.sq_bits} sum^2",
+            "distractors": len(wl.distractors),
+            "l2": f"flushed between timed steps (256 MiB write); tables {tb / 1e6:.0f} MB > L2",
+            "candidates_per_step": candidates(H, W, wl.radii)}
+
+
+def survival(mask, wl):
+    """Planted and distractor survival from a (S, H, Ww) uint32 mask: the copy at
+    (y, x) with true scale s survives when its candidate bit is set at a scale
+    whose radius R satisfies t_min - 1 <= R / s <= r + 1 (a covering scale)."""
+    S, H, _ = mask.shape
+    W = wl.image.shape[1]
+
+    def bits(y, x):
+        return [s for s in range(S) if (int(mask[s, y, x >> 5]) >> (x & 31)) & 1]
+
+    def covering(scale):
+        return [s for s, R in enumerate(wl.radii) if wl.t_min - 1 <= R / scale <= wl.r + 1]
+
+    out = {}
+    y, x = wl.planted
+    if 0 <= y < H and 0 <= x < W:
+        hit, cov = bits(y, x), covering(wl.s_true)
+        out["planted"] = {"survives": bool(set(hit) & set(cov)), "at": [y, x], "s_true": round(wl.s_true, 4),
+                          "scales_set": hit, "covering_scales": cov}
+    if wl.distractors:
+        d_any = d_cov = 0
+        for (dy, dx, _g, ds) in wl.distractors:
+            if 0 <= dy < H and 0 <= dx < W:
+                hit = bits(dy, dx)
+                d_any += bool(hit)
+                d_cov += bool(set(hit) & set(covering(ds)))
+        out["distractors"] = {"total": len(wl.distractors), "survive_at_covering_scale": d_cov,
+                              "survive_at_any_scale": d_any}
+    return out
 
 
 def oracle_baseline(wl, max_rows=None, threads=0, split=None, min_seconds=0.0):
@@ -168,59 +311,134 @@ def oracle_baseline(wl, max_rows=None, threads=0, split=None, min_seconds=0.0):
         t_all += time.perf_counter() - t0
         t_tab += t1 - t0
         reps += 1
+        del tb
     if split is not None:
         split["tables_s"] = t_tab / reps
         split["screen_s"] = (t_all - t_tab) / reps
     n = candidates(H, W, wl.radii)
-    sample = f"{H}x{W} rows of the same image, all {len(wl.radii)} scales, tables + screen"
+    sample = f"first {H} of {wl.image.shape[0]} rows ({H}x{W}), all {len(wl.radii)} scales, tables + screen"
     if reps > 1:
         sample += f", repeated {reps} times"
     return n * reps / t_all, sample, used, t_all
 
 
-def oracle_threads(n):
-    import oracle
-    oracle.threads(n)
+# rows of the image the CPU oracle screens per sample (all columns, all scales)
+ORACLE_ROWS = {1: None, 2: 1024, 3: 1024}
+ORACLE_ROWS_1T = {1: None, 2: 512, 3: 512}
+REFERENCE_ROWS = {1: None, 2: 512, 3: 512}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import synth
-    wl = synth.config2()
-    rows = 512
+    wl = workload(args.config, size=args.size)
+    rows = REFERENCE_ROWS[args.config]
     for _ in range(args.warmup):
         oracle_baseline(wl, rows)
-    vals, secs = [], []
+    secs = []
     for _ in range(args.steps):
         v, sample, cores, dt = oracle_baseline(wl, rows)
-        vals.append(v)
         secs.append(dt)
-    value = len(secs) * candidates(rows, wl.image.shape[1], wl.radii) / sum(secs)
+    H = rows or wl.image.shape[0]
+    value = len(secs) * candidates(H, wl.image.shape[1], wl.radii) / sum(secs)
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-        "data": "synthetic", "config": config_dict(wl),
+        "data": "synthetic", "config": config_dict(wl, args.config),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
 
-def config_dict(wl):
-    H, W = wl.image.shape
-    return {"workload": f"single large image: {H}x{W} u8, planted r=48 template, 8 scales 0.5-2, "
-                        "mean+variance+contrast, u32 sum / u64 sum^2 tables",
-            "image": f"{wl.image.shape[0]}x{wl.image.shape[1]}", "radii": wl.radii, "t_min": wl.t_min,
-            "features": "mean+var+contrast", "tables": f"u{wl.sum_bits} sum / u{wl.sq_bits} sum^2",
-            "l2": "flushed between timed steps (256 MiB write); tables 403 MB > L2",
-            "candidates_per_step": candidates(*wl.image.shape, wl.radii)}
+class Single:
+    """One single-image workload on one device: inputs resident, buffers sized."""
+
+    def __init__(self, scr, torch, ctx, wl):
+        self.scr, self.torch, self.ctx, self.wl = scr, torch, ctx, wl
+        H, W = wl.image.shape
+        self.H, self.W, self.S = H, W, len(wl.radii)
+        self.ncand = candidates(H, W, wl.radii)
+        self.p = scr.Params(wl.radii, wl.features, wl.tol.mean_rel, wl.tol.std_rel, wl.tol.grad_rel,
+                            wl.tol.grad_abs)
+        self.tm = scr.template_features(ctx, wl.template, wl.r, wl.t_min, wl.features)
+        self.stream = torch.cuda.current_stream()
+        self.img = torch.from_numpy(wl.image).cuda()
+        self.mask = torch.empty(scr.mask_words(self.S, H, W), dtype=torch.int32, device="cuda")
+        self.cap = 1 << 22
+        self.lst = torch.empty(self.cap, dtype=torch.int64, device="cuda")
+        self.count = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+    def step(self, evs=None):
+        scr, wl, st = self.scr, self.wl, self.stream
+        tb = scr.build_tables(self.ctx, self.img, wl.sum_bits, wl.sq_bits, st)
+        if evs:
+            evs[0].record(st)
+        scr.screen_features(self.ctx, tb, self.tm, self.p, self.mask, st)
+        if evs:
+            evs[1].record(st)
+        scr.compact_mask(self.ctx, self.mask, self.S, self.H, self.W, self.lst, self.count, st)
+        scr.tables_release(self.ctx, tb)
+
+    def timed(self, steps, warmup, flush, clocks=None, dist=None):
+        """warmup untimed steps, then `steps` steps each bracketed by CUDA events
+        on the launching stream, the L2 flushed before each outside the events.
+        With `clocks`, the same steps keep running untimed after the region
+        until the sampler has a few samples (the timed region of a short run is
+        shorter than one sampling interval)."""
+        torch, scr, st = self.torch, self.scr, self.stream
+        for _ in range(max(warmup, 3)):
+            self.step()
+        torch.cuda.synchronize()
+        Ev = torch.cuda.Event
+        ev = [(Ev(enable_timing=True), Ev(enable_timing=True)) for _ in range(steps)]
+        kev = [(Ev(enable_timing=True), Ev(enable_timing=True)) for _ in range(steps)]
+        launches0 = scr.screen_stats(self.ctx)["kernel_launches"]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.time()
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(st)
+            self.step(kev[k])
+            ev[k][1].record(st)
+        torch.cuda.synchronize()
+        t1 = time.time()
+        if dist:
+            dist.barrier()
+        launches = scr.screen_stats(self.ctx)["kernel_launches"] - launches0
+        clk = None
+        if clocks is not None:
+            extra, t_ext = 0, t1
+            # keep the GPU under the same load until >= 4 samples fall after t0 (at most 3 s)
+            while clocks.p is not None and clocks.count_between(t0) < 4 and time.time() - t1 < 3.0:
+                for _ in range(8):
+                    flush.zero_()
+                    self.step()
+                    extra += 1
+                torch.cuda.synchronize()
+                t_ext = time.time()
+            note = f"timed region ({1e3 * (t1 - t0):.0f} ms)"
+            if extra:
+                note += f" + {extra} more identical steps run untimed right after it ({1e3 * (t_ext - t1):.0f} ms)"
+            clk = clocks.summary(t0, t_ext + 0.1, note)
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        return {"step_ms": step_ms, "k3_ms": [a.elapsed_time(b) for a, b in kev],
+                "tab_ms": [ev[k][0].elapsed_time(kev[k][0]) for k in range(steps)],
+                "total_s": sum(step_ms) / 1e3, "launches": launches, "clocks": clk,
+                "survivors": int(self.count.item())}
+
+    def mask_host(self):
+        return self.mask.cpu().numpy().view(np.uint32).reshape(self.S, self.H, (self.W + 31) // 32)
+
+    def release(self):
+        self.scr.template_release(self.ctx, self.tm)
 
 
 def run_ours(args):
     import torch
-    import synth
     import paper_1707_05647_gb300 as scr
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -231,149 +449,137 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
-    wl = synth.config2(synth.BASE_SEED + 1 + 1000 * rank)
-    if args.size != 4096:      # smaller case of the same recipe (profiling captures)
-        wl.image = np.ascontiguousarray(wl.image[:args.size, :args.size])
-    H, W = wl.image.shape
-    S = len(wl.radii)
-    ncand = candidates(H, W, wl.radii)
+    clocks = Clocks(local).start() if rank == 0 else None
+    wl = workload(args.config, 1000 * rank, args.size)
     ctx = scr.screen_init(local, 0)
-    p = scr.Params(wl.radii, wl.features, wl.tol.mean_rel, wl.tol.std_rel, wl.tol.grad_rel, wl.tol.grad_abs)
-    tm = scr.template_features(ctx, wl.template, wl.r, wl.t_min, wl.features)
-    stream = torch.cuda.current_stream()
-    img = torch.from_numpy(wl.image).cuda()
-    mask = torch.empty(scr.mask_words(S, H, W), dtype=torch.int32, device="cuda")
-    cap = 1 << 22
-    lst = torch.empty(cap, dtype=torch.int64, device="cuda")
-    count = torch.zeros(1, dtype=torch.int64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-
-    def step(evs=None):
-        tb = scr.build_tables(ctx, img, wl.sum_bits, wl.sq_bits, stream)
-        if evs:
-            evs[0].record(stream)
-        scr.screen_features(ctx, tb, tm, p, mask, stream)
-        if evs:
-            evs[1].record(stream)
-        scr.compact_mask(ctx, mask, S, H, W, lst, count, stream)
-        scr.tables_release(ctx, tb)
-
-    for _ in range(max(args.warmup, 3)):
-        step()
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    launches0 = scr.screen_stats(ctx)["kernel_launches"]
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with Clocks(local) as clk:
-        for k in range(args.steps):
-            flush.zero_()
-            ev[k][0].record(stream)
-            step(kev[k])
-            ev[k][1].record(stream)
-        torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    launches = scr.screen_stats(ctx)["kernel_launches"] - launches0
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    k3_ms = [a.elapsed_time(b) for a, b in kev]
-    tab_ms = [ev[k][0].elapsed_time(kev[k][0]) for k in range(args.steps)]
-    total_s = sum(step_ms) / 1e3
+    run = Single(scr, torch, ctx, wl)
+    m = run.timed(args.steps, args.warmup, flush, clocks, dist)
+    total_s = m["total_s"]
     if dist:
         t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_s = float(t.item())
-    value = world * ncand * args.steps / total_s
-    n_surv = int(count.item())
-
-    # end to end through the C ABI with host buffers
+    m["value"] = world * run.ncand * args.steps / total_s
+    m["total_s"] = total_s
+    surv = survival(run.mask_host(), wl)
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(scr, torch, ctx, wl, tm, p, cap, ncand, args)
+        e2e = run_e2e(scr, torch, ctx, run, args)
+    run.release()
+    second = None
+    if args.config == 3 and not args.no_secondary and not args.size:
+        wl2 = workload(2, 1000 * rank)
+        run2 = Single(scr, torch, ctx, wl2)
+        steps2 = max(args.steps, 20)
+        m2 = run2.timed(steps2, args.warmup, flush)
+        second = secondary_dict(wl2, run2, m2, steps2, surv_of=survival(run2.mask_host(), wl2))
+        run2.release()
+    if clocks is not None:
+        clocks.stop()
     if rank == 0:
-        emit(args, wl, world, total_s, value, k3_ms, step_ms, launches, clk, n_surv, e2e, tab_ms)
-    scr.template_release(ctx, tm)
+        emit(args, wl, world, m, e2e, surv, second)
     scr.screen_shutdown(ctx)
     if dist:
         dist.destroy_process_group()
 
 
-def run_e2e(scr, torch, ctx, wl, tm, p, cap, ncand, args):
+def run_e2e(scr, torch, ctx, run, args):
+    wl = run.wl
     H, W = wl.image.shape
     img_host = torch.from_numpy(wl.image).pin_memory()
-    lst_host = torch.empty(cap, dtype=torch.int64).pin_memory()
+    lst_host = torch.empty(run.cap, dtype=torch.int64).pin_memory()
     for _ in range(2):
-        scr.screen_host(ctx, img_host.numpy(), wl.sum_bits, wl.sq_bits, tm, p, lst_host.numpy())
+        scr.screen_host(ctx, img_host.numpy(), wl.sum_bits, wl.sq_bits, run.tm, run.p, lst_host.numpy())
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2e_steps = max(10, min(args.steps, 100))
     for _ in range(e2e_steps):
-        n_e2e, _ = scr.screen_host(ctx, img_host.numpy(), wl.sum_bits, wl.sq_bits, tm, p, lst_host.numpy())
+        n_e2e, _ = scr.screen_host(ctx, img_host.numpy(), wl.sum_bits, wl.sq_bits, run.tm, run.p, lst_host.numpy())
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    return {"value": ncand / e2e_s, "unit": UNIT, "h2d_bytes_per_step": H * W,
-            "d2h_bytes_per_step": 8 + 8 * min(n_e2e, cap), "steps": e2e_steps}
+    return {"value": run.ncand / e2e_s, "unit": UNIT, "h2d_bytes_per_step": H * W,
+            "d2h_bytes_per_step": 8 + 8 * min(n_e2e, run.cap), "steps": e2e_steps, "ms_per_call": 1e3 * e2e_s,
+            "how": "screen_host(): pinned host image -> device, tables, screen, compaction, count + keys back "
+                   "to pinned host memory, one synchronisation per call; host wall clock"}
 
 
-def emit(args, wl, world, total_s, value, k3_ms, step_ms, launches, clk, n_surv, e2e, tab_ms):
+def rooflines(wl, k3_s, tab_s, n_surv):
     H, W = wl.image.shape
     S = len(wl.radii)
     peak, src = measured_peak_gbs()
-    k3 = statistics.mean(k3_ms) / 1e3
     alg = compulsory_bytes(H, W, S, wl.sum_bits, wl.sq_bits, n_surv)
-    achieved = alg / k3 / 1e9
-    alg1 = per_scale_bytes(H, W, S, wl.sum_bits, wl.sq_bits) / k3 / 1e9
-    traffic = recorded_traffic(H, W)
+    achieved = alg / k3_s / 1e9
+    alg1 = per_scale_bytes(H, W, S, wl.sum_bits, wl.sq_bits) / k3_s / 1e9
     ncand = candidates(H, W, wl.radii)
     per_scale_model = ("Algorithm 1 per-scale: the 4 full-width tables read once per scale + mask "
                        f"({per_scale_bytes(H, W, S, wl.sum_bits, wl.sq_bits) / ncand:.1f} B/candidate)")
     compulsory = {"achieved": achieved, "frac": achieved / peak,
                   "model": f"compulsory (tables once across scales + mask + list): {alg} B/launch, "
                            f"{alg / ncand:.2f} B/candidate"}
-    binding = ("on-chip: L1/L2 load latency and the L1 data pipe; DRAM traffic is the low "
-               "planes of L1 and T1 once (ncu: L1 LSU wavefronts 66%, L1/TEX 72%, ALU pipe 52%, "
-               "issue 62%, L2 48% of peak on the 3072^2 case)")
+    traffic = recorded_traffic(H, W)
+    binding = ("on-chip: the L1 data pipe and instruction issue; the tables are read from DRAM about "
+               "once (low 32-bit planes) and re-read across scales from L2")
+    common = {"bound": "hbm", "peak": peak, "unit": "GB/s", "traffic": traffic, "peak_source": src,
+              "kernel": "k_screen", "kernel_ms": 1e3 * k3_s, "binding": binding}
     if alg1 <= peak:
-        # Algorithm 1's per-scale traffic, served partly from L2: the fraction of the HBM roof
-        # that model implies (kept only while it stays below 1)
-        roofline = {"bound": "hbm", "achieved": alg1, "peak": peak, "unit": "GB/s", "frac": alg1 / peak,
-                    "traffic": traffic, "peak_source": src, "kernel": "k_screen", "kernel_ms": 1e3 * k3,
-                    "model": per_scale_model, "compulsory": compulsory, "binding": binding}
+        roofline = dict(common, achieved=alg1, frac=alg1 / peak, model=per_scale_model, compulsory=compulsory)
     else:
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": traffic, "peak_source": src, "kernel": "k_screen", "kernel_ms": 1e3 * k3,
-                    "model": compulsory["model"], "per_scale_above_peak": {"achieved": alg1, "model": per_scale_model},
-                    "binding": binding}
-    # table build: 1 B/px read + the four tables written, over the measured build time
-    tb_s = statistics.mean(tab_ms) / 1e3
-    tb_bytes = H * W + ((H + 1) * (W + 1) + (H + 1) * (W + 2)) * (wl.sum_bits + wl.sq_bits) // 8
-    tables_roofline = {"bound": "hbm", "achieved": tb_bytes / tb_s / 1e9, "peak": peak, "unit": "GB/s",
-                       "frac": tb_bytes / tb_s / 1e9 / peak, "build_ms": 1e3 * tb_s,
+        roofline = dict(common, achieved=achieved, frac=achieved / peak, model=compulsory["model"],
+                        per_scale_above_peak={"achieved": alg1, "model": per_scale_model})
+    tb_bytes = H * W + table_bytes(H, W, wl.sum_bits, wl.sq_bits)
+    tables_roofline = {"bound": "hbm", "achieved": tb_bytes / tab_s / 1e9, "peak": peak, "unit": "GB/s",
+                       "frac": tb_bytes / tab_s / 1e9 / peak, "build_ms": 1e3 * tab_s,
                        "model": f"1 B/px image read + tables written: {tb_bytes} B per build",
                        "kernels": "k_tab_reduce, k_tab_carry, k_tab_prefix, k_tab_write"}
+    return roofline, tables_roofline
+
+
+def secondary_dict(wl, run, m, steps, surv_of):
+    k3 = statistics.mean(m["k3_ms"]) / 1e3
+    tab = statistics.mean(m["tab_ms"]) / 1e3
+    roof, troof = rooflines(wl, k3, tab, m["survivors"])
+    return {"workload": config_dict(wl, 2)["workload"], "steps": steps,
+            "value": run.ncand * steps / m["total_s"], "unit": UNIT, "ms_per_step": 1e3 * m["total_s"] / steps,
+            "k_screen_ms": 1e3 * k3, "roofline_frac": roof["frac"], "roofline_model": roof["model"],
+            "tables_ms": 1e3 * tab, "tables_frac": troof["frac"], "survivors": m["survivors"],
+            **surv_of}
+
+
+def dtype_of(wl):
+    """Arithmetic type of the path: the table words (window sums are formed in
+    32 bits, products in 64)."""
+    return "u32" if wl.sum_bits == wl.sq_bits == 32 else ("u64" if wl.sum_bits == 64 else "u32+u64")
+
+
+def emit(args, wl, world, m, e2e, surv, second=None):
+    k3 = statistics.mean(m["k3_ms"]) / 1e3
+    tab = statistics.mean(m["tab_ms"]) / 1e3
+    roofline, tables_roofline = rooflines(wl, k3, tab, m["survivors"])
     cpu = None
     if not args.no_cpu_baseline:
         split, split1 = {}, {}
-        v, sample, cores, dt = oracle_baseline(wl, split=split, min_seconds=10.0)
-        v1, sample1, _, dt1 = oracle_baseline(wl, 1024, threads=1, split=split1, min_seconds=10.0)
-        oracle_threads(cores)
+        v, sample, cores, dt = oracle_baseline(wl, ORACLE_ROWS[args.config], split=split, min_seconds=10.0)
+        v1, sample1, _, dt1 = oracle_baseline(wl, ORACLE_ROWS_1T[args.config], threads=1, split=split1,
+                                              min_seconds=10.0)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
                "seconds": round(dt, 2), "tables_s": round(split["tables_s"], 3),
                "screen_s": round(split["screen_s"], 3),
                "single_thread": {"value": v1, "sample": sample1, "seconds": round(dt1, 2),
                                  "tables_s": round(split1["tables_s"], 3), "screen_s": round(split1["screen_s"], 3)}}
+    steps = len(m["step_ms"])
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u32+u64", "data": "synthetic",
-        "config": config_dict(wl),
-        "roofline": roofline,
-        "tables_roofline": tables_roofline,
-        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-        "clocks": clk.summary(), "survivors": n_surv,
-        "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
+        "metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * m["total_s"] / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype_of(wl),
+        "data": "synthetic", "config": config_dict(wl, args.config),
+        "roofline": roofline, "tables_roofline": tables_roofline,
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": m["launches"],
+        "clocks": m["clocks"] or {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled on this rank"]},
+        "survivors": m["survivors"], "survival": surv,
+        "step_ms": {"min": min(m["step_ms"]), "median": statistics.median(m["step_ms"]), "max": max(m["step_ms"])},
     }
+    if second is not None:
+        line["config2"] = second
     print(json.dumps(line), flush=True)
 
 
@@ -466,7 +672,7 @@ def run_batched(args):
         "speedup_vs_per_request": req_s / batch_s, "counts_identical": same,
         "candidates": info["candidates"], "survivors": n_keys, "keys_complete": int(nk[1].item()) <= keys.numel(),
         "plan": info, "plan_seconds": plan_s, "plan_seconds_tuned_cached": plan_cached_s,
-        "clocks": clk.summary(), "data": "synthetic"}), flush=True)
+        "clocks": clk.summary_all(), "data": "synthetic"}), flush=True)
     scr.screen_batch_release(ctx, b)
     scr.screen_shutdown(ctx)
 
@@ -536,7 +742,7 @@ def run_joint(args):
     scr.compact_mask(ctx, mask, S, H, W, lst, cnt, st)
     torch.cuda.synchronize()
     n_int = int(cnt.item())
-    cand = 127458510
+    cand = candidates(H, W, wl.radii)
     print(json.dumps({
         "metric": "candidate (position x scale) evaluations/s", "workload":
             "joint membership: 4096x4096, r 48, 8 scales, 3 nested central areas, q = (4, 2, 4) grey levels",
@@ -580,7 +786,7 @@ def run_serve(args):
         H, W = img_shape
         tot = 0
         for R in radii:
-            n = scr_square_half(R)
+            n = square_half(R)
             m = max(n, R)
             rows = (H - 1 - m) - (m - 1) + 1
             cols = min(W - 1 - n, W - R) - (m - 1) + 1
@@ -735,12 +941,6 @@ def run_serve(args):
     scr.screen_shutdown(ctx)
 
 
-def scr_square_half(R: int) -> int:
-    """n with (2n-1)^2 < 2R^2 < (2n+1)^2, for counting valid positions in reports."""
-    m = math.isqrt(2 * R * R)
-    return (m + 1) // 2
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -748,9 +948,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--size", type=int, default=4096,
-                    help="crop the 4096x4096 image to size x size (smaller ncu captures)")
+    ap.add_argument("--config", type=int, default=3, choices=[1, 2, 3],
+                    help="single-image workload: 3 = 8192x8192, 16 scales (default); 2 = 4096x4096, 8 scales; "
+                         "1 = 512x512, 1 scale")
+    ap.add_argument("--size", type=int, default=None,
+                    help="crop the image to size x size (smaller ncu captures)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the 4096x4096 run after config 3")
     ap.add_argument("--workload", default="single", choices=["single", "batched", "serve", "joint"])
     ap.add_argument("--duration", type=float, default=2.0, help="seconds of arrivals (serve workload)")
     ap.add_argument("--rates", default="2000,8000,16000",

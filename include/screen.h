@@ -247,20 +247,26 @@ int compact_mask(scr_ctx *ctx, const uint32_t *mask_dev, int32_t n_scales, int32
                  uint64_t *list_dev, uint64_t list_cap, uint64_t *count_dev, scr_stream stream);
 
 /* Allocation-free variant of compact_mask, for callers that cannot allocate
- * device memory where they compact -- code inside CUDA stream capture,
- * real-time loops that must not enter an allocator, or processes whose device
- * memory belongs to another framework's allocator.  (The paper has no
- * counterpart; this is a deployment convenience.)
+ * device memory where they compact: real-time loops that must never enter an
+ * allocator (an allocation can stall on the driver for an unbounded time),
+ * processes whose device memory all belongs to another framework's allocator,
+ * and embedded runtimes that fix every buffer when they start.  The paper has
+ * no counterpart; this is a deployment convenience.
  *   Inputs, outputs and results are exactly those of compact_mask, on the
  *   CUDA device that is current for the calling thread; no context is used.
  *   Scratch: a fixed array of about 0.75 MiB inside the library, held by every
  *   GPU that loads the library until the process exits.  Masks of more than
  *   268435456 words (65536 chunks of 4096 words) are rejected with SCR_EINVAL.
  *   The call allocates nothing: no cudaMalloc, cudaFree or allocating library
- *   routine.  The first call on each device looks up the array's device address
- *   (a one-time set-up); make that first call before any stream capture.
- *   All calls share the one array: calls whose work overlaps on the GPU (for
- *   example on two streams) race and must be ordered by the caller.
+ *   routine.  The first call on each device does a one-time set-up (it looks
+ *   up the array's device address, which also creates the device's context if
+ *   there is none yet); make that first call before any stream capture.  The
+ *   set-up runs again on the first call after the device's context has been
+ *   re-created (cudaDeviceReset), since the array may then have moved.
+ *   All calls share the one array and it keeps the last call's contents (each
+ *   call rewrites what it reads): calls whose work overlaps on the GPU (for
+ *   example on two streams, or on one stream from two threads without
+ *   ordering) race and must be ordered by the caller.
  *   Errors return SCR_E* codes; their message is compact_mask_noalloc_error(). */
 int compact_mask_noalloc(const uint32_t *mask_dev, int32_t n_scales, int32_t H, int32_t W,
                          uint64_t *list_dev, uint64_t list_cap, uint64_t *count_dev, scr_stream stream);

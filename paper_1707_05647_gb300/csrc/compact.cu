@@ -365,17 +365,21 @@ cudaError_t launch_compact(const uint32_t *mask, uint64_t total_words, int H, in
 // Allocation-free compaction.
 //
 // Some callers cannot allocate device memory at the point where they compact
-// a mask: code running while a stream is being captured into a CUDA graph
-// (where cudaMalloc is not allowed), real-time loops that must not enter the
-// allocator, and hosts whose device memory is owned by another framework's
-// allocator with no hook for a foreign library.  compact_mask_noalloc serves
-// them: its scratch (per-chunk bit counts and their prefix offsets) lives in
-// the fixed device array below instead of coming from an allocation.
+// a mask: real-time loops that must never enter an allocator (an allocation
+// can block on the driver for an unbounded time), hosts whose device memory is
+// all owned by another framework's allocator with no hook for a foreign
+// library, and embedded runtimes that fix every buffer when they start.
+// compact_mask_noalloc serves them: its scratch (per-chunk bit counts and
+// their prefix offsets) lives in the fixed device array below instead of
+// coming from an allocation.
 //
 // The array is a file-scope __device__ variable, so every GPU that loads this
 // library holds it (kStaticCompactBytes) until the process exits.  In host
 // code its name is only a host-side stand-in; the device address is looked up
-// once per device with cudaGetSymbolAddress, with that device current.
+// with cudaGetSymbolAddress, with the device current, once per device -- and
+// once more if that device's context has been re-created since (after
+// cudaDeviceReset the module is loaded again and the array may move), which
+// the entry point notices by the context's unique id.
 // ---------------------------------------------------------------------------
 namespace scr {
 namespace {
@@ -388,7 +392,37 @@ static __device__ __align__(256) unsigned char g_compact_scratch[kStaticCompactB
 
 std::mutex g_static_mu;
 void *g_static_ptr[kMaxDevices] = {nullptr};
+unsigned long long g_static_ctx[kMaxDevices] = {0};   // unique id of the context the address belongs to
 thread_local char g_noalloc_err[256];
+
+// Unique id of the calling thread's current context (cuCtxGetCurrent +
+// cuCtxGetId, reached through the runtime so the library needs no link to the
+// driver library).  0 when it cannot be read.
+unsigned long long current_context_id() {
+    using GetCurrent = int (*)(void **);
+    using GetId = int (*)(void *, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {   // called with g_static_mu held
+        looked_up = true;
+        void *f = nullptr, *g = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &g, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q2 == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<GetCurrent>(f);
+            get_id = reinterpret_cast<GetId>(g);
+        }
+        cudaGetLastError();
+    }
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0)
+        return 0;
+    return id;
+}
 
 int noalloc_fail(int code, const char *msg) {
     snprintf(g_noalloc_err, sizeof g_noalloc_err, "%s", msg);
@@ -422,8 +456,10 @@ extern "C" int compact_mask_noalloc(const uint32_t *mask_dev, int32_t n_scales, 
     void *scratch = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_static_mu);
-        if (!g_static_ptr[dev]) {
-            // one-time set-up for this device (the current device)
+        const unsigned long long ctx = current_context_id();   // 0: no context yet, or unreadable
+        if (!g_static_ptr[dev] || ctx == 0 || ctx != g_static_ctx[dev]) {
+            // set-up for this device (the current device), once per context;
+            // cudaGetSymbolAddress also creates the context if there is none yet
             void *p = nullptr;
             const cudaError_t e = cudaGetSymbolAddress(&p, g_compact_scratch);
             if (e != cudaSuccess || !p) {
@@ -431,6 +467,7 @@ extern "C" int compact_mask_noalloc(const uint32_t *mask_dev, int32_t n_scales, 
                 return noalloc_fail(SCR_ECUDA, "cudaGetSymbolAddress of the fixed compaction scratch failed");
             }
             g_static_ptr[dev] = p;
+            g_static_ctx[dev] = current_context_id();
         }
         scratch = g_static_ptr[dev];
     }

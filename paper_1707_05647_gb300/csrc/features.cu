@@ -134,19 +134,29 @@ k_screen(const __grid_constant__ ScreenArgs a) {
             }
             if (fv && __any_sync(0xffffffffu, keep != 0)) {
                 // the square and diamond sums of I^2 are each below 2^32 but
-                // their sum may not be: add them in 64 bits
+                // their sum may not be: add them in 64 bits.  The reads of
+                // half the words (those still alive) are issued together
+                // before any of them is used, so a warp waits for the L2 twice
+                // per scale, not once per word: on workloads whose mean test
+                // passes most candidates this path runs for nearly every word.
                 const Corners cq(L2, T2, p.oL, p.oT);
 #pragma unroll
-                for (int j = 0; j < WPW; ++j) {
-                    if (!((keep >> j) & 1u))
-                        continue;
-                    const int d = 32 * j;
-                    const uint32_t qs = ld(cq.p[0] + d) - ld(cq.p[1] + d) - ld(cq.p[2] + d) + ld(cq.p[3] + d);
-                    const uint32_t qd = ld(cq.p[4] + d) - ld(cq.p[5] + d) - ld(cq.p[6] + d) + ld(cq.p[7] + d);
-                    const uint64_t Q = (uint64_t)qs + qd;
-                    const uint64_t V = (uint64_t)p.A * Q - (uint64_t)S[j] * S[j];   // A^2 * variance
-                    if ((V - (uint64_t)p.V_lo) > p.V_rng)
-                        keep &= ~(1u << j);
+                for (int h = 0; h < WPW; h += WPW / 2) {
+                    uint32_t q[WPW / 2][8];
+#pragma unroll
+                    for (int j = 0; j < WPW / 2; ++j)
+#pragma unroll
+                        for (int k = 0; k < 8; ++k)
+                            q[j][k] = ((keep >> (h + j)) & 1u) ? ld(cq.p[k] + 32 * (h + j)) : 0u;
+#pragma unroll
+                    for (int j = 0; j < WPW / 2; ++j) {
+                        const uint32_t qs = q[j][0] - q[j][1] - q[j][2] + q[j][3];
+                        const uint32_t qd = q[j][4] - q[j][5] - q[j][6] + q[j][7];
+                        const uint64_t Q = (uint64_t)qs + qd;
+                        const uint64_t V = (uint64_t)p.A * Q - (uint64_t)S[h + j] * S[h + j];   // A^2 * variance
+                        if ((V - (uint64_t)p.V_lo) > p.V_rng)
+                            keep &= ~(1u << (h + j));
+                    }
                 }
             }
             if (fg && __any_sync(0xffffffffu, keep != 0)) {

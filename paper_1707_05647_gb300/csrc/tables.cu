@@ -22,15 +22,19 @@
 //   k_tab_carry   per column / diagonal index: exclusive prefix over bands.
 //   k_tab_prefix  per band: prefix along the row of those sums -> the carry
 //                 rows L(r0, .), D1(r0-1, .), D2(r0-1, .) and per-tile row carries.
-//   k_tab_write   per tile: walk the band's rows; each thread owns 4 adjacent
-//                 columns, keeps L, D1, D2 for them in registers; per row it
-//                 scans the pixels into P (warp shuffles + one block step), adds
-//                 P to L, moves D1 one column left and D2 one column right
-//                 (register moves plus one neighbour shuffle), and stores L and
-//                 T = D1 - D2 with 16-byte stores.
-// A tile carries kHalo extra columns on each side so its D1 (which flows in
-// from the right) and D2 (from the left) stay exact over its core columns for
-// the kBand rows of a band.
+//   k_tab_write   one warp per (band, 192-column warp tile): lane l owns 8
+//                 adjacent columns of the tile's 256 slots (32 halo slots on
+//                 each side) and keeps L, D1, D2 for them in registers.  Per row
+//                 it forms P with one warp scan of the lanes' pixel sums plus
+//                 the tile's row carry, adds P to L, moves D1 one column left
+//                 and D2 one column right (register moves plus one neighbour
+//                 shuffle), puts the core columns' L and T = D1 - D2 into a
+//                 double-buffered shared-memory row, and one lane writes each
+//                 plane's 768-byte row segment with a bulk copy (cp.async.bulk).
+//                 No block barrier and no inter-warp exchange.
+// A warp tile carries kHalo extra columns on each side so its D1 (which flows
+// in from the right) and D2 (from the left) stay exact over its core columns
+// for the kBand rows of a band.
 #include <cuda_runtime.h>
 #include <stdint.h>
 

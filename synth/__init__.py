@@ -156,7 +156,7 @@ class Workload:
     s_true: float
     theta: float
     scales: list[float] = field(default_factory=list)
-    distractors: list[tuple[int, int, float]] = field(default_factory=list)
+    distractors: list[tuple[int, int, float, float]] = field(default_factory=list)   # (y, x, gain, scale)
 
 
 def _pick_site(rng, H, W, side, margin, floor_std, img, tries=400):
@@ -225,9 +225,10 @@ def _planted_workload(name, seed, H, r, s_min, s_max, n_scales, sum_bits, sq_bit
         dy = int(rng.integers(margin, H - margin))
         dx = int(rng.integers(margin, W - margin))
         g = 1.0 + (distractor_gain if rng.integers(0, 2) else -distractor_gain)
-        paste(fld, tmpl, dy + 0.5, dx + 0.5, float(rng.uniform(0, 2 * math.pi)),
-              float(math.exp(rng.uniform(math.log(0.5), math.log(2.0)))), gain=g)
-        distractors.append((dy, dx, g))
+        d_theta = float(rng.uniform(0, 2 * math.pi))
+        d_scale = float(math.exp(rng.uniform(math.log(0.5), math.log(2.0))))
+        paste(fld, tmpl, dy + 0.5, dx + 0.5, d_theta, d_scale, gain=g)
+        distractors.append((dy, dx, g, d_scale))
     # the true copy is pasted last so no distractor overwrites it
     paste(fld, tmpl, ys + 0.5, xs + 0.5, theta, s_true)
     img = quantize_with_noise(fld, rng)

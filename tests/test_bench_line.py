@@ -1,4 +1,5 @@
-"""The bench's JSON line: required keys and the roofline arithmetic (host only)."""
+"""The bench's JSON line: required keys, the roofline arithmetic, the survival
+report and the traffic record's code key (host only)."""
 import argparse
 import io
 import json
@@ -14,19 +15,25 @@ import numpy as np  # noqa: E402
 
 import bench  # noqa: E402
 
-
-class _Clk:
-    def summary(self):
-        return {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []}
+RADII2 = [24, 29, 36, 43, 53, 65, 79, 96]
 
 
-def _line(H, W, k3_ms, tab_ms):
-    wl = types.SimpleNamespace(image=np.zeros((H, W), np.uint8), radii=[24, 29, 36, 43, 53, 65, 79, 96],
-                               t_min=40, sum_bits=32, sq_bits=64)
-    args = argparse.Namespace(steps=2, warmup=3, no_cpu_baseline=True)
+def _wl(H, W, radii=RADII2, sum_bits=32, sq_bits=64):
+    return types.SimpleNamespace(image=np.zeros((H, W), np.uint8), radii=radii, t_min=40, r=48,
+                                 scales=[0.5 * 4 ** (i / 7) for i in range(8)], features=7,
+                                 sum_bits=sum_bits, sq_bits=sq_bits, distractors=[], planted=(100, 100),
+                                 s_true=1.0)
+
+
+def _line(H, W, k3_ms, tab_ms, config=2):
+    wl = _wl(H, W)
+    args = argparse.Namespace(steps=2, warmup=3, no_cpu_baseline=True, config=config)
+    m = {"k3_ms": [k3_ms] * 2, "tab_ms": [tab_ms] * 2, "step_ms": [0.4] * 2, "total_s": 0.8e-3,
+         "launches": 16, "clocks": {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []}, "survivors": 10,
+         "value": 1.0}
     buf = io.StringIO()
     with redirect_stdout(buf):
-        bench.emit(args, wl, 1, 2 * 0.4e-3, 1.0, [k3_ms] * 2, [0.4] * 2, 16, _Clk(), 10, None, [tab_ms] * 2)
+        bench.emit(args, wl, 1, m, None, {})
     return json.loads(buf.getvalue().strip().splitlines()[-1])
 
 
@@ -36,6 +43,7 @@ def test_line_keys_and_per_scale_roofline():
               "scaling", "vs_baseline", "dtype", "data", "config", "roofline", "tables_roofline",
               "cpu_baseline", "e2e", "gpu_launches", "clocks"):
         assert k in d, k
+    assert d["config"]["workload"].startswith("config 2: single image 4096x4096")
     r = d["roofline"]
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
     # per-scale model: 8 passes over the four tables (u32 + u64 planes) plus the mask
@@ -58,13 +66,46 @@ def test_per_scale_fraction_never_quoted_above_one():
     assert r["per_scale_above_peak"]["achieved"] > r["peak"]
 
 
+def test_candidate_counts_of_the_configurations():
+    import synth
+    wl3 = types.SimpleNamespace(radii=synth.radii_for(64, synth.geometric_scales(0.35, 2.8, 16)))
+    assert wl3.radii[0] == 22 and wl3.radii[-1] == 179
+    assert bench.candidates(8192, 8192, wl3.radii) == 1034216188
+    assert bench.candidates(4096, 4096, RADII2) == 127458510
+    # config 3's compulsory bytes: u64/u64 tables once + 16 mask planes
+    b = bench.compulsory_bytes(8192, 8192, 16, 64, 64, 0)
+    assert abs(b / 1034216188 - 2.2) < 0.05
+
+
+def test_survival_report_reads_covering_scales():
+    wl = _wl(64, 64)
+    wl.radii, wl.t_min, wl.r = [10, 14, 20], 10, 14
+    wl.planted, wl.s_true = (30, 33), 1.0                  # covering scales: R/1 in [9, 15] -> 0, 1
+    wl.distractors = [(20, 5, 1.03, 1.4), (40, 40, 0.97, 1.0)]
+    mask = np.zeros((3, 64, 2), np.uint32)
+    mask[2, 30, 1] |= np.uint32(1 << 1)                    # planted set only at a non-covering scale
+    mask[2, 20, 0] |= np.uint32(1 << 5)                    # distractor 0 at scale 2: R/1.4 = 14.3, covering
+    s = bench.survival(mask, wl)
+    assert s["planted"]["survives"] is False and s["planted"]["scales_set"] == [2]
+    assert s["distractors"] == {"total": 2, "survive_at_covering_scale": 1, "survive_at_any_scale": 1}
+    mask[1, 30, 1] |= np.uint32(1 << 1)
+    assert bench.survival(mask, wl)["planted"]["survives"] is True
+
+
 def test_traffic_record_follows_kernel_code_not_comments(tmp_path):
     base = "// a comment\n__global__ void k(int *p) { /* note */ p[0] = 1; }\n"
     a, b, c = tmp_path / "a.cu", tmp_path / "b.cu", tmp_path / "c.cu"
     a.write_text(base)
     b.write_text(base.replace("a comment", "another comment").replace("note", "other"))
     c.write_text(base.replace("p[0] = 1", "p[0] = 2"))
-    assert bench.kernel_code_sha256(str(a)) == bench.kernel_code_sha256(str(b))
-    assert bench.kernel_code_sha256(str(a)) != bench.kernel_code_sha256(str(c))
-    # the committed record matches the committed kernel
-    assert bench.recorded_traffic(4096, 4096) is not None
+    assert bench.code_sha256([str(a)]) == bench.code_sha256([str(b)])
+    assert bench.code_sha256([str(a)]) != bench.code_sha256([str(c)])
+    # a record is used only while its key matches the kernel's code and flags
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    rec = prof / "k_screen_8192_traffic.txt"
+    rec.write_text(f"dram_bytes_per_launch: 123\nkernel_code_sha256: {bench.kernel_code_sha256()}\n")
+    assert bench.recorded_traffic(8192, 8192, root=str(tmp_path)) == 123
+    rec.write_text("dram_bytes_per_launch: 123\nkernel_code_sha256: 00\n")
+    assert bench.recorded_traffic(8192, 8192, root=str(tmp_path)) is None
+    assert bench.recorded_traffic(8192, 8192, root=str(tmp_path / "none")) is None
