@@ -24,6 +24,7 @@ from __future__ import annotations
 
 import argparse
 import datetime
+import gc
 import json
 import math
 import os
@@ -217,6 +218,28 @@ def recorded_traffic(H, W, root=ROOT):
     if rec.get("kernel_code_sha256") != kernel_code_sha256():
         return None
     return int(rec["dram_bytes_per_launch"])
+
+
+def recorded_onchip(H, W, root=ROOT):
+    """On-chip utilisation of k_screen from the committed ncu full-set capture
+    (profiles/k_screen_<H>_onchip.txt: the same workload's recipe, cropped so the
+    capture ends in seconds), or None when the kernel's code changed since."""
+    path = os.path.join(root, "profiles", f"k_screen_{H}_onchip.txt")
+    if H != W or not os.path.exists(path):
+        return None
+    rec = {}
+    for line in open(path):
+        if ":" in line and not line.startswith(("#", " ", "`")):
+            k, v = line.split(":", 1)
+            rec[k.strip()] = v.strip()
+    if rec.get("kernel_code_sha256") != kernel_code_sha256():
+        return None
+    out = {k: float(rec[k]) for k in ("l1_lsu_data_pipe_pct", "l1tex_pct", "issue_active_pct", "l2_pct",
+                                      "dram_pct", "l1_hit_pct", "warp_instructions_per_32_candidates")
+           if k in rec}
+    out["bound"] = "L1 data pipe and instruction issue (no HBM bound)"
+    out["source"] = f"profiles/k_screen_{H}_onchip.txt ({rec.get('case', 'ncu --set full')})"
+    return out
 
 
 def measured_peak_gbs():
@@ -477,11 +500,67 @@ def run_ours(args):
         run2.release()
     if clocks is not None:
         clocks.stop()
+    legs = {}
+    if args.config == 3 and not args.no_secondary and not args.size and world == 1:
+        legs = secondary_legs(args)
     if rank == 0:
-        emit(args, wl, world, m, e2e, surv, second)
+        emit(args, wl, world, m, e2e, surv, second, legs)
     scr.screen_shutdown(ctx)
     if dist:
         dist.destroy_process_group()
+
+
+SERVE_SEEDS = (1004, 1005, 1006)
+
+
+def secondary_legs(args):
+    """Short runs of the batched (configuration 4) and serving (configuration 5)
+    workloads for the default line, each with its oracle checks; a failure is
+    reported in the line instead of ending the run."""
+    out = {}
+    bargs = argparse.Namespace(images=64, templates=256, steps=3, warmup=1)
+    sargs = argparse.Namespace(duration=2.0)
+    legs = [("batched_config4", lambda: batched_leg(bargs))]
+    for k, sd in enumerate(SERVE_SEEDS):
+        legs.append((f"serve_config5_seed{sd}", lambda sd=sd, k=k: serve_leg(sargs, [2000.0], check=(k == 0), seed=sd)))
+    for name, fn in legs:
+        try:
+            r = fn()
+        except Exception as e:          # reported, not raised: the headline above stands on its own
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+            continue
+        if name == "batched_config4":
+            oc = r["oracle_check"] or {}
+            out[name] = {"workload": r["workload"], "value": r["value"], "unit": r["unit"],
+                         "ms_per_run": r["ms_per_run"], "per_request_ms": r["per_request"]["ms"],
+                         "speedup_vs_per_request": r["speedup_vs_per_request"],
+                         "counts_identical": r["counts_identical"], "survivors": r["survivors"],
+                         "oracle_check": {k: oc.get(k) for k in ("pairs_compared_with_oracle", "pairs_with_mismatch",
+                                                                 "keys_compared", "plants")},
+                         "clocks": r["clocks"]}
+        else:
+            oc = r["oracle_check"] or {}
+            pick = ("screen_latency_ms", "screen_latency_by_size_ms", "screen_latency_no_rebuild_ms",
+                    "screens_waiting_for_rebuild", "submit_late_ms", "slowest_screens", "requests_per_s",
+                    "evals_per_s", "mean_batch_size", "errors", "overflowed_lists")
+            out[name] = {"workload": r["workload"], "batched": {k: r["batched"][k] for k in pick},
+                         "plain": {k: r["plain"][k] for k in pick},
+                         "p50_speedup_vs_plain": r["p50_speedup_vs_plain"],
+                         "p99_speedup_vs_plain": r["p99_speedup_vs_plain"], "counts_identical": r["counts_identical"],
+                         "oracle_check": {k: oc.get(k) for k in ("screens_compared_with_oracle", "lists_with_mismatch",
+                                                                 "keys_compared")} if r["oracle_check"] else None}
+    serve = [v for k, v in out.items() if k.startswith("serve_config5") and "error" not in v]
+    if serve:
+        out["serve_config5_summary"] = {
+            "seeds": len(serve),
+            "batched_p50_le_plain_every_seed": all(v["batched"]["screen_latency_ms"]["p50"] <=
+                                                   v["plain"]["screen_latency_ms"]["p50"] for v in serve),
+            "batched_p99_le_plain_every_seed": all(v["batched"]["screen_latency_ms"]["p99"] <=
+                                                   v["plain"]["screen_latency_ms"]["p99"] for v in serve),
+            "counts_identical_every_seed": all(v["counts_identical"] for v in serve),
+            "p50_speedup_vs_plain": [round(v["p50_speedup_vs_plain"], 3) for v in serve],
+            "p99_speedup_vs_plain": [round(v["p99_speedup_vs_plain"], 3) for v in serve]}
+    return out
 
 
 def run_e2e(scr, torch, ctx, run, args):
@@ -520,7 +599,8 @@ def rooflines(wl, k3_s, tab_s, n_surv):
     binding = ("on-chip: the L1 data pipe and instruction issue; the tables are read from DRAM about "
                "once (low 32-bit planes) and re-read across scales from L2")
     common = {"bound": "hbm", "peak": peak, "unit": "GB/s", "traffic": traffic, "peak_source": src,
-              "kernel": "k_screen", "kernel_ms": 1e3 * k3_s, "binding": binding}
+              "kernel": "k_screen", "kernel_ms": 1e3 * k3_s, "binding": binding,
+              "onchip": recorded_onchip(H, W)}
     if alg1 <= peak:
         roofline = dict(common, achieved=alg1, frac=alg1 / peak, model=per_scale_model, compulsory=compulsory)
     else:
@@ -551,7 +631,7 @@ def dtype_of(wl):
     return "u32" if wl.sum_bits == wl.sq_bits == 32 else ("u64" if wl.sum_bits == 64 else "u32+u64")
 
 
-def emit(args, wl, world, m, e2e, surv, second=None):
+def emit(args, wl, world, m, e2e, surv, second=None, legs=None):
     k3 = statistics.mean(m["k3_ms"]) / 1e3
     tab = statistics.mean(m["tab_ms"]) / 1e3
     roofline, tables_roofline = rooflines(wl, k3, tab, m["survivors"])
@@ -580,13 +660,110 @@ def emit(args, wl, world, m, e2e, surv, second=None):
     }
     if second is not None:
         line["config2"] = second
+    if legs:
+        line.update(legs)
     print(json.dumps(line), flush=True)
 
 
-def run_batched(args):
+def _covering(radii, t_min, r, scale):
+    """Scale indices whose radius R covers a copy at `scale`: t_min - 1 <= R / scale <= r + 1."""
+    return [k for k, R in enumerate(radii) if t_min - 1 <= R / scale <= r + 1]
+
+
+def batched_checks(bw, pairs, counts, offsets, keys, n_sample=12, seed=7):
+    """Full-size checks of a batched run against the oracle (after the timed
+    region): the complete key list of a sample of pairs spread over image size
+    and template radius, and every planted copy present in its pair's list at
+    a covering scale.  Batched keys are (pair << 37) | (s << 32) | (y << 16) | x."""
+    import torch
+    import oracle
+    index = {pr: k for k, pr in enumerate(pairs)}
+    cnt = counts.cpu().numpy().view(np.uint64)
+    off = offsets.cpu().numpy().view(np.uint64)
+
+    def pair_keys(k):
+        a, n = int(off[k]), int(cnt[k])
+        return keys[a:a + n]
+
+    def as_list(kk):                      # batched keys -> (s << 48) | (y << 24) | x
+        kk = kk.cpu().numpy().view(np.uint64)
+        s = (kk >> np.uint64(32)) & np.uint64(31)
+        y = (kk >> np.uint64(16)) & np.uint64(0xFFFF)
+        x = kk & np.uint64(0xFFFF)
+        return (s << np.uint64(48)) | (y << np.uint64(24)) | x
+
+    # sample: images at area quantiles x templates at radius quantiles
+    by_area = sorted(range(len(bw.images)), key=lambda i: bw.images[i].size)
+    by_r = sorted(range(len(bw.templates)), key=lambda t: (bw.templates[t].r, len(bw.templates[t].radii)))
+    rng = np.random.default_rng(seed)
+    q = np.linspace(0, 1, 4)
+    imgs = sorted({by_area[int(round(v * (len(by_area) - 1)))] for v in q})
+    sample = []
+    for i in imgs:
+        for v in np.linspace(0, 1, max(1, n_sample // len(imgs))):
+            t = by_r[int(round(v * (len(by_r) - 1)))]
+            if (i, t) in index:
+                sample.append((i, t))
+    extra = rng.choice(len(pairs), size=2, replace=False)
+    sample += [pairs[int(k)] for k in extra if pairs[int(k)] not in sample]
+    tabs = {}
+    t0 = time.perf_counter()
+    compared = mism = 0
+    detail = []
+    for (i, t) in sample:
+        ts = bw.templates[t]
+        if i not in tabs:
+            tabs[i] = oracle.Tables(bw.images[i])
+        ref = oracle.screen_workload(bw.images[i], ts.template, ts.r, max(ts.t_min, 2), ts.radii, bw.features,
+                                     bw.tol, tables=tabs[i])
+        got = as_list(pair_keys(index[(i, t)]))
+        same = got.shape == ref["list"].shape and bool(np.array_equal(got, ref["list"]))
+        compared += len(ref["list"])
+        mism += 0 if same else 1
+        detail.append({"image": f"{bw.images[i].shape[0]}x{bw.images[i].shape[1]}", "r": ts.r,
+                       "scales": len(ts.radii), "keys": int(ref["count"]), "identical": same})
+    oracle_s = time.perf_counter() - t0
+    tabs.clear()
+    # planted copies: exact (the copy's own candidate at a covering scale) and
+    # paper-style (a survivor at a covering scale whose 2n x 2n square overlaps
+    # the copy's by at least 90% of its area, the success criterion of Sec. 6)
+    total = exact = paper = 0
+    missed = []
+    for i, pl in enumerate(bw.plants):
+        for (t, y, x, sc) in pl:
+            ts = bw.templates[t]
+            k = index[(i, t)]
+            kk = pair_keys(k)
+            hit = near = False
+            for sidx in _covering(ts.radii, max(ts.t_min, 2), ts.r, sc):
+                n = square_half(ts.radii[sidx])
+                lo = (k << 37) | (sidx << 32) | (max(0, y - n) << 16)
+                hi = (k << 37) | (sidx << 32) | (min(0xFFFF, y + n) << 16) | 0xFFFF
+                pos = torch.searchsorted(kk, torch.tensor([lo, hi + 1], dtype=torch.int64, device=kk.device))
+                seg = kk[int(pos[0]):int(pos[1])].cpu().numpy().view(np.uint64)
+                if not len(seg):
+                    continue
+                dy = ((seg >> np.uint64(16)) & np.uint64(0xFFFF)).astype(np.int64) - y
+                dx = (seg & np.uint64(0xFFFF)).astype(np.int64) - x
+                hit |= bool(((dy == 0) & (dx == 0)).any())
+                near |= bool((((2 * n - np.abs(dy)) * (2 * n - np.abs(dx)) * 10 >= 9 * 4 * n * n) &
+                              (np.abs(dx) <= 2 * n)).any())
+            total += 1
+            exact += hit
+            paper += near
+            if not (hit and near):
+                missed.append({"image": i, "template": t, "y": y, "x": x, "scale": round(sc, 3),
+                               "exact": hit, "within_90pct_overlap": near})
+    return {"pairs_compared_with_oracle": len(sample), "pairs_with_mismatch": mism, "keys_compared": compared,
+            "oracle_seconds": round(oracle_s, 1), "sample": detail,
+            "plants": {"total": total, "survive_exact": exact, "survive_within_90pct_overlap": paper,
+                       "not_both": missed[:8]}}
+
+
+def batched_leg(args, check=True):
     """Configuration 4: many images x many templates, one batched run (CUDA graph)
     against per-request plain launches (screen_features + compact_mask per pair)
-    on the same data, same outputs, same exactness."""
+    on the same data, same outputs, same exactness.  Returns the result dict."""
     import torch
     import synth
     import paper_1707_05647_gb300 as scr
@@ -663,7 +840,9 @@ def run_batched(args):
     torch.cuda.synchronize()
     req_s = e0.elapsed_time(e1) / 1e3
     same = bool(torch.equal(pcnt, counts))
-    print(json.dumps({
+    del mask, plst
+    checks = batched_checks(bw, pairs, counts, offsets, keys) if check else None
+    out = {
         "metric": METRIC, "workload": f"batched: {len(bw.images)} images (640x480..4096x3072, log-uniform) x "
                                       f"{len(bw.templates)} templates (r 8..64, 1..16 scales in [0.5, 2]), all pairs",
         "value": info["candidates"] / batch_s, "unit": UNIT, "ms_per_run": 1e3 * batch_s, "runs": args.steps,
@@ -671,10 +850,18 @@ def run_batched(args):
                         "how": "screen_features + compact_mask per pair (complete lists), stream-ordered, no host sync"},
         "speedup_vs_per_request": req_s / batch_s, "counts_identical": same,
         "candidates": info["candidates"], "survivors": n_keys, "keys_complete": int(nk[1].item()) <= keys.numel(),
+        "oracle_check": checks,
         "plan": info, "plan_seconds": plan_s, "plan_seconds_tuned_cached": plan_cached_s,
-        "clocks": clk.summary_all(), "data": "synthetic"}), flush=True)
+        "clocks": clk.summary_all(), "data": "synthetic"}
     scr.screen_batch_release(ctx, b)
     scr.screen_shutdown(ctx)
+    del keys
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batched(args):
+    print(json.dumps(batched_leg(args, check=not args.no_check)), flush=True)
 
 
 def run_joint(args):
@@ -757,11 +944,13 @@ def run_joint(args):
     scr.screen_shutdown(ctx)
 
 
-def run_serve(args):
+def serve_leg(args, rates, check=True, n_sample=12, seed=None):
     """Configuration 5: replay one seeded Poisson stream of uploads and screens
     through the serving loop, batched (continuous batching) and plain (one
     launch pair per screen), each on a fresh server warmed to the same resident
-    set; latency = done - scheduled arrival, so a late submission counts."""
+    set; latency = done - scheduled arrival, so a late submission counts.
+    With `check`, the lists of a seeded sample of the headline stream's screens
+    (kept from both modes) are compared with the oracle after the replays."""
     import queue
     import threading
     import torch
@@ -769,8 +958,18 @@ def run_serve(args):
     import paper_1707_05647_gb300 as scr
 
     torch.cuda.set_device(0)
-    rates = [float(r) for r in args.rates.split(",")]
-    w = synth.serve_workload(duration=args.duration, rate=rates[0])
+    seed = synth.BASE_SEED + 4 if seed is None else seed
+    w = synth.serve_workload(seed=seed, duration=args.duration, rate=rates[0])
+    # pool image of every upload, in upload order (warm uploads first)
+    upload_pool = list(w.warm) + [ev.image for ev in w.events if ev.kind == "upload"]
+    screens = [k for k, ev in enumerate(w.events) if ev.kind == "screen"]
+    rng = np.random.default_rng(11)
+    small = [k for k in screens if w.pool[upload_pool[w.events[k].image]].shape[0] <= 4096]
+    small_set = set(small)
+    large = [k for k in screens if k not in small_set]
+    sample = set(int(k) for k in rng.choice(small, size=min(n_sample - 2, len(small)), replace=False))
+    if large:
+        sample |= set(int(k) for k in rng.choice(large, size=min(2, len(large)), replace=False))
     ctx = scr.screen_init(0, 0)
     tmpls = [scr.template_features(ctx, ts.template, ts.r, max(ts.t_min, 2), 7) for ts in w.templates]
     params = {}
@@ -793,7 +992,7 @@ def run_serve(args):
             tot += max(rows, 0) * max(cols, 0)
         return tot
 
-    def replay(mode):
+    def replay(mode, keep=()):
         s = scr.server_create(ctx, table_budget_bytes=w.table_budget, sum_bits=w.sum_bits, sq_bits=w.sq_bits,
                               mode=mode)
         uploads = []   # image id per upload, in order
@@ -814,10 +1013,14 @@ def run_serve(args):
         meta, early = {}, {}          # request id -> (event index, buffer); results seen before their id
         state = {"done": 0, "expected": None}
 
+        kept = {}
+
         def record(k, buf, res):      # lock held
             results[k] = res
             state["done"] += 1
             if buf is not None:
+                if k in keep:
+                    kept[k] = buf[:min(int(res["count"]), cap)].copy()
                 bufs.put(buf)
 
         def collect():                # completion order: a slow request holds no one else's buffer
@@ -838,10 +1041,15 @@ def run_serve(args):
                     else:
                         early[rid] = res
 
+        # the client must submit on time: no garbage-collector pass during the
+        # replay (a full pass over the process's objects stalled submissions by
+        # tens of ms when earlier legs had left many objects behind)
+        gc.collect()
+        gc.disable()
         th = threading.Thread(target=collect)
         th.start()
         t0 = scr.server_clock_ns() + 50_000_000
-        cand = {}
+        cand, late, cost = {}, {}, {}
         for k, ev in enumerate(w.events):
             due = t0 + int(ev.t * 1e9)
             while True:
@@ -859,7 +1067,9 @@ def run_serve(args):
                 buf = bufs.get()
                 rid = scr.server_screen(s, iid, tmpls[ev.template], params[(ev.template, ev.features)], buf,
                                         arrival_ns=due)
+                late[k] = (scr.server_clock_ns() - due) / 1e6
                 cand[k] = candidates(shape, w.templates[ev.template].radii)
+                cost[k] = len(w.templates[ev.template].radii) * shape[0] * shape[1]
             with lock:
                 if rid in early:
                     record(k, buf, early.pop(rid))
@@ -868,6 +1078,7 @@ def run_serve(args):
         with lock:
             state["expected"] = len(w.events)
         th.join()
+        gc.enable()
         st = scr.server_stats(s)
         scr.server_destroy(s)
         scr_lat = np.array([(results[k]["done_ns"] - results[k]["arrival_ns"]) / 1e6 for k in cand])
@@ -880,7 +1091,25 @@ def run_serve(args):
         span = (end - t0) / 1e9
         counts = {k: results[k]["count"] for k in cand}
         sizes = np.array([r["batch_size"] for r in results.values()])
+        keys_ = list(cand)
+        small = np.array([cost[k] <= (1 << 24) for k in keys_])
+        lat_by = {}
+        for name, sel in (("small", small), ("large", ~small)):
+            if sel.any():
+                lat_by[name] = {"screens": int(sel.sum()), "p50": float(np.percentile(scr_lat[sel], 50)),
+                                "p99": float(np.percentile(scr_lat[sel], 99))}
+        lt = np.array([late[k] for k in keys_])
+        slow = sorted(range(len(keys_)), key=lambda i: -scr_lat[i])[:5]
+        slowest = [{"ms": round(float(scr_lat[i]), 3), "image": "x".join(map(str, uploads[w.events[keys_[i]].image][1])),
+                    "scales": len(w.templates[w.events[keys_[i]].template].radii),
+                    "start_delay_ms": round(float(queue_ms[i]), 3), "rebuilt": bool(rebuilt[i]),
+                    "submit_late_ms": round(float(lt[i]), 3), "batch_size": int(results[keys_[i]]["batch_size"])}
+                   for i in slow]
         return {
+            "screen_latency_by_size_ms": lat_by,
+            "submit_late_ms": {"p50": float(np.percentile(lt, 50)), "p99": float(np.percentile(lt, 99)),
+                               "max": float(lt.max())},
+            "slowest_screens": slowest,
             "screen_latency_ms": {"p50": float(np.percentile(scr_lat, 50)), "p99": float(np.percentile(scr_lat, 99)),
                                   "mean": float(scr_lat.mean()), "max": float(scr_lat.max())},
             "upload_latency_ms": {"p50": float(np.percentile(up_lat, 50)), "p99": float(np.percentile(up_lat, 99))},
@@ -903,30 +1132,53 @@ def run_serve(args):
             "batches": st["batches"] - warm_stats["batches"], "mean_batch_size": float(sizes.mean()),
             "evictions": st["evictions"], "rebuilds": st["rebuilds"], "builds": st["builds"],
             "peak_resident_gb": st["peak_resident_bytes"] / 1e9, "launches": st["launches"] - warm_stats["launches"],
-        }, counts
+        }, counts, kept
 
-    batched, cb = replay(scr.SERVE_BATCHED)
-    plain, cp = replay(scr.SERVE_PLAIN)
+    batched, cb, kept_b = replay(scr.SERVE_BATCHED, sample if check else ())
+    plain, cp, kept_p = replay(scr.SERVE_PLAIN, sample if check else ())
     n_screens = sum(1 for e in w.events if e.kind == "screen")
     head = w
     sweep = []
     for rate in rates[1:]:
         # same seed: same image pool, templates and warm set; a denser stream
-        w = synth.serve_workload(duration=args.duration, rate=rate)
+        w = synth.serve_workload(seed=seed, duration=args.duration, rate=rate)
         assert [t.r for t in w.templates] == [t.r for t in head.templates]
         params.update({(ev.template, ev.features): scr.Params(w.templates[ev.template].radii, ev.features,
                                                                w.tol.mean_rel, w.tol.std_rel, w.tol.grad_rel,
                                                                w.tol.grad_abs)
                        for ev in w.events if ev.kind == "screen" and (ev.template, ev.features) not in params})
-        b2, c2b = replay(scr.SERVE_BATCHED)
-        p2, c2p = replay(scr.SERVE_PLAIN)
+        b2, c2b, _ = replay(scr.SERVE_BATCHED)
+        p2, c2p, _ = replay(scr.SERVE_PLAIN)
         sweep.append({"rate": rate, "requests": len(w.events), "counts_identical": c2b == c2p,
                       "batched": {k: b2[k] for k in ("screen_latency_ms", "evals_per_s", "requests_per_s",
                                                      "mean_batch_size", "errors")},
                       "plain": {k: p2[k] for k in ("screen_latency_ms", "evals_per_s", "requests_per_s",
                                                    "mean_batch_size", "errors")}})
     w = head
-    print(json.dumps({
+    checks = None
+    if check:
+        import oracle
+        t0 = time.perf_counter()
+        detail, mism = [], 0
+        for k in sorted(sample):
+            ev = w.events[k]
+            ts = w.templates[ev.template]
+            img = w.pool[upload_pool[ev.image]]
+            ref = oracle.screen_workload(img, ts.template, ts.r, max(ts.t_min, 2), ts.radii, ev.features, w.tol)
+            want = ref["list"][:cap]
+            row = {"image": f"{img.shape[0]}x{img.shape[1]}", "r": ts.r, "scales": len(ts.radii),
+                   "features": ev.features, "count": int(ref["count"])}
+            for name, kept in (("batched", kept_b), ("plain", kept_p)):
+                got = kept.get(k)
+                ok = got is not None and got.shape == want.shape and bool(np.array_equal(got, want)) and \
+                    (cb if name == "batched" else cp)[k] == ref["count"]
+                row[name] = ok
+                mism += 0 if ok else 1
+            detail.append(row)
+        checks = {"screens_compared_with_oracle": len(sample), "lists_with_mismatch": mism,
+                  "keys_compared": int(sum(min(r["count"], cap) for r in detail)) * 2,
+                  "oracle_seconds": round(time.perf_counter() - t0, 1), "sample": detail}
+    out = {
         "metric": "served screen latency p50/p99 (ms) and evaluations/s", "workload":
             f"serving: Poisson {w.rate:.0f} req/s for {w.duration:g} s ({len(w.events)} requests, "
             f"{len(w.events) - n_screens} uploads of side 256..8192 log-uniform, {n_screens} screens r 8..96, "
@@ -935,10 +1187,18 @@ def run_serve(args):
         "batched": batched, "plain": plain,
         "p99_speedup_vs_plain": plain["screen_latency_ms"]["p99"] / batched["screen_latency_ms"]["p99"],
         "p50_speedup_vs_plain": plain["screen_latency_ms"]["p50"] / batched["screen_latency_ms"]["p50"],
-        "counts_identical": cb == cp, "list_cap": cap, "load_sweep": sweep, "data": "synthetic"}), flush=True)
+        "counts_identical": cb == cp, "oracle_check": checks, "list_cap": cap, "load_sweep": sweep,
+        "seed": seed, "data": "synthetic"}
     for t in tmpls:
         scr.template_release(ctx, t)
     scr.screen_shutdown(ctx)
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_serve(args):
+    rates = [float(r) for r in args.rates.split(",")]
+    print(json.dumps(serve_leg(args, rates, check=not args.no_check, seed=args.seed)), flush=True)
 
 
 def main():
@@ -955,6 +1215,8 @@ def main():
                     help="crop the image to size x size (smaller ncu captures)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the 4096x4096 run after config 3")
+    ap.add_argument("--no-check", action="store_true", help="skip the oracle checks of the batched and serve legs")
+    ap.add_argument("--seed", type=int, default=None, help="serve workload seed (default 1004)")
     ap.add_argument("--workload", default="single", choices=["single", "batched", "serve", "joint"])
     ap.add_argument("--duration", type=float, default=2.0, help="seconds of arrivals (serve workload)")
     ap.add_argument("--rates", default="2000,8000,16000",

@@ -274,8 +274,10 @@ const char *compact_mask_noalloc_error(void);
 
 /* ---- a3..a5 together ----------------------------------------------------- */
 
-/* screen_features + compact_mask, then wait for the stream and return the
- * survivor count in *n_survivors (host).  Returns SCR_EOVERFLOW when the count
+/* The whole screen of Sec. 5, Algorithm 1 on resident tables: every candidate
+ * (scale, position) whose features pass the template's bounds goes into the
+ * result set R.  screen_features + compact_mask, then wait for the stream and
+ * return the survivor count in *n_survivors (host).  Returns SCR_EOVERFLOW when the count
  * exceeds list_cap (the mask is complete and the list holds the first list_cap
  * keys). */
 int screen_positions(scr_ctx *ctx, const scr_tables *t, const scr_tmpl *tm, const scr_params *p,
@@ -364,13 +366,21 @@ void screen_batch_release(scr_ctx *ctx, scr_batch *b);
  * and rebuild from the host copy the tables of images evicted earlier: they admit
  * new tables by the table budget, evicting least recently used tables that no
  * queued or running screen holds, and waits for running screens to release
- * tables when the rest does not make room.  The screener thread, whenever it is
- * free, takes every screen whose tables are resident (continuous batching, at
- * most max_batch) and screens them in one batched run (SCR_SERVE_BATCHED:
- * records grouped per (image, star radius) as in screen_batch_create) or one
- * plain screen_features + compact_mask each (SCR_SERVE_PLAIN), while the
- * builder's copies and table builds overlap on the device; screens whose tables
- * are being built join a later batch.  Each request's survivor list, in
+ * tables when the rest does not make room.  The screener thread serves the
+ * screens whose tables are resident, in one of two modes:
+ *   SCR_SERVE_BATCHED (continuous batching): whenever screens are ready and
+ *   there is room in flight, it takes them all (at most max_batch) as one batch,
+ *   orders the batch shortest first and enqueues every screen without waiting
+ *   (the screening kernel into a stream-ordered mask, the compaction straight
+ *   into mapped host memory); screens of at most 2^small_log2 candidate slots
+ *   (scales x pixels) run on a higher-priority stream, so they overtake large
+ *   screens already on the device; each screen completes as soon as its own
+ *   work is done, while later batches are admitted.  In flight at most
+ *   max_inflight screens and 4 GiB of their masks.
+ *   SCR_SERVE_PLAIN: one screen_features + compact_mask per screen, each
+ *   waited for before the next.
+ * The builders' copies and table builds overlap on the device with both;
+ * screens whose tables are being built join a later batch.  Each request's survivor list, in
  * compact_mask's key format and order, goes to the caller's host buffer.  A
  * request's result does not depend on which other requests share its batch, nor
  * on the mode.  This is the paper's screen (Sec. 5, Algorithm 1) served to many
@@ -385,8 +395,8 @@ typedef struct {
     int32_t mode;                /* SCR_SERVE_BATCHED or SCR_SERVE_PLAIN */
     int32_t max_batch;           /* most requests per batch; 0 = every queued request */
     int32_t start_held;          /* 1: queue requests without serving them until server_hold(s, 0) */
-    int32_t words_per_warp;      /* batched launch shape (0 = 4) */
-    int32_t blocks_per_sm;       /* (0 = 4) */
+    int32_t small_log2;          /* batched: priority lane for screens of <= 2^small_log2 candidate slots (0 = 24) */
+    int32_t max_inflight;        /* batched: screens enqueued and not yet complete, at most (0 = 64) */
     int32_t reserved;
 } scr_server_config;
 
@@ -406,7 +416,7 @@ typedef struct {
     uint64_t requests, batches, uploads, screens;
     uint64_t builds, rebuilds, evictions;
     uint64_t resident_images, resident_bytes, peak_resident_bytes;
-    uint64_t mask_bytes;         /* device bytes of the batched path's mask buffers */
+    uint64_t mask_bytes;         /* device bytes of the plain path's mask buffer */
     uint64_t launches;           /* kernels the server launched */
     uint64_t build_ns;           /* time the builders spent on uploads, rebuilds and evictions (summed), of which: */
     uint64_t build_copy_ns;      /*   copying images to the device */

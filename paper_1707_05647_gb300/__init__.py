@@ -72,7 +72,7 @@ class _Joint(ctypes.Structure):
 class _ServerConfig(ctypes.Structure):
     _fields_ = [("table_budget_bytes", ctypes.c_uint64), ("sum_bits", ctypes.c_int32), ("sq_bits", ctypes.c_int32),
                 ("mode", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("start_held", ctypes.c_int32),
-                ("words_per_warp", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("small_log2", ctypes.c_int32), ("max_inflight", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class _RequestResult(ctypes.Structure):
@@ -417,9 +417,9 @@ def server_clock_ns() -> int:
 
 
 def server_create(ctx, table_budget_bytes: int = 0, sum_bits: int = 32, sq_bits: int = 64, mode: int = SERVE_BATCHED,
-                  max_batch: int = 0, start_held: bool = False, words_per_warp: int = 0, blocks_per_sm: int = 0):
-    cfg = _ServerConfig(table_budget_bytes, sum_bits, sq_bits, mode, max_batch, int(start_held), words_per_warp,
-                        blocks_per_sm, 0)
+                  max_batch: int = 0, start_held: bool = False, small_log2: int = 0, max_inflight: int = 0):
+    cfg = _ServerConfig(table_budget_bytes, sum_bits, sq_bits, mode, max_batch, int(start_held), small_log2,
+                        max_inflight, 0)
     s = ctypes.c_void_p()
     _check(load().server_create(ctx, ctypes.byref(cfg), ctypes.byref(s)))
     return s

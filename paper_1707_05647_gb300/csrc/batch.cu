@@ -98,22 +98,16 @@ __global__ void __launch_bounds__(32 * kBatchWarps, (WPW >= 8 ? 3 : 4)) k_batch(
     // so the units in flight stay within a few rows of each other and the
     // table rows they read are still in L2 when the next radius needs them.
     // The next index is fetched one unit ahead to hide the atomic's latency.
-    // With a unit limit the warp fetches no index it will not process.
     int img = -1;   // image of the current unit (warp-uniform)
     uint64_t next = 0;
-    uint32_t taken = 0;
     if (lane == 0)
         next = atomicAdd((unsigned long long *)a.next_unit, 1ull);
     next = __shfl_sync(0xffffffffu, next, 0);
     while (next < (uint64_t)a.n_units) {
         const int64_t u = (int64_t)next * a.unit_stride;
-        if (a.units_per_warp == 0 || ++taken < a.units_per_warp) {
-            if (lane == 0)
-                next = atomicAdd((unsigned long long *)a.next_unit, 1ull);
-            next = __shfl_sync(0xffffffffu, next, 0);
-        } else {
-            next = ~0ull;   // this is the warp's last unit
-        }
+        if (lane == 0)
+            next = atomicAdd((unsigned long long *)a.next_unit, 1ull);
+        next = __shfl_sync(0xffffffffu, next, 0);
         if (img < 0) {
             // first unit of this warp: last image with unit0 <= u (binary search)
             int l = 0, h = a.n_images - 1;
@@ -271,17 +265,6 @@ __global__ void __launch_bounds__(32 * kBatchWarps, (WPW >= 8 ? 3 : 4)) k_batch(
                 }
                 if (!__any_sync(0xffffffffu, keep))
                     continue;
-                if (a.masks) {   // mask mode: lane j writes word j of the record's row
-                    uint32_t mine = 0;
-#pragma unroll
-                    for (int j = 0; j < WPW; ++j) {
-                        const uint32_t bits = __ballot_sync(0xffffffffu, (keep >> j) & 1u);
-                        mine = lane == j ? bits : mine;
-                    }
-                    if (mine)
-                        a.masks[__ldg(&rc->mask_plane) + (int64_t)y * __ldg(&ip->Wwords) + w0 + lane] = mine;
-                    continue;
-                }
                 const uint64_t key_hi = ((uint64_t)__ldg(&rc->pair) << 37) | ((uint64_t)__ldg(&rc->s) << 32) |
                                         ((uint64_t)y << 16);
                 uint32_t nrec = 0;   // survivors of this record in the warp's words

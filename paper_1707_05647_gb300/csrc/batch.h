@@ -37,7 +37,6 @@ struct BRecord {                       // one (pair, scale) test
     uint64_t V_rng;
     int64_t N_lo;
     uint64_t N_rng;
-    int64_t mask_plane;                // mask mode: first word of this (pair, scale) plane
 };
 
 struct BatchArgs {
@@ -48,13 +47,10 @@ struct BatchArgs {
     int32_t n_groups;
     int64_t n_units;                   // units this launch processes
     int64_t unit_stride;               // unit u of the launch is unit u * unit_stride of the plan
-    uint32_t units_per_warp;           // 0: warps run until no unit is left (persistent); else a
-                                       // warp stops after this many, so blocks come and go
     uint64_t *counts;                  // per pair
     uint32_t *union_mask;              // per image [H][Wwords], may be null
     uint64_t *keys;
     uint64_t keys_cap;
-    uint32_t *masks;                   // non-null: mask mode (bits to each record's plane, no keys, no counts)
     uint64_t *n_reserved;              // key slots handed out (chunks of kKeyChunk)
     uint64_t *next_unit;               // next unit to hand out (zero before the launch)
 };

@@ -178,160 +178,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const uint32_t *mask, uint
     }
 }
 
-// ---- several masks at once (segments aligned to chunks) ----------------------
-
-static_assert(kChunk == kCompactChunk, "chunk size");
-
-__device__ __forceinline__ int seg_of_chunk(const MaskSeg *segs, int nseg, uint32_t c) {
-    int lo = 0, hi = nseg - 1;   // last segment with chunk0 <= c
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (segs[mid].chunk0 <= c)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
-}
-
-// per-chunk popcounts (padding words are zero, so no segment lookup is needed)
-__global__ void __launch_bounds__(kThreads) k_seg_count(const uint32_t *mask, uint64_t total, uint32_t *counts,
-                                                        uint32_t nchunks) {
-    pdl_begin();
-    __shared__ uint32_t sh[72];
-    for (uint32_t b = blockIdx.x; b < nchunks; b += gridDim.x) {
-        const uint64_t first = (uint64_t)b * kChunk + (uint64_t)threadIdx.x * kWordsPerThread;
-        uint32_t w[kWordsPerThread];
-        load_words(mask, total, first, w);
-        uint32_t c = 0;
-#pragma unroll
-        for (int k = 0; k < kWordsPerThread; ++k)
-            c += __popc(w[k]);
-        uint32_t tot;
-        block_excl_scan(c, sh, tot);
-        if (threadIdx.x == 0)
-            counts[b] = tot;
-        __syncthreads();
-    }
-}
-
-// one block per segment: exclusive scan of its chunk counts, and its total
-__global__ void __launch_bounds__(1024) k_seg_scan(const MaskSeg *segs, int nseg, const uint32_t *counts,
-                                                   uint64_t *offsets, uint64_t *out_counts) {
-    pdl_begin();
-    __shared__ uint64_t sh[72];
-    const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
-    for (int g = blockIdx.x; g < nseg; g += gridDim.x) {
-        const uint32_t c0 = segs[g].chunk0, nc = segs[g].nchunks;
-        uint64_t carry = 0;
-        for (uint32_t base = 0; base < nc; base += 1024) {
-            const uint32_t k = base + t;
-            const uint64_t v = k < nc ? counts[c0 + k] : 0;
-            uint64_t inc = v;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint64_t u = __shfl_up_sync(0xffffffffu, inc, o);
-                if (lane >= o)
-                    inc += u;
-            }
-            if (lane == 31)
-                sh[wp] = inc;
-            __syncthreads();
-            if (wp == 0) {
-                const uint64_t s0 = sh[lane];
-                uint64_t si = s0;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint64_t u = __shfl_up_sync(0xffffffffu, si, o);
-                    if (lane >= o)
-                        si += u;
-                }
-                sh[32 + lane] = si - s0;
-                if (lane == 31)
-                    sh[64] = si;
-            }
-            __syncthreads();
-            if (k < nc)
-                offsets[c0 + k] = carry + sh[32 + wp] + inc - v;
-            carry += sh[64];
-            __syncthreads();
-        }
-        if (t == 0)
-            out_counts[g] = carry;
-    }
-}
-
-__global__ void __launch_bounds__(kThreads) k_seg_scatter(const uint32_t *mask, uint64_t total, const MaskSeg *segs,
-                                                          int nseg, const uint32_t *counts, const uint64_t *offsets,
-                                                          uint64_t *out, uint32_t nchunks) {
-    pdl_begin();
-    __shared__ uint32_t sh[72];
-    for (uint32_t b = blockIdx.x; b < nchunks; b += gridDim.x) {
-        const int g = seg_of_chunk(segs, nseg, b);
-        const uint64_t cap = segs[g].cap;
-        if (counts[b] == 0 || offsets[b] >= cap)   // block-uniform
-            continue;
-        const uint64_t word0 = segs[g].word0, out0 = segs[g].out0;
-        const uint64_t rowWords = (uint64_t)segs[g].Wwords, planeWords = (uint64_t)segs[g].H * rowWords;
-        const uint64_t first = (uint64_t)b * kChunk + (uint64_t)threadIdx.x * kWordsPerThread;
-        uint32_t w[kWordsPerThread];
-        load_words(mask, total, first, w);
-        uint32_t c = 0;
-#pragma unroll
-        for (int k = 0; k < kWordsPerThread; ++k)
-            c += __popc(w[k]);
-        uint32_t tot;
-        uint64_t pos = offsets[b] + block_excl_scan(c, sh, tot);
-        __syncthreads();
-        if (c == 0 || pos >= cap)
-            continue;
-#pragma unroll
-        for (int k = 0; k < kWordsPerThread; ++k) {
-            uint32_t bits = w[k];
-            if (!bits)
-                continue;
-            const uint64_t wi = first + k - word0;
-            const uint64_t s = wi / planeWords;
-            const uint64_t rem = wi - s * planeWords;
-            const uint64_t y = rem / rowWords;
-            const uint64_t x0 = (rem - y * rowWords) * 32;
-            const uint64_t keyb = (s << 48) | (y << 24);
-            while (bits) {
-                const int bit = __ffs(bits) - 1;
-                bits &= bits - 1;
-                if (pos < cap)
-                    out[out0 + pos] = keyb | (x0 + bit);
-                ++pos;
-            }
-        }
-    }
-}
-
 }  // namespace
-
-size_t compact_segments_scratch_bytes(uint64_t nchunks) {
-    return ((nchunks * 4 + 255) & ~uint64_t(255)) + nchunks * 8 + 256;
-}
-
-cudaError_t launch_compact_segments(const uint32_t *mask, const MaskSeg *segs, int nseg, uint64_t nchunks,
-                                    uint64_t *out, uint64_t *out_counts, void *scratch, cudaStream_t st,
-                                    uint64_t *launches) {
-    uint32_t *counts = (uint32_t *)scratch;
-    uint64_t *offsets = (uint64_t *)((char *)scratch + ((nchunks * 4 + 255) & ~uint64_t(255)));
-    const uint64_t total = nchunks * kChunk;
-    const unsigned grid = (unsigned)std::min<uint64_t>(std::max<uint64_t>(nchunks, 1), 152 * 4);
-    cudaError_t e;
-    if (launches)
-        *launches += 3;
-    if ((e = launch_pdl(k_seg_count, dim3(grid), dim3(kThreads), st, mask, total, counts, (uint32_t)nchunks)) !=
-        cudaSuccess)
-        return e;
-    if ((e = launch_pdl(k_seg_scan, dim3((unsigned)std::min(nseg, 1024)), dim3(1024), st, segs, nseg,
-                        (const uint32_t *)counts, offsets, out_counts)) != cudaSuccess)
-        return e;
-    return launch_pdl(k_seg_scatter, dim3(grid), dim3(kThreads), st, mask, total, segs, nseg,
-                      (const uint32_t *)counts, (const uint64_t *)offsets, out, (uint32_t)nchunks);
-}
 
 size_t compact_scratch_bytes(uint64_t total_words) {
     const uint64_t nchunks = (total_words + kChunk - 1) / kChunk;

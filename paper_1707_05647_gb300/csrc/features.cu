@@ -142,12 +142,17 @@ k_screen(const __grid_constant__ ScreenArgs a) {
                 const Corners cq(L2, T2, p.oL, p.oT);
 #pragma unroll
                 for (int h = 0; h < WPW; h += WPW / 2) {
+                    // a lane with a live word in this half reads all of the
+                    // half's corners (one condition, not one per read); the
+                    // test of a word that was already dead changes nothing
+                    if (!((keep >> h) & ((1u << (WPW / 2)) - 1)))
+                        continue;
                     uint32_t q[WPW / 2][8];
 #pragma unroll
                     for (int j = 0; j < WPW / 2; ++j)
 #pragma unroll
                         for (int k = 0; k < 8; ++k)
-                            q[j][k] = ((keep >> (h + j)) & 1u) ? ld(cq.p[k] + 32 * (h + j)) : 0u;
+                            q[j][k] = ld(cq.p[k] + 32 * (h + j));
 #pragma unroll
                     for (int j = 0; j < WPW / 2; ++j) {
                         const uint32_t qs = q[j][0] - q[j][1] - q[j][2] + q[j][3];

@@ -156,26 +156,6 @@ size_t moment_scratch_bytes(int H, int W);
 cudaError_t launch_moment_tables(const uint8_t *img, int64_t ipitch, int H, int W, int64_t pitch, uint64_t *Mx,
                                  uint64_t *My, void *scratch, cudaStream_t st, uint64_t *launches);
 
-// One mask in a buffer of several (segmented compaction): S planes of H rows of
-// Wwords words starting at word0, a multiple of kCompactChunk; the words up to
-// the next chunk boundary are zero.  Its first `cap` keys go to out[out0 ..].
-struct MaskSeg {
-    uint64_t word0, words;
-    uint32_t chunk0, nchunks;
-    int32_t H, Wwords;
-    uint64_t cap, out0;
-};
-constexpr int kCompactChunk = 4096;   // words per compaction chunk
-
-// Compact every segment of `mask` (chunks [0, nchunks) cover them all, in
-// segment order): out_counts[i] = set bits of segment i, and its first cap keys
-// (s << 48) | (y << 24) | x, ascending, at out[segs[i].out0 ..].  out and
-// out_counts may be host-mapped.  scratch: compact_segments_scratch_bytes.
-size_t compact_segments_scratch_bytes(uint64_t nchunks);
-cudaError_t launch_compact_segments(const uint32_t *mask, const MaskSeg *segs, int nseg, uint64_t nchunks,
-                                    uint64_t *out, uint64_t *out_counts, void *scratch, cudaStream_t st,
-                                    uint64_t *launches);
-
 size_t compact_scratch_bytes(uint64_t total_words);
 cudaError_t launch_compact(const uint32_t *mask, uint64_t total_words, int H, int Wwords,
                            uint64_t *list, uint64_t cap, uint64_t *count, void *scratch,

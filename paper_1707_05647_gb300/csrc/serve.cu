@@ -1,13 +1,16 @@
-// Serving loop of include/screen.h.  Two threads per server:
+// Serving loop of include/screen.h.  Three threads per server:
 //  - two builders build the tables of uploaded images and rebuild evicted ones
 //    from their host copy (each on its own stream), admitting new tables by the
-//    table budget: it evicts least recently used tables that no ready or running
-//    screen pins, and waits for pins to be released when that is not enough;
-//  - the screener takes every screen whose tables are resident whenever it is
-//    free (continuous batching) and runs them as one batched launch or as one
-//    plain launch pair each, then hands each request its list in the
-//    single-image key format.
-// Copies and table builds of the builder overlap with the screener's kernels.
+//    table budget: they evict least recently used tables that no ready or
+//    running screen pins, and wait for pins to be released when that is not
+//    enough;
+//  - the screener serves the screens whose tables are resident.  Batched mode
+//    (continuous batching): each turn it takes every ready screen, orders them
+//    shortest first and enqueues each one's screening kernel and compaction
+//    without waiting (small screens on a higher-priority stream), then retires
+//    every screen whose own work has completed; plain mode runs one screen at
+//    a time and waits for it.  Lists come back in the single-image key format.
+// Copies and table builds of the builders overlap with the screener's kernels.
 #include <condition_variable>
 #include <deque>
 #include <map>
@@ -107,19 +110,17 @@ struct scr_server {
     std::map<size_t, size_t> free_by_off;              // the arena's holes: offset -> size
     std::multimap<size_t, size_t> free_by_size;        // size -> offset
     scr_server_stats stats = {};
-    // screener buffers: the plain path's, and one set per batched run in flight
+    // screener buffers of the plain path
     DevBuf mask_dev, list_dev, small_dev;
     DevBuf keys_host, small_host;                      // pinned
     uint64_t list_dev_cap = 0;
-    struct Slot {
-        DevBuf mask_dev;       // every request's mask planes, one segment each
-        DevBuf segs_dev;       // the segments (MaskSeg)
-        DevBuf scratch_dev;    // segmented compaction scratch
-        DevBuf desc_host;      // pinned copy of the plan and the segments for the upload
-        DevBuf out_host;       // mapped pinned: counts[n] | staged keys
-        cudaEvent_t done = nullptr;
-        bool busy = false;
-    } slots[2];
+    // batched path: small screens go on a higher-priority stream so they do not
+    // queue behind large ones; mapped pinned staging buffers (count | keys) and
+    // events are pooled and reused
+    cudaStream_t st_small = nullptr;
+    std::vector<cudaEvent_t> free_events;
+    std::multimap<size_t, void *> free_stage;          // bytes -> mapped pinned buffer
+    std::vector<std::pair<void *, size_t>> all_stage;  // every staging buffer, freed at destroy
 };
 
 namespace {
@@ -153,23 +154,6 @@ int grow_host(DevBuf &b, size_t bytes) {
         cudaGetLastError();
         b.p = nullptr;
         return fail(SCR_ENOMEM, "pinned host allocation of %zu bytes failed", bytes);
-    }
-    b.bytes = bytes;
-    return SCR_OK;
-}
-
-int grow_mapped(DevBuf &b, size_t bytes) {
-    if (b.bytes >= bytes)
-        return SCR_OK;
-    if (b.p)
-        cudaFreeHost(b.p);
-    b.p = nullptr;
-    b.bytes = 0;
-    bytes = std::max<size_t>(bytes + (bytes >> 2), 1 << 20);
-    if (cudaHostAlloc(&b.p, bytes, cudaHostAllocMapped) != cudaSuccess) {
-        cudaGetLastError();
-        b.p = nullptr;
-        return fail(SCR_ENOMEM, "mapped host allocation of %zu bytes failed", bytes);
     }
     b.bytes = bytes;
     return SCR_OK;
@@ -500,173 +484,123 @@ uint64_t mask_words_of(const SrvRequest *r) {
     return (uint64_t)r->p.n_scales * r->img->H * ((r->img->W + 31) / 32);
 }
 
-uint64_t seg_words_of(const SrvRequest *r) {   // rounded up to whole compaction chunks
-    return (mask_words_of(r) + kCompactChunk - 1) / kCompactChunk * kCompactChunk;
-}
+// Work of one screen, in candidate slots (scales x pixels): orders a batch
+// shortest first and picks the stream lane.
+uint64_t cost_of(const SrvRequest *r) { return (uint64_t)r->p.n_scales * r->img->H * r->img->W; }
 
-struct StageLayout {
-    size_t counts, keys, bytes;          // byte offsets in the mapped area
-    std::vector<uint64_t> cap, off;      // per request: staged keys and their offset
+// A screen of at most 2^small_log2 candidate slots (default 2^24) takes the
+// priority lane; at most max_inflight screens (default 64) and 4 GiB of their
+// masks are enqueued and not yet retired (one screen larger than that runs alone).
+uint64_t small_cost(const scr_server *s) { return 1ull << (s->cfg.small_log2 ? s->cfg.small_log2 : 24); }
+size_t max_inflight(const scr_server *s) { return s->cfg.max_inflight ? (size_t)s->cfg.max_inflight : 64; }
+constexpr uint64_t kInflightMaskBytes = 4ull << 30;
+
+// One screen of the batched path from enqueue to retirement.
+struct Inflight {
+    SrvRequest *r = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    void *mask = nullptr;
+    size_t mask_bytes = 0;
+    void *stage = nullptr;        // mapped pinned: count | staged keys
+    size_t stage_bytes = 0;
+    uint64_t staged_cap = 0;
 };
 
-StageLayout stage_layout(const std::vector<SrvRequest *> &scr) {
-    StageLayout L;
-    L.counts = 0;
-    L.keys = (8 * scr.size() + 255) & ~size_t(255);
-    uint64_t pos = 0;
-    for (SrvRequest *r : scr) {
-        const uint64_t c = std::min(r->list_cap, kStageKeys);
-        L.cap.push_back(c);
-        L.off.push_back(pos);
-        pos += c;
+int stage_get(scr_server *s, size_t bytes, void **p, size_t *got) {
+    auto it = s->free_stage.lower_bound(bytes);
+    if (it != s->free_stage.end()) {
+        *p = it->second;
+        *got = it->first;
+        s->free_stage.erase(it);
+        return SCR_OK;
     }
-    L.bytes = L.keys + pos * 8 + 8;
-    return L;
+    size_t sz = 64 << 10;
+    while (sz < bytes)
+        sz <<= 1;
+    if (cudaHostAlloc(p, sz, cudaHostAllocMapped) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(SCR_ENOMEM, "mapped host allocation of %zu bytes failed", sz);
+    }
+    s->all_stage.emplace_back(*p, sz);
+    *got = sz;
+    return SCR_OK;
 }
 
-// Enqueue one batched run of `scr` on the screener stream using slot `sl`:
-// the screening kernel in mask mode writes each (request, scale) plane of a
-// zeroed mask buffer (records grouped per (image, star radius), so positions
-// and radii shared by several requests are computed once), then one segmented
-// compaction writes each request's first keys, in compact_mask's format and
-// order, and its count into mapped host memory; then the slot's event.
+void release_inflight(scr_server *s, Inflight &f) {
+    if (f.mask)
+        dev_free(s->ctx, f.mask, f.mask_bytes, f.st);   // stream-ordered: after the screen's kernels
+    if (f.stage)
+        s->free_stage.emplace(f.stage_bytes, f.stage);
+    if (f.ev)
+        s->free_events.push_back(f.ev);
+    f.mask = f.stage = nullptr;
+    f.ev = nullptr;
+}
+
+// Enqueue one screen: the single-image screening kernel writes its mask (a
+// stream-ordered allocation from the context's pool), the compaction writes its
+// count and first keys into mapped host memory, then the screen's event.
 // Nothing waits for the device.
-int launch_batched(scr_server *s, scr_server::Slot &sl, const std::vector<SrvRequest *> &scr) {
-    const int n = (int)scr.size();
-    std::vector<const scr_tables *> tabs;
-    std::unordered_map<SrvImage *, int> idx;
-    std::vector<scr_pair> pairs(n);
-    std::vector<const scr_tmpl *> tms(n);
-    std::vector<scr_params> ps(n);
-    std::vector<MaskSeg> segs(n);
-    const StageLayout L = stage_layout(scr);
-    uint64_t words = 0;
-    for (int k = 0; k < n; ++k) {
-        SrvRequest *r = scr[k];
-        auto it = idx.find(r->img);
-        if (it == idx.end()) {
-            it = idx.emplace(r->img, (int)tabs.size()).first;
-            tabs.push_back(r->img->t);
-        }
-        pairs[k].image = it->second;
-        pairs[k].tmpl = k;
-        tms[k] = r->tm;
-        ps[k] = r->p;
-        MaskSeg &g = segs[k];
-        g.word0 = words;
-        g.words = mask_words_of(r);
-        g.chunk0 = (uint32_t)(words / kCompactChunk);
-        g.nchunks = (uint32_t)(seg_words_of(r) / kCompactChunk);
-        g.H = r->img->H;
-        g.Wwords = (r->img->W + 31) / 32;
-        g.cap = L.cap[k];
-        g.out0 = L.off[k];
-        words += seg_words_of(r);
-    }
-    const uint64_t nchunks = words / kCompactChunk;
+int enqueue_screen(scr_server *s, Inflight &f) {
+    SrvRequest *r = f.r;
+    const uint64_t words = mask_words_of(r);
+    f.st = cost_of(r) <= small_cost(s) ? s->st_small : s->st;
+    f.staged_cap = std::min(r->list_cap, kStageKeys);
     int rc;
-    if ((rc = grow_dev(s, sl.mask_dev, words * 4, s->st)) ||
-        (rc = grow_dev(s, sl.segs_dev, (size_t)n * sizeof(MaskSeg), s->st)) ||
-        (rc = grow_dev(s, sl.scratch_dev, compact_segments_scratch_bytes(nchunks), s->st)) ||
-        (rc = grow_mapped(sl.out_host, L.bytes)))
+    if (s->free_events.empty()) {
+        cudaEvent_t ev;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SCR_ECUDA, "event creation failed");
+        }
+        s->free_events.push_back(ev);
+    }
+    f.ev = s->free_events.back();
+    s->free_events.pop_back();
+    if ((rc = stage_get(s, 8 + f.staged_cap * 8, &f.stage, &f.stage_bytes)))
         return rc;
-    s->stats.mask_bytes = s->slots[0].mask_dev.bytes + s->slots[1].mask_dev.bytes;
-    char *dout = device_view<char>(sl.out_host.p);
-    if (!dout)
+    f.mask_bytes = (size_t)std::max<uint64_t>(words, 1) * 4;
+    if ((rc = dev_alloc(s->ctx, f.mask_bytes, f.st, &f.mask))) {
+        f.mask = nullptr;
+        return rc;
+    }
+    uint64_t *dst = device_view<uint64_t>(f.stage);
+    if (!dst)
         return fail(SCR_ECUDA, "no device address for the mapped staging area");
-    scr_batch *b = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(s->ctx->mu);
-        rc = batch_prepare(s->ctx, tabs.data(), (int)tabs.size(), tms.data(), ps.data(), n, pairs.data(), n,
-                           (uint64_t *)sl.segs_dev.p, nullptr, nullptr, nullptr, 0, (uint64_t *)sl.segs_dev.p, s->st,
-                           &b);
-    }
-    if (rc)
+    const uint64_t before = s->ctx->launches.load();
+    if ((rc = screen_features(s->ctx, r->img->t, r->tm, &r->p, (uint32_t *)f.mask, words, (scr_stream)f.st)) ||
+        (rc = compact_mask(s->ctx, (const uint32_t *)f.mask, r->p.n_scales, r->img->H, r->img->W,
+                           f.staged_cap ? dst + 1 : nullptr, f.staged_cap, dst, (scr_stream)f.st)))
         return rc;
-    for (BRecord &rc_ : b->records)   // each (request, scale) plane of the mask buffer
-        rc_.mask_plane = (int64_t)(segs[rc_.pair].word0 + (uint64_t)rc_.s * segs[rc_.pair].H * segs[rc_.pair].Wwords);
-    batch_set_shape(b, s->cfg.words_per_warp ? s->cfg.words_per_warp : 4,
-                    s->cfg.blocks_per_sm ? s->cfg.blocks_per_sm : 4);
-    // Short-lived blocks: each warp takes at most kUnitsPerWarp units and the
-    // grid covers the plan, so blocks keep finishing and the builders'
-    // higher-priority table builds get SMs while a batch runs.
-    {
-        constexpr uint32_t kUnitsPerWarp = 4;
-        const uint64_t warps = ((uint64_t)b->n_units + kUnitsPerWarp - 1) / kUnitsPerWarp;
-        const uint64_t blocks = (warps + kBatchWarpsPerBlock - 1) / kBatchWarpsPerBlock;
-        b->grid = (int)std::max<uint64_t>(std::min<uint64_t>(blocks, 1u << 20), (uint64_t)b->grid);
-        b->args.units_per_warp = (uint32_t)std::max<uint64_t>(
-            1, ((uint64_t)b->n_units + (uint64_t)b->grid * kBatchWarpsPerBlock - 1) /
-                   ((uint64_t)b->grid * kBatchWarpsPerBlock));
-    }
-    b->args.masks = (uint32_t *)sl.mask_dev.p;
-    uint64_t launches = 0;
-    const size_t seg_at = (b->desc_bytes + 255) & ~size_t(255);
-    if ((rc = grow_host(sl.desc_host, seg_at + (size_t)n * sizeof(MaskSeg))) == SCR_OK) {
-        pack_plan(b, sl.desc_host.p);
-        memcpy((char *)sl.desc_host.p + seg_at, segs.data(), (size_t)n * sizeof(MaskSeg));
-        cudaError_t e = cudaMemcpyAsync(b->desc, sl.desc_host.p, b->desc_bytes, cudaMemcpyHostToDevice, s->st);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(sl.segs_dev.p, (char *)sl.desc_host.p + seg_at, (size_t)n * sizeof(MaskSeg),
-                                cudaMemcpyHostToDevice, s->st);
-        if (e == cudaSuccess)
-            e = cudaMemsetAsync(sl.mask_dev.p, 0, words * 4, s->st);
-        if (e == cudaSuccess)
-            e = cudaMemsetAsync(b->n_reserved, 0, 16, s->st);   // the kernel's unit counter
-        if (e == cudaSuccess && b->n_units > 0 && !b->groups.empty())
-            e = launch_batch(b->args, b->wpw, b->grid, s->st, &launches);
-        if (e == cudaSuccess)
-            e = launch_compact_segments((const uint32_t *)sl.mask_dev.p, (const MaskSeg *)sl.segs_dev.p, n, nchunks,
-                                        (uint64_t *)(dout + L.keys), (uint64_t *)(dout + L.counts), sl.scratch_dev.p,
-                                        s->st, &launches);
-        if (e == cudaSuccess)
-            e = cudaEventRecord(sl.done, s->st);
-        if (e != cudaSuccess)
-            rc = fail(SCR_ECUDA, "batched run: %s", cudaGetErrorString(e));
-    }
-    s->stats.launches += launches;
-    s->ctx->launches += launches;
-    {
-        std::lock_guard<std::mutex> lk(s->ctx->mu);
-        free_batch_on(s->ctx, b, s->st);   // stream-ordered after the run
-    }
-    return rc;
+    s->stats.launches += s->ctx->launches.load() - before;
+    CUDA_TRY(cudaEventRecord(f.ev, f.st));
+    return SCR_OK;
 }
 
-// Wait for a run launched by launch_batched and deliver every request's list.
-int finish_batched(scr_server *s, scr_server::Slot &sl, const std::vector<SrvRequest *> &scr) {
-    const int64_t t0 = now_ns();
-    CUDA_TRY(cudaEventSynchronize(sl.done));
-    const int64_t t1 = now_ns();
-    s->stats.wait_ns += t1 - t0;
-    const StageLayout L = stage_layout(scr);
-    const char *out = (const char *)sl.out_host.p;
-    const uint64_t *cnt = (const uint64_t *)(out + L.counts);
-    const uint64_t *keys = (const uint64_t *)(out + L.keys);
-    uint64_t word0 = 0;
-    for (size_t k = 0; k < scr.size(); ++k) {
-        SrvRequest *r = scr[k];
-        const uint64_t c = cnt[k], m = std::min(c, r->list_cap);
-        const uint64_t staged = std::min(m, L.cap[k]);
-        if (staged && r->list_host)
-            memcpy(r->list_host, keys + L.off[k], staged * 8);
-        if (m > staged) {   // a list longer than its staging slot: compact the mask again, in full
-            int rc;
-            if ((rc = grow_dev(s, s->list_dev, (size_t)m * 8, s->st)) || (rc = grow_dev(s, s->small_dev, 64, s->st)))
-                return rc;
-            if ((rc = compact_mask(s->ctx, (const uint32_t *)sl.mask_dev.p + word0, r->p.n_scales, r->img->H,
-                                   r->img->W, (uint64_t *)s->list_dev.p, m, (uint64_t *)s->small_dev.p,
-                                   (scr_stream)s->st)))
-                return rc;
-            CUDA_TRY(cudaMemcpyAsync(r->list_host, s->list_dev.p, m * 8, cudaMemcpyDeviceToHost, s->st));
-            CUDA_TRY(cudaStreamSynchronize(s->st));
-            s->list_dev_cap = s->list_dev.bytes / 8;
-        }
-        r->res.count = c;
-        r->res.status = c > r->list_cap ? SCR_EOVERFLOW : SCR_OK;
-        word0 += seg_words_of(r);
+// The screen's event has completed: hand the caller its list (a list longer
+// than the staging area is compacted again in full from the mask).
+int finish_screen(scr_server *s, Inflight &f) {
+    SrvRequest *r = f.r;
+    const uint64_t *stage = (const uint64_t *)f.stage;
+    const uint64_t count = stage[0], m = std::min(count, r->list_cap);
+    const uint64_t staged = std::min(m, f.staged_cap);
+    if (staged && r->list_host)
+        memcpy(r->list_host, stage + 1, staged * 8);
+    if (m > staged) {
+        int rc;
+        if ((rc = grow_dev(s, s->list_dev, (size_t)m * 8, f.st)) || (rc = grow_dev(s, s->small_dev, 64, f.st)))
+            return rc;
+        if ((rc = compact_mask(s->ctx, (const uint32_t *)f.mask, r->p.n_scales, r->img->H, r->img->W,
+                               (uint64_t *)s->list_dev.p, m, (uint64_t *)s->small_dev.p, (scr_stream)f.st)))
+            return rc;
+        CUDA_TRY(cudaMemcpyAsync(r->list_host, s->list_dev.p, m * 8, cudaMemcpyDeviceToHost, f.st));
+        CUDA_TRY(cudaStreamSynchronize(f.st));
+        s->list_dev_cap = s->list_dev.bytes / 8;
     }
-    s->stats.copy_ns += now_ns() - t1;
+    r->res.count = count;
+    r->res.status = count > r->list_cap ? SCR_EOVERFLOW : SCR_OK;
     return SCR_OK;
 }
 
@@ -679,6 +613,7 @@ int run_plain(scr_server *s, SrvRequest *r) {
     if ((rc = grow_dev(s, s->mask_dev, words * 4, s->st)) || (rc = grow_dev(s, s->small_dev, 64, s->st)) ||
         (rc = grow_host(s->small_host, 64)))
         return rc;
+    s->stats.mask_bytes = s->mask_dev.bytes;
     if (!s->list_dev_cap) {
         if ((rc = grow_dev(s, s->list_dev, (size_t)8 << 20, s->st)))
             return rc;
@@ -745,15 +680,6 @@ bool drained(const scr_server *s) {
     return s->pending.empty() && s->ready.empty() && s->jobs.empty() && s->jobs_in_flight == 0;
 }
 
-constexpr uint64_t kBatchMaskWords = 1ull << 31;   // 8 GiB of masks per batched run at most
-
-struct Flight {
-    std::vector<SrvRequest *> reqs;
-    int slot = 0;
-    int rc = SCR_OK;
-    int64_t t0 = 0;
-};
-
 // Release a finished batch's requests (takes the server lock).
 void retire(scr_server *s, const std::vector<SrvRequest *> &batch, int64_t t0) {
     std::lock_guard<std::mutex> lk(s->mu);
@@ -767,33 +693,84 @@ void retire(scr_server *s, const std::vector<SrvRequest *> &batch, int64_t t0) {
     s->cv_unpin.notify_all();
 }
 
-// The screener: batched mode keeps up to two runs in flight, so the next batch
-// is planned and enqueued while the device still works on the previous one;
-// plain mode serves each screen with its own launches and waits for it.
-void screener_main(scr_server *s) {
-    cudaSetDevice(s->ctx->device);
-    std::deque<Flight> flights;
-    const bool batched = s->cfg.mode == SCR_SERVE_BATCHED;
+// Release one screen of the batched path (server lock held).
+void retire_one(scr_server *s, SrvRequest *r) {
+    r->img->pins--;
+    r->img->last_use = ++s->lru_clock;
+    complete(s, r, r->res.status);
+}
+
+// Plain mode: serve each screen with its own launches and wait for it.
+void plain_loop(scr_server *s) {
     for (;;) {
         std::vector<SrvRequest *> batch;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            auto can_take = [&] { return !s->hold && (!s->pending.empty() || !s->ready.empty()); };
-            if (flights.empty())
+            s->cv_screen.wait(lk, [&] {
+                return (!s->hold && (!s->pending.empty() || !s->ready.empty())) || (s->stop && drained(s));
+            });
+            if (s->stop && drained(s))
+                return;
+            sort_pending(s);
+            const size_t lim = s->cfg.max_batch > 0 ? (size_t)s->cfg.max_batch : s->ready.size();
+            const size_t take = std::min(lim, s->ready.size());
+            batch.assign(s->ready.begin(), s->ready.begin() + take);
+            s->ready.erase(s->ready.begin(), s->ready.begin() + take);
+        }
+        if (batch.empty())
+            continue;
+        const int64_t t0 = now_ns();
+        const uint64_t seq = ++s->batch_seq;
+        for (SrvRequest *r : batch) {
+            r->res.start_ns = t0;
+            r->res.batch = seq;
+            r->res.batch_size = (int32_t)batch.size();
+        }
+        for (SrvRequest *r : batch) {
+            const int rc = run_plain(s, r);
+            if (rc)
+                r->res.status = rc;
+        }
+        retire(s, batch, t0);
+    }
+}
+
+// Batched mode (continuous batching): whenever screens are ready and there is
+// room in flight, take them all (at most max_batch) as one batch, order it
+// shortest first and enqueue every screen without waiting (small ones on the
+// priority stream, so they overtake large ones already on the device); retire
+// each screen as soon as its own event completes, while later batches are
+// being admitted.  Room in flight: max_inflight screens and kInflightMaskBytes
+// of masks (one screen larger than that runs alone).
+void batched_loop(scr_server *s) {
+    std::vector<Inflight> flying;
+    uint64_t flying_mask = 0;
+    for (;;) {
+        std::vector<SrvRequest *> batch;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            auto room = [&] { return flying.size() < max_inflight(s) && flying_mask < kInflightMaskBytes; };
+            auto can_take = [&] { return !s->hold && room() && (!s->pending.empty() || !s->ready.empty()); };
+            if (flying.empty()) {
                 s->cv_screen.wait(lk, [&] { return can_take() || (s->stop && drained(s)); });
-            else if (!can_take())   // poll the oldest run while waiting for arrivals
-                s->cv_screen.wait_for(lk, std::chrono::microseconds(20), can_take);
-            if (flights.empty() && s->stop && drained(s))
-                break;
-            if (flights.size() < 2 && can_take()) {
+                if (s->stop && drained(s))
+                    return;
+            } else if (!can_take()) {   // poll the screens in flight while waiting for arrivals
+                const int64_t w0 = now_ns();
+                s->cv_screen.wait_for(lk, std::chrono::microseconds(10), can_take);
+                s->stats.wait_ns += now_ns() - w0;
+                s->stats.screen_ns += now_ns() - w0;
+            }
+            if (can_take()) {
                 sort_pending(s);
                 const size_t lim = s->cfg.max_batch > 0 ? (size_t)s->cfg.max_batch : s->ready.size();
+                uint64_t m = flying_mask;
                 size_t take = 0;
-                uint64_t words = 0;   // the batched path's mask buffer stays below kBatchMaskWords
-                while (take < std::min(lim, s->ready.size())) {
-                    words += seg_words_of(s->ready[take]);
-                    if (take && batched && words > kBatchMaskWords)
+                while (take < std::min(lim, s->ready.size()) && flying.size() + take < max_inflight(s)) {
+                    const uint64_t b = mask_words_of(s->ready[take]) * 4;
+                    if ((take || !flying.empty()) && m + b > kInflightMaskBytes)
                         break;
+                    m += b;
                     ++take;
                 }
                 batch.assign(s->ready.begin(), s->ready.begin() + take);
@@ -803,49 +780,76 @@ void screener_main(scr_server *s) {
         if (!batch.empty()) {
             const int64_t t0 = now_ns();
             const uint64_t seq = ++s->batch_seq;
+            std::stable_sort(batch.begin(), batch.end(),
+                             [](const SrvRequest *a, const SrvRequest *b) { return cost_of(a) < cost_of(b); });
+            std::vector<SrvRequest *> failed;
             for (SrvRequest *r : batch) {
                 r->res.start_ns = t0;
                 r->res.batch = seq;
                 r->res.batch_size = (int32_t)batch.size();
+                Inflight f;
+                f.r = r;
+                const int rc = enqueue_screen(s, f);
+                if (rc) {
+                    // nothing of this screen is left on the device past this point
+                    if (f.st)
+                        cudaStreamSynchronize(f.st);
+                    release_inflight(s, f);
+                    r->res.status = rc;
+                    failed.push_back(r);
+                    continue;
+                }
+                flying_mask += f.mask_bytes;
+                flying.push_back(f);
             }
-            if (batched) {
-                Flight f;
-                f.reqs = std::move(batch);
-                f.t0 = t0;
-                f.slot = s->slots[0].busy ? 1 : 0;
-                s->slots[f.slot].busy = true;
-                f.rc = launch_batched(s, s->slots[f.slot], f.reqs);
-                s->stats.plan_ns += now_ns() - t0;
-                flights.push_back(std::move(f));
+            s->stats.batches++;
+            s->stats.plan_ns += now_ns() - t0;
+            s->stats.screen_ns += now_ns() - t0;
+            if (!failed.empty()) {
+                std::lock_guard<std::mutex> lk(s->mu);
+                for (SrvRequest *r : failed)
+                    retire_one(s, r);
+                s->cv_unpin.notify_all();
+            }
+        }
+        // retire every screen whose event has completed (out of order across the lanes)
+        std::vector<SrvRequest *> done;
+        const int64_t c0 = now_ns();
+        for (size_t k = 0; k < flying.size();) {
+            Inflight &f = flying[k];
+            const cudaError_t q = cudaEventQuery(f.ev);
+            if (q == cudaErrorNotReady) {
+                cudaGetLastError();
+                ++k;
                 continue;
             }
-            for (SrvRequest *r : batch) {
-                const int rc = run_plain(s, r);
-                if (rc)
-                    r->res.status = rc;
-            }
-            retire(s, batch, t0);
-            continue;
-        }
-        if (flights.empty())
-            continue;
-        Flight &f = flights.front();
-        // with room for another run, keep polling (arrivals get planned and
-        // enqueued behind it); with two in flight, wait for the oldest
-        if (f.rc == SCR_OK && flights.size() < 2 && cudaEventQuery(s->slots[f.slot].done) == cudaErrorNotReady) {
+            int rc = q == cudaSuccess ? finish_screen(s, f) : fail(SCR_ECUDA, "screen: %s", cudaGetErrorString(q));
+            if (rc)
+                f.r->res.status = rc;
             cudaGetLastError();
-            continue;
+            flying_mask -= f.mask_bytes;
+            release_inflight(s, f);
+            done.push_back(f.r);
+            flying[k] = flying.back();
+            flying.pop_back();
         }
-        cudaGetLastError();
-        if (f.rc == SCR_OK)
-            f.rc = finish_batched(s, s->slots[f.slot], f.reqs);
-        if (f.rc)
-            for (SrvRequest *r : f.reqs)
-                r->res.status = f.rc;
-        s->slots[f.slot].busy = false;
-        retire(s, f.reqs, f.t0);
-        flights.pop_front();
+        if (!done.empty()) {
+            s->stats.copy_ns += now_ns() - c0;
+            s->stats.screen_ns += now_ns() - c0;
+            std::lock_guard<std::mutex> lk(s->mu);
+            for (SrvRequest *r : done)
+                retire_one(s, r);
+            s->cv_unpin.notify_all();
+        }
     }
+}
+
+void screener_main(scr_server *s) {
+    cudaSetDevice(s->ctx->device);
+    if (s->cfg.mode == SCR_SERVE_BATCHED)
+        batched_loop(s);
+    else
+        plain_loop(s);
 }
 
 int submit(scr_server *s, SrvRequest *r, uint64_t *request_id) {
@@ -934,10 +938,9 @@ int server_create(scr_ctx *c, const scr_server_config *cfg, scr_server **out) {
         return fail(SCR_EINVAL, "table widths must be 32 or 64 bits");
     if (cfg->mode != SCR_SERVE_BATCHED && cfg->mode != SCR_SERVE_PLAIN)
         return fail(SCR_EINVAL, "unknown serving mode %d", cfg->mode);
-    if (cfg->words_per_warp && cfg->words_per_warp != 2 && cfg->words_per_warp != 4 && cfg->words_per_warp != 8)
-        return fail(SCR_EINVAL, "words_per_warp must be 0, 2, 4 or 8");
-    if (cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 16 || cfg->max_batch < 0)
-        return fail(SCR_EINVAL, "blocks_per_sm must be in [0, 16] and max_batch >= 0");
+    if (cfg->small_log2 < 0 || cfg->small_log2 > 40 || cfg->max_inflight < 0 || cfg->max_inflight > 4096 ||
+        cfg->max_batch < 0)
+        return fail(SCR_EINVAL, "small_log2 must be in [0, 40], max_inflight in [0, 4096], max_batch >= 0");
     *out = nullptr;
     DeviceGuard dg(c->device);
     auto *s = new (std::nothrow) scr_server();
@@ -946,43 +949,34 @@ int server_create(scr_ctx *c, const scr_server_config *cfg, scr_server **out) {
     s->ctx = c;
     s->cfg = *cfg;
     s->hold = cfg->start_held != 0;
-    // table builds go first when they and screening kernels wait for the same SMs
+    // table builds go first when they and screening kernels wait for the same
+    // SMs; small screens come next, large screens last
     int prio_lo = 0, prio_hi = 0;
     cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    const int prio_small = prio_hi < prio_lo ? prio_hi + 1 : prio_hi;
     cudaError_t e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithPriority(&s->st_small, cudaStreamNonBlocking, prio_small);
     for (auto &bd : s->builders)
         if (e == cudaSuccess)
             e = cudaStreamCreateWithPriority(&bd.st, cudaStreamNonBlocking, prio_hi);
-    if (e != cudaSuccess) {
-        if (s->st)
-            cudaStreamDestroy(s->st);
+    auto drop_streams = [&] {
+        for (cudaStream_t q : {s->st, s->st_small})
+            if (q)
+                cudaStreamDestroy(q);
         for (auto &bd : s->builders)
             if (bd.st)
                 cudaStreamDestroy(bd.st);
+    };
+    if (e != cudaSuccess) {
+        drop_streams();
         delete s;
         return fail(SCR_ECUDA, "stream creation: %s", cudaGetErrorString(e));
-    }
-    for (auto &sl : s->slots)
-        if (e == cudaSuccess)
-            e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
-    if (e != cudaSuccess) {
-        for (auto &sl : s->slots)
-            if (sl.done)
-                cudaEventDestroy(sl.done);
-        cudaStreamDestroy(s->st);
-        for (auto &bd : s->builders)
-            cudaStreamDestroy(bd.st);
-        delete s;
-        return fail(SCR_ECUDA, "event creation: %s", cudaGetErrorString(e));
     }
     if (cfg->table_budget_bytes) {
         const size_t want = (size_t)cfg->table_budget_bytes + (size_t)(cfg->table_budget_bytes >> 4);
         if ((rc = dev_alloc(c, (want + kArenaAlign - 1) & ~(kArenaAlign - 1), s->st, &s->arena))) {
-            cudaStreamDestroy(s->st);
-            for (auto &bd : s->builders)
-                cudaStreamDestroy(bd.st);
-            for (auto &sl : s->slots)
-                cudaEventDestroy(sl.done);
+            drop_streams();
             delete s;
             return rc;
         }
@@ -1223,6 +1217,7 @@ void server_destroy(scr_server *s) {
     scr_ctx *c = s->ctx;
     DeviceGuard dg(c->device);
     cudaStreamSynchronize(s->st);
+    cudaStreamSynchronize(s->st_small);
     for (auto &bd : s->builders)
         cudaStreamSynchronize(bd.st);
     std::vector<std::pair<size_t, void *>> blocks;
@@ -1243,9 +1238,6 @@ void server_destroy(scr_server *s) {
         delete kv.second;
     for (DevBuf *b : {&s->mask_dev, &s->list_dev, &s->small_dev})
         dev_free(c, b->p, b->bytes, s->st);
-    for (auto &sl : s->slots)
-        for (DevBuf *b : {&sl.mask_dev, &sl.segs_dev, &sl.scratch_dev})
-            dev_free(c, b->p, b->bytes, s->st);
     for (auto &bd : s->builders) {
         dev_free(c, bd.img.p, bd.img.bytes, bd.st);
         dev_free(c, bd.scratch.p, bd.scratch.bytes, bd.st);
@@ -1256,13 +1248,12 @@ void server_destroy(scr_server *s) {
     for (DevBuf *b : {&s->keys_host, &s->small_host})
         if (b->p)
             cudaFreeHost(b->p);
-    for (auto &sl : s->slots) {
-        for (DevBuf *b : {&sl.desc_host, &sl.out_host})
-            if (b->p)
-                cudaFreeHost(b->p);
-        cudaEventDestroy(sl.done);
-    }
+    for (auto &kv : s->all_stage)
+        cudaFreeHost(kv.first);
+    for (cudaEvent_t ev : s->free_events)
+        cudaEventDestroy(ev);
     cudaStreamDestroy(s->st);
+    cudaStreamDestroy(s->st_small);
     for (auto &bd : s->builders) {
         cudaStreamDestroy(bd.st);
         for (cudaEvent_t e : bd.ev)

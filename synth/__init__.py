@@ -318,7 +318,8 @@ def batch_workload(seed: int = BASE_SEED + 3, n_images: int = 64, n_templates: i
                    area_range=(640 * 480, 4096 * 3072), r_range=(8, 64), scale_range=(0.5, 2.0),
                    max_scales: int = 16, plants_per_image: int = 4, all_pairs: bool = True) -> BatchWorkload:
     """Configuration 4: images with log-uniform area (4:3), templates with r ~ U{8..64}
-    and 1..16 geometric scales in [0.5, 2]; 4 planted copies per image."""
+    and 1..16 geometric scales in [0.5, 2]; 4 planted copies per image, placed
+    so that no two copies overlap (a copy that fits nowhere is left out)."""
     rng = rng_for(seed)
     templates = _batch_templates(rng, n_templates, r_range, scale_range, max_scales)
     images, plants = [], []
@@ -327,7 +328,7 @@ def batch_workload(seed: int = BASE_SEED + 3, n_images: int = 64, n_templates: i
         H = max(8, int(round(math.sqrt(area * 3.0 / 4.0))))
         W = max(8, int(round(H * 4.0 / 3.0)))
         fld = blob_field(rng, H, W)
-        pl = []
+        pl, placed = [], []
         for _p in range(plants_per_image):
             t = int(rng.integers(0, n_templates))
             ts = templates[t]
@@ -335,8 +336,17 @@ def batch_workload(seed: int = BASE_SEED + 3, n_images: int = 64, n_templates: i
             margin = int(math.ceil(s * (2 * ts.r + 1))) + 4
             if H <= 2 * margin or W <= 2 * margin:
                 continue
-            y = int(rng.integers(margin, H - margin))
-            x = int(rng.integers(margin, W - margin))
+            # copies do not overlap: a later paste would overwrite part of an
+            # earlier copy (reach = half-diagonal of the pasted square)
+            reach = s * (2 * ts.r + 1) * math.sqrt(0.5) + 2
+            for _try in range(64):
+                y = int(rng.integers(margin, H - margin))
+                x = int(rng.integers(margin, W - margin))
+                if all(math.hypot(y - py, x - px) > reach + pr for (py, px, pr) in placed):
+                    break
+            else:
+                continue
+            placed.append((y, x, reach))
             paste(fld, ts.template, y + 0.5, x + 0.5, float(rng.uniform(0, 2 * math.pi)), s)
             pl.append((t, y, x, s))
         images.append(quantize_with_noise(fld, rng))

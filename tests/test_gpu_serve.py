@@ -152,7 +152,9 @@ def test_lru_eviction_and_rebuild(ctx, work):
 
 def test_forget_overflow_and_budget_errors(ctx, work):
     bw, tmpls, params, want = work
-    s = scr.server_create(ctx, start_held=True, table_budget_bytes=scr_table_bytes(bw.images[0].shape) + 4096)
+    # room for the tables of image 0 or image 1, one at a time
+    budget = max(scr_table_bytes(bw.images[0].shape), scr_table_bytes(bw.images[1].shape)) + 4096
+    s = scr.server_create(ctx, start_held=True, table_budget_bytes=budget)
     try:
         i0, _ = scr.server_upload(s, bw.images[0])
         small = np.zeros(3, np.uint64)
