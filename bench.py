@@ -1201,6 +1201,20 @@ def run_serve(args):
     print(json.dumps(serve_leg(args, rates, check=not args.no_check, seed=args.seed)), flush=True)
 
 
+def run_l1probe(args):
+    """Build and run the load-throughput probe (csrc/probe_l1.cu) that fixes the
+    screening kernel's on-chip ceiling; prints its JSON line."""
+    pkg = os.path.join(ROOT, "paper_1707_05647_gb300")
+    src = os.path.join(pkg, "csrc", "probe_l1.cu")
+    exe = os.path.join(pkg, "_build", "probe_l1")
+    os.makedirs(os.path.dirname(exe), exist_ok=True)
+    nvcc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")
+    subprocess.check_call([nvcc if os.path.exists(nvcc) else "nvcc", "-gencode", "arch=compute_103a,code=sm_103a",
+                           "-O3", "-o", exe, src])
+    out = json.loads(subprocess.check_output([exe], text=True).strip().splitlines()[-1])
+    print(json.dumps({"metric": "L1 data-pipe throughput per load shape", **out}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1217,13 +1231,16 @@ def main():
     ap.add_argument("--no-secondary", action="store_true", help="skip the 4096x4096 run after config 3")
     ap.add_argument("--no-check", action="store_true", help="skip the oracle checks of the batched and serve legs")
     ap.add_argument("--seed", type=int, default=None, help="serve workload seed (default 1004)")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "serve", "joint"])
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "serve", "joint", "l1probe"])
     ap.add_argument("--duration", type=float, default=2.0, help="seconds of arrivals (serve workload)")
     ap.add_argument("--rates", default="2000,8000,16000",
                     help="arrival rates (req/s) of the serve workload; the first is the headline")
     ap.add_argument("--images", type=int, default=64)
     ap.add_argument("--templates", type=int, default=256)
     args = ap.parse_args()
+    if args.workload == "l1probe":
+        run_l1probe(args)
+        return
     if args.workload == "serve":
         run_serve(args)
         return
