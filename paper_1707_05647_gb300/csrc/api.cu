@@ -1206,10 +1206,12 @@ int screen_host(scr_ctx *c, const uint8_t *img_host, int32_t H, int32_t W, int64
     if ((rc = img.take((size_t)dpitch * H)))
         return rc;
     CUDA_TRY(cudaMemcpy2DAsync(img.p, dpitch, img_host, pitch, W, H, cudaMemcpyHostToDevice, st));
-    // A pinned, mapped list buffer (cudaHostAlloc / cudaMallocHost memory) is
-    // written by the compaction directly, with the count going to the
-    // context's pinned slot: one synchronisation instead of a count read, a
-    // list copy and two.
+    // A pinned, mapped list buffer (cudaHostAlloc / cudaMallocHost memory)
+    // gets the keys and the count (to the context's pinned slot) from one
+    // copy kernel after the compaction into device memory: one synchronisation
+    // instead of a count read, a list copy and two.  (The compaction writing
+    // the keys into host memory itself is slower for long lists: 0.45 ms more
+    // for 2.2 M keys, measured.)
     uint64_t *list_map = nullptr;
     if (list_cap && c->pinned_dev) {
         cudaPointerAttributes pa;
@@ -1223,7 +1225,7 @@ int screen_host(scr_ctx *c, const uint8_t *img_host, int32_t H, int32_t W, int64
     }
     const uint64_t words = (uint64_t)p->n_scales * H * ((W + 31) / 32);
     // an error from here on returns only after the copy has stopped reading img_host
-    if ((rc = mask.take(words * 4)) || (!list_map && (rc = list.take(std::max<uint64_t>(list_cap, 1) * 8 + 64)))) {
+    if ((rc = mask.take(words * 4)) || (rc = list.take(std::max<uint64_t>(list_cap, 1) * 8 + 64))) {
         cudaStreamSynchronize(st);
         return rc;
     }
@@ -1232,19 +1234,24 @@ int screen_host(scr_ctx *c, const uint8_t *img_host, int32_t H, int32_t W, int64
         cudaStreamSynchronize(st);
         return rc;
     }
+    uint64_t *cnt_dev = (uint64_t *)((char *)list.p + std::max<uint64_t>(list_cap, 1) * 8);
     if (list_map) {
         std::lock_guard<std::mutex> lk(c->mu);   // the pinned count slot
-        rc = screen_positions_async(c, t, tm, p, (uint32_t *)mask.p, words, list_map, list_cap, c->pinned_dev,
+        rc = screen_positions_async(c, t, tm, p, (uint32_t *)mask.p, words, (uint64_t *)list.p, list_cap, cnt_dev,
                                     stream);
         if (!rc) {
-            const cudaError_t e = cudaStreamSynchronize(st);
+            uint64_t n = 0;
+            cudaError_t e = launch_copy_keys((const uint64_t *)list.p, cnt_dev, list_cap, list_map, c->pinned_dev,
+                                             st, &n);
+            c->launches += n;
+            if (e == cudaSuccess)
+                e = cudaStreamSynchronize(st);
             if (e == cudaSuccess)
                 *n_survivors = c->pinned[0];
             else
                 rc = fail(SCR_ECUDA, "screen_host: %s", cudaGetErrorString(e));
         }
     } else {
-        uint64_t *cnt_dev = (uint64_t *)((char *)list.p + std::max<uint64_t>(list_cap, 1) * 8);
         rc = screen_positions_async(c, t, tm, p, (uint32_t *)mask.p, words, list_cap ? (uint64_t *)list.p : nullptr,
                                     list_cap, cnt_dev, stream);
         if (!rc) {

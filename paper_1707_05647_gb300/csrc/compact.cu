@@ -178,7 +178,27 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const uint32_t *mask, uint
     }
 }
 
+// Copy a compacted list (device) and its count to host memory the device can
+// address (pinned, mapped): min(count, cap) keys with coalesced stores, and the
+// count.  The host then needs one synchronisation and no copy of its own.
+__global__ void __launch_bounds__(kThreads) k_copy_keys(const uint64_t *src, const uint64_t *count, uint64_t cap,
+                                                          uint64_t *dst, uint64_t *count_out) {
+    pdl_begin();
+    const uint64_t c = *count, n = c < cap ? c : cap;
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        *count_out = c;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
 }  // namespace
+
+cudaError_t launch_copy_keys(const uint64_t *src, const uint64_t *count, uint64_t cap, uint64_t *dst,
+                             uint64_t *count_out, cudaStream_t st, uint64_t *launches) {
+    if (launches)
+        *launches += 1;
+    return launch_pdl(k_copy_keys, dim3(152 * 4), dim3(kThreads), st, src, count, cap, dst, count_out);
+}
 
 size_t compact_scratch_bytes(uint64_t total_words) {
     const uint64_t nchunks = (total_words + kChunk - 1) / kChunk;

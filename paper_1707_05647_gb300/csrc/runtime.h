@@ -192,3 +192,10 @@ void batch_set_shape(scr_batch *b, int wpw, int blocks_per_sm);
 void destroy_servers(scr_ctx *c);
 
 }  // namespace scr_rt
+
+namespace scr {
+// Copy min(*count, cap) keys of a device list to dst and *count to count_out,
+// both host memory the device can address (one kernel; compact.cu).
+cudaError_t launch_copy_keys(const uint64_t *src, const uint64_t *count, uint64_t cap, uint64_t *dst,
+                             uint64_t *count_out, cudaStream_t st, uint64_t *launches);
+}  // namespace scr
