@@ -658,13 +658,20 @@ __device__ __forceinline__ void store1(uint32_t *lo, uint32_t *hi, int64_t word,
 // an edge moves one column per row, so after the band's B rows it has crossed
 // at most B = HALO columns and never reaches the core.  At the right end of the
 // image D1 is constant in the column, so there the edge value is exact.
+//
+// Programmatic dependent launch: the writer waits for the prefix kernel at its
+// start like every kernel, but lets the next kernel (the screening kernel)
+// launch only when its own rows are written.  Released at the start, the
+// screening kernel's 256-thread blocks took the SM slots freed during the
+// writer's last wave and waited there, and the build-then-screen sequence took
+// 3.87 ms instead of 3.35 on the 8192x8192 workload (measured).
 template <typename TS, typename TQ>
 __global__ void __launch_bounds__(32) k_tab_write(const WriteArgs a) {
     // planes of a row in obuf: L1 (lo[, hi]), L2 (lo[, hi]), T1 (lo[, hi]), T2 (lo[, hi])
     constexpr int HS = sizeof(TS) == 8 ? 1 : 0, HQ = sizeof(TQ) == 8 ? 1 : 0;
     constexpr int PL1 = 0, PL2 = PL1 + 1 + HS, PT1 = PL2 + 1 + HQ, PT2 = PT1 + 1 + HS;
     constexpr int NPL = PT2 + 1 + HQ;
-    pdl_begin();
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const Geometry &g = a.g;
     const int j = blockIdx.x, i = blockIdx.y, lane = threadIdx.x;
     const int r0 = i * B;
@@ -860,6 +867,7 @@ __global__ void __launch_bounds__(32) k_tab_write(const WriteArgs a) {
     if (lane == 0)
         asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     __syncwarp();
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 template <typename TS, typename TQ>
