@@ -34,7 +34,7 @@
 namespace scr {
 namespace {
 
-constexpr int kWarpsPerBlock = 8;
+constexpr int kWarpsPerBlock = 16;   // 16 warps = 4096 x of one row per block
 
 __device__ __forceinline__ uint32_t ld(const uint32_t *p) { return __ldg(p); }
 
@@ -71,11 +71,14 @@ constexpr int WPW = 8;
 // PW: the Prewitt gradient test of the star's square (Sec. 3, Eq. S_y with
 // the moment tables of Eq. T_x; magnitude of Sec. 4) runs after the others,
 // compared squared in 128 bits.  The default kernel has no Prewitt code.
-// 64 registers (4 blocks per SM) let the batched star-sum reads stay in
-// flight together: measured 182 us against 189 us at 48 registers (5 blocks)
-// and 192 us at 80 (3 blocks) on the 4096^2 workload.
+// 64 registers let the batched star-sum reads stay in flight together:
+// measured 182 us against 189 us at 48 registers and 192 us at 80 on the
+// 4096^2 workload.  Blocks of 16 warps (2 per SM) cover 4096 x of a row, so
+// the left and right corner segments of more warps meet in one SM's L1:
+// 2.64 ms against 2.71 ms with 8-warp blocks on the 8192^2 workload (4096^2:
+// 0.184 against 0.182 ms).
 template <bool PW>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock, 4)
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, 2)
 k_screen(const __grid_constant__ ScreenArgs a) {
     pdl_begin();
     const int lane = threadIdx.x & 31;
