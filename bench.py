@@ -361,7 +361,7 @@ def run_reference(args):
         oracle_baseline(wl, rows)
     secs = []
     for _ in range(args.steps):
-        v, sample, cores, dt = oracle_baseline(wl, rows)
+        _v, sample, cores, dt = oracle_baseline(wl, rows)
         secs.append(dt)
     H = rows or wl.image.shape[0]
     value = len(secs) * candidates(H, wl.image.shape[1], wl.radii) / sum(secs)
@@ -980,6 +980,11 @@ def serve_leg(args, rates, check=True, n_sample=12, seed=None):
                                                              w.tol.grad_rel, w.tol.grad_abs)
     cap = 1 << 18
     n_bufs = 1024   # list buffers in flight (2 GiB of host memory)
+    # allocated once and every page touched before any replay: first-touch page
+    # faults on fresh buffers stalled the whole process for up to ~0.2 s
+    list_bufs = [np.empty(cap, np.uint64) for _ in range(n_bufs)]
+    for b_ in list_bufs:
+        b_.fill(0)
 
     def candidates(img_shape, radii):
         H, W = img_shape
@@ -1006,8 +1011,8 @@ def serve_leg(args, rates, check=True, n_sample=12, seed=None):
             assert r["status"] == scr.SCR_OK, r
         warm_stats = scr.server_stats(s)
         bufs = queue.Queue()
-        for _ in range(n_bufs):
-            bufs.put(np.zeros(cap, np.uint64))
+        for b_ in list_bufs:
+            bufs.put(b_)
         results = {}
         lock = threading.Lock()
         meta, early = {}, {}          # request id -> (event index, buffer); results seen before their id

@@ -109,3 +109,23 @@ def test_traffic_record_follows_kernel_code_not_comments(tmp_path):
     rec.write_text("dram_bytes_per_launch: 123\nkernel_code_sha256: 00\n")
     assert bench.recorded_traffic(8192, 8192, root=str(tmp_path)) is None
     assert bench.recorded_traffic(8192, 8192, root=str(tmp_path / "none")) is None
+
+
+def test_clock_samples_are_kept_only_inside_the_window():
+    import datetime
+    import tempfile
+    c = bench.Clocks(0)
+    c.f = tempfile.TemporaryFile(mode="w+")
+    t0 = datetime.datetime(2026, 1, 2, 3, 4, 5)
+
+    def line(dt_ms, mhz, slowdown="Not Active"):
+        ts = (t0 + datetime.timedelta(milliseconds=dt_ms)).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        return f"{ts}, {mhz}, 2070, 500.0, 0x0, {slowdown}, Not Active, Not Active, Not Active\n"
+
+    c.f.write(line(0, 1000) + line(100, 2070) + line(150, 2070, "Active") + line(400, 900) + "garbage\n")
+    base = t0.timestamp()
+    s = c.summary(base + 0.05, base + 0.2, "test window")
+    assert s["samples"] == 2 and s["sm_mhz"] == 2070.0 and s["reasons"] == ["hw_slowdown"]
+    assert c.count_between(base + 0.05) == 3
+    empty = c.summary(base + 1.0, base + 2.0, "later")
+    assert empty["samples"] == 0 and empty["sm_mhz"] is None
