@@ -156,23 +156,28 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const uint32_t *mask, uint
         __syncthreads();
         if (c == 0 || pos >= cap)
             continue;
+        // (scale, row, word) of the thread's first word by division, then by
+        // stepping through its consecutive words
+        uint64_t sc = first / planeWords;
+        const uint32_t rem = (uint32_t)(first - sc * planeWords);
+        uint32_t y = rem / (uint32_t)rowWords, xw = rem - y * (uint32_t)rowWords;
 #pragma unroll
         for (int k = 0; k < kWordsPerThread; ++k) {
             uint32_t bits = w[k];
-            if (!bits)
-                continue;
-            const uint64_t wi = first + k;
-            const uint64_t s = wi / planeWords;
-            const uint64_t rem = wi - s * planeWords;
-            const uint64_t y = rem / rowWords;
-            const uint64_t x0 = (rem - y * rowWords) * 32;
-            const uint64_t keyb = (s << 48) | (y << 24);
+            const uint64_t keyb = (sc << 48) | ((uint64_t)y << 24) | ((uint64_t)xw * 32);
             while (bits) {
                 const int bit = __ffs(bits) - 1;
                 bits &= bits - 1;
                 if (pos < cap)
-                    list[pos] = keyb | (x0 + bit);
+                    list[pos] = keyb + bit;
                 ++pos;
+            }
+            if (++xw == (uint32_t)rowWords) {
+                xw = 0;
+                if (++y == (uint32_t)H) {
+                    y = 0;
+                    ++sc;
+                }
             }
         }
     }
