@@ -506,6 +506,49 @@ int screen_host(scr_ctx *ctx, const uint8_t *img_host, int32_t H, int32_t W, int
                 uint64_t *list_host, uint64_t list_cap, uint64_t *n_survivors,
                 scr_stream stream);
 
+/* ---- a stream of same-sized host images (video frames) -------------------- */
+
+/* The whole path of screen_host for a sequence of H x W host images screened
+ * against one template with one parameter set, as in the paper's tracking use
+ * (Sec. 6: every frame of a video screened for the target): Algorithm 1 on each
+ * frame, with the copy of frame k+1 to the device overlapping the tables,
+ * screen and compaction of frame k.
+ *
+ * frames_create reserves, once, every device buffer the path needs (depth image
+ * slots of H x W bytes, one set of four tables, the table-build and compaction
+ * scratch, one S x H x ceil(W/32) mask, a list of list_cap keys), charged to
+ * the context's budget, and two streams of its own (copies; compute).  depth
+ * (1..4) is the number of frames that may be in flight: 2 overlaps one copy
+ * with one computation.  The template and the parameters are copied; the
+ * template handle must outlive the pipeline.  SCR_EINVAL for bad geometry,
+ * widths or parameters, SCR_EBUDGET / SCR_ENOMEM when the buffers do not fit.
+ *
+ * frames_submit queues one frame: img_host (H rows of W bytes, pitch bytes
+ * apart; pinned memory makes the copy asynchronous) and list_host, room for
+ * list_cap keys (s << 48) | (y << 24) | x in pinned host memory the device can
+ * address (cudaHostAlloc / cudaMallocHost), into which the device writes the
+ * frame's ascending survivor keys.  Both buffers belong to the pipeline until
+ * frames_wait returns for that frame: the caller must neither change img_host
+ * nor read list_host before then.  Returns the frame's ticket (0, 1, 2, ... in
+ * submission order).  SCR_EINVAL when depth frames are already in flight (wait
+ * for the oldest first) or list_host is not device-addressable pinned memory
+ * (list_cap > 0); list_host may be NULL when list_cap is 0 (count only).
+ *
+ * frames_wait blocks until the frame with the given ticket is done and returns
+ * its survivor count; tickets are waited for in submission order (SCR_EINVAL
+ * otherwise).  SCR_EOVERFLOW when the count exceeds list_cap (the first
+ * list_cap keys are in list_host, *n_survivors is the true count).
+ *
+ * frames_destroy waits for every frame in flight and frees the pipeline; so
+ * does screen_shutdown for pipelines still alive.  One pipeline may be used
+ * from several host threads (calls are serialised on it). */
+typedef struct scr_frames scr_frames;
+int frames_create(scr_ctx *ctx, int32_t H, int32_t W, int32_t sum_bits, int32_t sq_bits, const scr_tmpl *tm,
+                  const scr_params *p, uint64_t list_cap, int32_t depth, scr_frames **out);
+int frames_submit(scr_frames *f, const uint8_t *img_host, int64_t pitch, uint64_t *list_host, int64_t *ticket);
+int frames_wait(scr_frames *f, int64_t ticket, uint64_t *n_survivors);
+void frames_destroy(scr_frames *f);
+
 #ifdef __cplusplus
 }
 #endif

@@ -128,6 +128,10 @@ def load(build_if_missing: bool = True):
         "screen_positions_async": ([vp, vp, vp, ctypes.POINTER(_Params), vp, u64, vp, u64, vp, vp], ctypes.c_int),
         "screen_host": ([vp, vp, i32, i32, i64, i32, i32, vp, ctypes.POINTER(_Params), vp, u64,
                          ctypes.POINTER(u64), vp], ctypes.c_int),
+        "frames_create": ([vp, i32, i32, i32, i32, vp, ctypes.POINTER(_Params), u64, i32, pp], ctypes.c_int),
+        "frames_submit": ([vp, vp, i64, vp, ctypes.POINTER(i64)], ctypes.c_int),
+        "frames_wait": ([vp, i64, ctypes.POINTER(u64)], ctypes.c_int),
+        "frames_destroy": ([vp], None),
         "screen_batch_create": ([vp, vp, i32, vp, ctypes.POINTER(_Params), i32, ctypes.POINTER(_Pair), i32,
                                  vp, vp, vp, vp, u64, vp, ctypes.POINTER(_Tuning), vp, pp], ctypes.c_int),
         "screen_batch_run": ([vp, vp], ctypes.c_int),
@@ -162,7 +166,8 @@ def exported_symbols():
             "template_release", "screen_bounds", "screen_features", "screen_joint", "compact_mask",
             "compact_mask_noalloc",
             "compact_mask_noalloc_error", "screen_positions",
-            "screen_positions_async", "screen_host", "screen_batch_create", "screen_batch_run",
+            "screen_positions_async", "screen_host", "frames_create", "frames_submit", "frames_wait",
+            "frames_destroy", "screen_batch_create", "screen_batch_run",
             "screen_batch_info", "screen_batch_release", "server_clock_ns", "server_create", "server_upload",
             "server_screen", "server_evict", "server_forget", "server_wait", "server_next", "server_hold", "server_resident",
             "server_stats", "server_destroy", "server_lru_victims"]
@@ -374,6 +379,36 @@ def screen_host(ctx, img: np.ndarray, sum_bits: int, sq_bits: int, tm, params: P
                                    ctypes.byref(params.c), _ptr(lst), 0 if lst is None else lst.size,
                                    ctypes.byref(n), _stream(stream)), allow=(SCR_EOVERFLOW,))
     return int(n.value), rc == SCR_EOVERFLOW
+
+
+# ---- a stream of same-sized host images -------------------------------------
+
+def frames_create(ctx, H: int, W: int, sum_bits: int, sq_bits: int, tm, params: Params, list_cap: int,
+                  depth: int = 2):
+    out = ctypes.c_void_p()
+    _check(load().frames_create(ctx, H, W, sum_bits, sq_bits, tm, ctypes.byref(params.c), list_cap, depth,
+                                ctypes.byref(out)))
+    return out
+
+
+def frames_submit(f, img, lst) -> int:
+    """img: H x W uint8 host array (pinned for an asynchronous copy); lst:
+    pinned host array of at least list_cap uint64/int64 keys, or None when
+    list_cap is 0.  Returns the frame's ticket."""
+    t = ctypes.c_int64()
+    pitch = img.strides[0] if isinstance(img, np.ndarray) else img.stride(0)
+    _check(load().frames_submit(f, _ptr(img), pitch, _ptr(lst), ctypes.byref(t)))
+    return int(t.value)
+
+
+def frames_wait(f, ticket: int) -> tuple[int, bool]:
+    n = ctypes.c_uint64()
+    rc = _check(load().frames_wait(f, ticket, ctypes.byref(n)), allow=(SCR_EOVERFLOW,))
+    return int(n.value), rc == SCR_EOVERFLOW
+
+
+def frames_destroy(f) -> None:
+    load().frames_destroy(f)
 
 
 # ---- batched screening ------------------------------------------------------

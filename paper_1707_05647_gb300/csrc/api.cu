@@ -588,6 +588,7 @@ void screen_shutdown(scr_ctx *c) {
         return;
     DeviceGuard dg(c->device);
     destroy_servers(c);
+    destroy_frames(c);
     cudaDeviceSynchronize();
     {
         std::lock_guard<std::mutex> lk(c->mu);
@@ -1278,6 +1279,278 @@ int screen_host(scr_ctx *c, const uint8_t *img_host, int32_t H, int32_t W, int64
         return fail(SCR_EOVERFLOW, "%llu survivors exceed list capacity %llu", (unsigned long long)*n_survivors,
                     (unsigned long long)list_cap);
     return rc;
+}
+
+// ---------------------------------------------------------------------------
+// A stream of same-sized host images (frames_*)
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+static constexpr int kMaxFrameDepth = 4;
+
+// Every buffer is reserved once at creation; per frame, the copy stream moves
+// the image into its slot while the compute stream builds the tables, screens
+// and compacts the previous frame, and the output stream moves the frame
+// before that one's keys to the host.  Events order them: the compute of a
+// frame waits for its image; the copy into a slot waits until the table build
+// of the frame that used the slot before has read it; the key copy of a frame
+// waits for its compaction, and the next compaction into the same slot's list
+// waits for that key copy.
+struct scr_frames {
+    scr_ctx *c = nullptr;
+    int H = 0, W = 0, depth = 0;
+    int64_t dpitch = 0;
+    uint64_t list_cap = 0, mask_words = 0;
+    ScreenArgs args;                       // fixed: same tables, template and bounds every frame
+    scr_tables tabs;                       // laid out in tab_base (not a context-owned handle)
+    cudaStream_t st_copy = nullptr, st_comp = nullptr, st_out = nullptr;
+    void *img[kMaxFrameDepth] = {};
+    void *list_dev[kMaxFrameDepth] = {};   // per slot: keys, then the count
+    void *tab_base = nullptr, *build_scratch = nullptr, *compact_scratch = nullptr;
+    size_t img_bytes = 0, tab_bytes = 0, build_bytes = 0, compact_bytes = 0, list_bytes = 0, mask_bytes = 0;
+    uint32_t *mask = nullptr;
+    uint64_t *cnt_host = nullptr;          // pinned, mapped: one count per slot
+    uint64_t *cnt_host_dev = nullptr;
+    cudaEvent_t ev_img[kMaxFrameDepth] = {}, ev_free[kMaxFrameDepth] = {}, ev_cmp[kMaxFrameDepth] = {},
+                ev_done[kMaxFrameDepth] = {};
+    int64_t next = 0, oldest = 0;          // frames in flight: tickets [oldest, next)
+    std::mutex mu;
+};
+
+namespace {
+
+void frames_free(scr_frames *f) {
+    scr_ctx *c = f->c;
+    if (f->st_copy)
+        cudaStreamSynchronize(f->st_copy);
+    if (f->st_comp)
+        cudaStreamSynchronize(f->st_comp);
+    if (f->st_out)
+        cudaStreamSynchronize(f->st_out);
+    cudaStream_t st = f->st_comp;
+    for (int k = 0; k < kMaxFrameDepth; ++k) {
+        dev_free(c, f->img[k], f->img_bytes, st);
+        dev_free(c, f->list_dev[k], f->list_bytes, st);
+    }
+    dev_free(c, f->tab_base, f->tab_bytes, st);
+    dev_free(c, f->build_scratch, f->build_bytes, st);
+    dev_free(c, f->compact_scratch, f->compact_bytes, st);
+    dev_free(c, f->mask, f->mask_bytes, st);
+    if (st)
+        cudaStreamSynchronize(st);
+    for (int k = 0; k < kMaxFrameDepth; ++k) {
+        if (f->ev_img[k]) cudaEventDestroy(f->ev_img[k]);
+        if (f->ev_free[k]) cudaEventDestroy(f->ev_free[k]);
+        if (f->ev_cmp[k]) cudaEventDestroy(f->ev_cmp[k]);
+        if (f->ev_done[k]) cudaEventDestroy(f->ev_done[k]);
+    }
+    if (f->cnt_host)
+        cudaFreeHost(f->cnt_host);
+    if (f->st_copy)
+        cudaStreamDestroy(f->st_copy);
+    if (f->st_comp)
+        cudaStreamDestroy(f->st_comp);
+    if (f->st_out)
+        cudaStreamDestroy(f->st_out);
+    delete f;
+}
+
+}  // namespace
+
+void scr_rt::destroy_frames(scr_ctx *c) {
+    std::set<scr_frames *> all;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        all.swap(c->frames);
+    }
+    for (auto *f : all)
+        frames_free(f);
+}
+
+extern "C" {
+
+int frames_create(scr_ctx *c, int32_t H, int32_t W, int32_t sum_bits, int32_t sq_bits, const scr_tmpl *tm,
+                  const scr_params *p, uint64_t list_cap, int32_t depth, scr_frames **out) {
+    int rc;
+    if ((rc = check_ctx(c)))
+        return rc;
+    if (!out || !tm)
+        return fail(SCR_EINVAL, "null template or out-pointer");
+    *out = nullptr;
+    if (H < 1 || W < 1 || H > 65535 || W > 65535)
+        return fail(SCR_EINVAL, "image %d x %d outside 1..65535", H, W);
+    if ((sum_bits != 32 && sum_bits != 64) || (sq_bits != 32 && sq_bits != 64))
+        return fail(SCR_EINVAL, "table widths must be 32 or 64 bits");
+    if (depth < 1 || depth > kMaxFrameDepth)
+        return fail(SCR_EINVAL, "depth %d outside 1..%d", depth, kMaxFrameDepth);
+    if ((rc = validate_params(p)))
+        return rc;
+    if (p->features & SCR_F_PREWITT)
+        return fail(SCR_EUNSUPPORTED, "frame pipelines do not build moment tables (SCR_F_PREWITT)");
+    if ((p->features & SCR_F_GRAD) && !(tm->features & SCR_F_GRAD))
+        return fail(SCR_EINVAL, "template features were computed without SCR_F_GRAD");
+    if (list_cap > ((uint64_t)1 << 40))
+        return fail(SCR_EINVAL, "list capacity %llu too large", (unsigned long long)list_cap);
+    DeviceGuard dg(c->device);
+    auto *f = new (std::nothrow) scr_frames();
+    if (!f)
+        return fail(SCR_ENOMEM, "host allocation failed");
+    f->c = c;
+    f->H = H;
+    f->W = W;
+    f->depth = depth;
+    f->dpitch = (W + 15) / 16 * 16;
+    f->list_cap = list_cap;
+    f->mask_words = (uint64_t)p->n_scales * H * ((W + 31) / 32);
+    cudaError_t e = cudaStreamCreateWithFlags(&f->st_copy, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithFlags(&f->st_comp, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithFlags(&f->st_out, cudaStreamNonBlocking);
+    for (int k = 0; k < depth && e == cudaSuccess; ++k) {
+        e = cudaEventCreateWithFlags(&f->ev_img[k], cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&f->ev_free[k], cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&f->ev_cmp[k], cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&f->ev_done[k], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess)
+        e = cudaHostAlloc((void **)&f->cnt_host, kMaxFrameDepth * 8, cudaHostAllocMapped);
+    if (e == cudaSuccess)
+        e = cudaHostGetDevicePointer((void **)&f->cnt_host_dev, f->cnt_host, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        frames_free(f);
+        return fail(SCR_ECUDA, "frame pipeline setup failed: %s", cudaGetErrorString(e));
+    }
+    cudaStream_t st = f->st_comp;
+    f->img_bytes = (size_t)f->dpitch * H;
+    f->tab_bytes = tables_bytes(H, W, sum_bits, sq_bits);
+    f->build_bytes = TableScratch::bytes(H, W, sum_bits, sq_bits);
+    f->compact_bytes = compact_scratch_bytes(f->mask_words);
+    f->mask_bytes = f->mask_words * 4;
+    f->list_bytes = std::max<uint64_t>(list_cap, 1) * 8 + 64;
+    rc = SCR_OK;
+    for (int k = 0; k < depth && !rc; ++k)
+        if (!(rc = dev_alloc(c, f->img_bytes, st, &f->img[k])))
+            rc = dev_alloc(c, f->list_bytes, st, &f->list_dev[k]);
+    if (!rc) rc = dev_alloc(c, f->tab_bytes, st, &f->tab_base);
+    if (!rc) rc = dev_alloc(c, f->build_bytes, st, &f->build_scratch);
+    if (!rc) rc = dev_alloc(c, f->compact_bytes, st, &f->compact_scratch);
+    if (!rc) rc = dev_alloc(c, f->mask_bytes, st, (void **)&f->mask);
+    if (!rc && (e = cudaStreamSynchronize(st)) != cudaSuccess)   // the other streams use the slots too
+        rc = fail(SCR_ECUDA, "frame pipeline allocation: %s", cudaGetErrorString(e));
+    if (rc) {
+        frames_free(f);
+        return rc;
+    }
+    layout_tables(&f->tabs, f->tab_base, f->tab_bytes, H, W, sum_bits, sq_bits, st);
+    fill_screen_args(&f->tabs, tm, p, &f->args);
+    f->args.mask = f->mask;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        c->frames.insert(f);
+    }
+    *out = f;
+    return SCR_OK;
+}
+
+int frames_submit(scr_frames *f, const uint8_t *img_host, int64_t pitch, uint64_t *list_host, int64_t *ticket) {
+    if (!f || !img_host || !ticket)
+        return fail(SCR_EINVAL, "null pipeline, image or ticket");
+    if (pitch < f->W)
+        return fail(SCR_EINVAL, "pitch %lld < width %d", (long long)pitch, f->W);
+    scr_ctx *c = f->c;
+    DeviceGuard dg(c->device);
+    uint64_t *list_map = nullptr;
+    if (f->list_cap) {
+        cudaPointerAttributes pa;
+        void *d = nullptr;
+        if (!list_host || cudaPointerGetAttributes(&pa, list_host) != cudaSuccess || pa.type != cudaMemoryTypeHost ||
+            cudaHostGetDevicePointer(&d, list_host, 0) != cudaSuccess || !d) {
+            cudaGetLastError();
+            return fail(SCR_EINVAL, "list_host must be pinned host memory the device can address");
+        }
+        list_map = (uint64_t *)d;
+    }
+    std::lock_guard<std::mutex> lk(f->mu);
+    if (f->next - f->oldest >= f->depth)
+        return fail(SCR_EINVAL, "%d frames in flight: wait for ticket %lld first", f->depth, (long long)f->oldest);
+    const int k = (int)(f->next % f->depth);
+    uint64_t n = 0;
+    cudaError_t e = cudaStreamWaitEvent(f->st_copy, f->ev_free[k], 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(f->img[k], f->dpitch, img_host, pitch, f->W, f->H, cudaMemcpyHostToDevice, f->st_copy);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(f->ev_img[k], f->st_copy);
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent(f->st_comp, f->ev_img[k], 0);
+    const TableDesc *t = f->tabs.t;
+    if (e == cudaSuccess)
+        e = launch_build_tables((const uint8_t *)f->img[k], f->H, f->W, f->dpitch, t[0], t[1], t[2], t[3],
+                                f->build_scratch, f->st_comp, &n);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(f->ev_free[k], f->st_comp);
+    if (e == cudaSuccess)
+        e = launch_screen(f->args, f->st_comp, &n);
+    uint64_t *keys = (uint64_t *)f->list_dev[k];
+    uint64_t *cnt = (uint64_t *)((char *)keys + std::max<uint64_t>(f->list_cap, 1) * 8);
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent(f->st_comp, f->ev_done[k], 0);
+    if (e == cudaSuccess)
+        e = launch_compact(f->mask, f->mask_words, f->H, (f->W + 31) / 32, f->list_cap ? keys : nullptr, f->list_cap,
+                           cnt, f->compact_scratch, f->st_comp, &n);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(f->ev_cmp[k], f->st_comp);
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent(f->st_out, f->ev_cmp[k], 0);
+    if (e == cudaSuccess)
+        e = launch_copy_keys(keys, cnt, f->list_cap, list_map, f->cnt_host_dev + k, f->st_out, &n);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(f->ev_done[k], f->st_out);
+    c->launches += n;
+    if (e != cudaSuccess) {
+        // nothing queued may still read img_host or write list_host
+        cudaStreamSynchronize(f->st_copy);
+        cudaStreamSynchronize(f->st_comp);
+        cudaStreamSynchronize(f->st_out);
+        return fail(SCR_ECUDA, "frames_submit: %s", cudaGetErrorString(e));
+    }
+    *ticket = f->next++;
+    return SCR_OK;
+}
+
+int frames_wait(scr_frames *f, int64_t ticket, uint64_t *n_survivors) {
+    if (!f || !n_survivors)
+        return fail(SCR_EINVAL, "null pipeline or count");
+    DeviceGuard dg(f->c->device);
+    std::lock_guard<std::mutex> lk(f->mu);
+    if (f->oldest == f->next || ticket != f->oldest)
+        return fail(SCR_EINVAL, "ticket %lld is not the oldest frame in flight", (long long)ticket);
+    const int k = (int)(ticket % f->depth);
+    cudaError_t e = cudaEventSynchronize(f->ev_done[k]);
+    if (e != cudaSuccess)
+        return fail(SCR_ECUDA, "frames_wait: %s", cudaGetErrorString(e));
+    ++f->oldest;
+    *n_survivors = ((volatile uint64_t *)f->cnt_host)[k];
+    if (*n_survivors > f->list_cap)
+        return fail(SCR_EOVERFLOW, "%llu survivors exceed list capacity %llu", (unsigned long long)*n_survivors,
+                    (unsigned long long)f->list_cap);
+    return SCR_OK;
+}
+
+void frames_destroy(scr_frames *f) {
+    if (!f)
+        return;
+    scr_ctx *c = f->c;
+    DeviceGuard dg(c->device);
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        c->frames.erase(f);
+    }
+    frames_free(f);
 }
 
 

@@ -67,6 +67,7 @@ struct scr_tmpl {
 
 struct scr_batch;
 struct scr_server;
+struct scr_frames;
 
 struct scr_ctx {
     int device = 0;
@@ -78,6 +79,7 @@ struct scr_ctx {
     std::set<scr_tmpl *> tmpls;
     std::set<scr_batch *> batches;
     std::set<scr_server *> servers;
+    std::set<scr_frames *> frames;   // frame pipelines (frames_create)
     std::map<std::string, std::pair<int, int>> tuned;   // batch shape -> (words per warp, blocks per SM)
     uint64_t *pinned = nullptr;      // 8-byte pinned slot for counts
     uint64_t *pinned_dev = nullptr;  // the same slot as the device sees it (null if not mapped)
@@ -190,6 +192,8 @@ int batch_prepare(scr_ctx *c, const scr_tables *const *tables, int n_images, con
 void batch_set_shape(scr_batch *b, int wpw, int blocks_per_sm);
 // serving loop (serve.cu)
 void destroy_servers(scr_ctx *c);
+// frame pipelines still alive at shutdown (api.cu)
+void destroy_frames(scr_ctx *c);
 
 }  // namespace scr_rt
 

@@ -439,3 +439,54 @@ def joint_areas(r: int, scales: list[float], n_areas: int):
     bands = [(int(math.ceil(r / lam ** (j + 1) - 1e-9)), int(math.floor(r / lam ** j + 1e-9)))
              for j in range(n_areas)]
     return area_radii, bands
+
+
+@dataclass
+class FrameSequence:
+    frames: list[np.ndarray]          # uint8 H x W each
+    template: np.ndarray              # uint8 (2r+1) x (2r+1)
+    r: int
+    radii: list[int]
+    t_min: int
+    features: int
+    tol: Tolerances
+    sum_bits: int
+    sq_bits: int
+    planted: list[tuple[int, int]]    # per frame: candidate (y*, x*) of the target
+    s_true: list[float]               # per frame: the target's scale
+
+
+def frame_sequence(seed: int, n_frames: int = 6, H: int = 256, W: int = 320, r: int = 16, n_scales: int = 4,
+                   s_min: float = 0.6, s_max: float = 1.6, sum_bits: int = 32, sq_bits: int = 64) -> FrameSequence:
+    """A short synthetic video for the tracking use of the screen (the paper
+    screens every frame of a tracking sequence for the target, Sec. 6): one
+    blob-field scene larger than the frame, seen through a window that pans a
+    few pixels per frame, with the target (a template cut from its own field)
+    pasted at a drifting position, rotating and changing scale from frame to
+    frame; each frame has its own noise."""
+    rng = rng_for(seed)
+    pad = 64
+    scene = blob_field(rng, H + 2 * pad, W + 2 * pad)
+    tmpl = _template_from_source(rng_for(seed + 7919), r)
+    scales = geometric_scales(s_min, s_max, n_scales)
+    side = 2 * r + 1
+    margin = int(math.ceil(s_max * side)) + 8
+    ys = float(rng.uniform(margin, H - margin))
+    xs = float(rng.uniform(margin, W - margin))
+    vy, vx = (float(v) for v in rng.uniform(-3.0, 3.0, 2))
+    theta = float(rng.uniform(0.0, 2.0 * math.pi))
+    s_now = float(math.exp(rng.uniform(math.log(s_min), math.log(s_max))))
+    frames, planted, s_list = [], [], []
+    for k in range(n_frames):
+        oy, ox = pad + (k * 2) % pad, pad - (k * 3) % pad
+        fld = scene[oy:oy + H, ox:ox + W].copy()
+        cy = int(min(max(ys + k * vy, margin), H - margin))
+        cx = int(min(max(xs + k * vx, margin), W - margin))
+        s_k = min(max(s_now * (1.0 + 0.02 * k), s_min), s_max)
+        paste(fld, tmpl, cy + 0.5, cx + 0.5, theta + 0.05 * k, s_k)
+        frames.append(quantize_with_noise(fld, rng))
+        planted.append((cy, cx))
+        s_list.append(s_k)
+    return FrameSequence(frames=frames, template=tmpl, r=r, radii=radii_for(r, scales),
+                         t_min=t_min_for(r, scales), features=F_MEAN | F_VAR | F_GRAD, tol=Tolerances(),
+                         sum_bits=sum_bits, sq_bits=sq_bits, planted=planted, s_true=s_list)

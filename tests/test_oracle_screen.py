@@ -155,3 +155,17 @@ def test_large_config_planted_match_survives(cfg):
     wl = synth.CONFIGS[cfg]()
     surv = _planted_survival(wl)
     assert any(s and c for s, c in zip(surv, _covering(wl))), (surv, wl.s_true)
+
+
+@pytest.mark.parametrize("seed", [5001, 5002, 5003])
+def test_tracked_target_survives_in_every_frame(seed):
+    """The frame-sequence workload (a panning scene with a drifting, rotating,
+    rescaling target): the target's own candidate survives at a covering scale
+    in every frame, from brute-force star sums."""
+    import types
+    fs = synth.frame_sequence(seed)
+    for k, img in enumerate(fs.frames):
+        wl = types.SimpleNamespace(image=img, template=fs.template, r=fs.r, t_min=fs.t_min, radii=fs.radii,
+                                   features=fs.features, tol=fs.tol, planted=fs.planted[k], s_true=fs.s_true[k])
+        surv = _planted_survival(wl)
+        assert any(s and c for s, c in zip(surv, _covering(wl))), (k, surv, wl.s_true)
