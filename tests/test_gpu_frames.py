@@ -190,3 +190,39 @@ def test_shutdown_frees_live_pipelines():
     lst = _pinned(1 << 14).view(np.uint64)
     scr.frames_submit(f, fs.frames[0], lst)
     scr.screen_shutdown(c)   # frees the pipeline after its frame completes
+
+
+def test_frames_full_size_against_the_oracle():
+    """Configuration 2 (4096 x 4096, 8 scales, u32/u64 tables) as a three-frame
+    stream (the image, its mirror image, the image again) through a depth-2
+    pipeline: every frame's complete list equals the oracle's."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    wl = synth.config2()
+    frames = [wl.image, np.ascontiguousarray(wl.image[:, ::-1]), wl.image]
+    ref = {}
+    for k in (0, 1):
+        ref[k] = oracle.screen_workload(frames[k], wl.template, wl.r, wl.t_min, wl.radii, wl.features,
+                                        wl.tol)["list"]
+    want = [ref[0], ref[1], ref[0]]
+    cap = max(len(w) for w in want) + 64
+    c = scr.screen_init(0, 0)
+    try:
+        tm = scr.template_features(c, wl.template, wl.r, wl.t_min, wl.features)
+        p = scr.Params(wl.radii, wl.features, wl.tol.mean_rel, wl.tol.std_rel, wl.tol.grad_rel, wl.tol.grad_abs)
+        H, W = wl.image.shape
+        f = scr.frames_create(c, H, W, wl.sum_bits, wl.sq_bits, tm, p, cap, 2)
+        imgs = [torch.from_numpy(im).pin_memory().numpy() for im in frames]
+        lists = [_pinned(cap).view(np.uint64) for _ in range(3)]
+        t0 = scr.frames_submit(f, imgs[0], lists[0])
+        t1 = scr.frames_submit(f, imgs[1], lists[1])
+        n0, _ = scr.frames_wait(f, t0)
+        t2 = scr.frames_submit(f, imgs[2], lists[2])
+        n1, _ = scr.frames_wait(f, t1)
+        n2, _ = scr.frames_wait(f, t2)
+        for n, lst, w in zip((n0, n1, n2), lists, want):
+            assert n == len(w)
+            assert np.array_equal(lst[:n], w)
+        scr.frames_destroy(f)
+    finally:
+        scr.screen_shutdown(c)
