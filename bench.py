@@ -1249,17 +1249,24 @@ def run_serve(args):
 
 
 def run_l1probe(args):
-    """Build and run the load-throughput probe (csrc/probe_l1.cu) that fixes the
-    screening kernel's on-chip ceiling; prints its JSON line."""
+    """Build and run the probes behind the screening kernel's on-chip ceiling:
+    load throughput per load shape (csrc/probe_l1.cu) and the kernel's own
+    locality bound (csrc/probe_locality.cu); prints one JSON line."""
     pkg = os.path.join(ROOT, "paper_1707_05647_gb300")
-    src = os.path.join(pkg, "csrc", "probe_l1.cu")
-    exe = os.path.join(pkg, "_build", "probe_l1")
-    os.makedirs(os.path.dirname(exe), exist_ok=True)
+    csrc = os.path.join(pkg, "csrc")
     nvcc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")
-    subprocess.check_call([nvcc if os.path.exists(nvcc) else "nvcc", "-gencode", "arch=compute_103a,code=sm_103a",
-                           "-O3", "-o", exe, src])
-    out = json.loads(subprocess.check_output([exe], text=True).strip().splitlines()[-1])
-    print(json.dumps({"metric": "L1 data-pipe throughput per load shape", **out}), flush=True)
+    nvcc = nvcc if os.path.exists(nvcc) else "nvcc"
+    os.makedirs(os.path.join(pkg, "_build"), exist_ok=True)
+    res = {}
+    for name, extra in (("probe_l1", []),
+                        ("probe_locality", ["-std=c++17", "-I", os.path.join(ROOT, "include"), "-I", csrc,
+                                            "--expt-relaxed-constexpr", "-diag-suppress", "68"])):
+        exe = os.path.join(pkg, "_build", name)
+        subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", *extra, "-o", exe,
+                               os.path.join(csrc, name + ".cu")])
+        res[name] = json.loads(subprocess.check_output([exe], text=True).strip().splitlines()[-1])
+    print(json.dumps({"metric": "L1 data-pipe throughput per load shape; screening-kernel locality bound",
+                      **res["probe_l1"], "locality": res["probe_locality"]}), flush=True)
 
 
 def main():

@@ -4,8 +4,11 @@
 // not; 64- and 128-bit vectors), for warp shuffles and shared-memory loads,
 // and for pairs of them issued together (whether they share the pipe).  Each
 // kernel's warps read 8 loads per iteration from a small region (L1-resident)
-// or a 32 MB region (mostly L2-served).  Not part of libscreen.so: bench.py
-// --workload l1probe builds and runs it and prints one JSON line.
+// or a 32 MB region (mostly L2-served).  Two further kernels read through a
+// texture object (tex1Dfetch) instead, alone and mixed with global loads, to
+// see whether the texture input path of L1TEX adds bandwidth next to the load
+// path.  Not part of libscreen.so: bench.py --workload l1probe builds and runs
+// it and prints one JSON line.
 // Every kernel reads only inside buf[0 .. words + PAD): the largest index read
 // is off + 1027 with off <= words - 32 (see each load's comment).
 #include <cstdio>
@@ -19,8 +22,8 @@
 constexpr uint32_t PAD = 4096;   // words of slack after the power-of-two region
 
 template <int M>
-__global__ void __launch_bounds__(256) probe(const uint32_t *__restrict__ buf, uint32_t wmask, int iters,
-                                             uint32_t *out) {
+__global__ void __launch_bounds__(256) probe(const uint32_t *__restrict__ buf, cudaTextureObject_t tx,
+                                             uint32_t wmask, int iters, uint32_t *out) {
     __shared__ uint32_t sm[2048 + 64];
     const int lane = threadIdx.x & 31;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -81,6 +84,14 @@ __global__ void __launch_bounds__(256) probe(const uint32_t *__restrict__ buf, u
                 const uint2 v = __ldg(b2 + lane + 32 * j);
                 acc[j] += v.x + v.y;
             }
+        } else if (M == 10) {    // 8 texture fetches, start 1 word past a 128-B line
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[j] += tex1Dfetch<unsigned int>(tx, (int)(off + 1 + lane + 32 * j));
+        } else if (M == 11) {    // 8 texture fetches + 8 misaligned 32-bit loads of other words
+#pragma unroll
+            for (int j = 0; j < 8; ++j)   // largest index off + 513 + 31 + 224 < off + 1027
+                acc[j] += tex1Dfetch<unsigned int>(tx, (int)(off + 1 + lane + 32 * j)) +
+                          __ldg(buf + off + 513 + lane + 32 * j);
         } else if (M == 9) {     // 8 LDG.128 shifted by 16 B (16-B aligned, not line aligned)
             const uint4 *b4 = reinterpret_cast<const uint4 *>(buf + off + 4);
 #pragma unroll
@@ -98,14 +109,14 @@ __global__ void __launch_bounds__(256) probe(const uint32_t *__restrict__ buf, u
 }
 
 template <int M>
-float run(const uint32_t *buf, uint32_t wmask, int iters, uint32_t *out, int blocks) {
+float run(const uint32_t *buf, cudaTextureObject_t tx, uint32_t wmask, int iters, uint32_t *out, int blocks) {
     cudaEvent_t a, b;
     CK(cudaEventCreate(&a));
     CK(cudaEventCreate(&b));
-    probe<M><<<blocks, 256>>>(buf, wmask, iters, out);
+    probe<M><<<blocks, 256>>>(buf, tx, wmask, iters, out);
     CK(cudaGetLastError());
     CK(cudaEventRecord(a));
-    for (int r = 0; r < 3; ++r) probe<M><<<blocks, 256>>>(buf, wmask, iters, out);
+    for (int r = 0; r < 3; ++r) probe<M><<<blocks, 256>>>(buf, tx, wmask, iters, out);
     CK(cudaEventRecord(b));
     CK(cudaEventSynchronize(b));
     float ms;
@@ -122,36 +133,50 @@ int main() {
     uint32_t *buf, *out;
     CK(cudaMalloc(&buf, maxw * 4ull));
     CK(cudaMemset(buf, 1, maxw * 4ull));
+    // a texture object over the same words (out-of-range fetches return 0)
+    cudaResourceDesc rd = {};
+    rd.resType = cudaResourceTypeLinear;
+    rd.res.linear.devPtr = buf;
+    rd.res.linear.desc = cudaCreateChannelDesc<unsigned int>();
+    rd.res.linear.sizeInBytes = maxw * 4ull;
+    cudaTextureDesc td = {};
+    td.readMode = cudaReadModeElementType;
+    cudaTextureObject_t tx;
+    CK(cudaCreateTextureObject(&tx, &rd, &td, nullptr));
     const int blocks = sms * 8;
     CK(cudaMalloc(&out, blocks * 256 * 4ull));
     const int iters = 2000;
     const char *names[] = {"ldg32_misaligned", "ldg32_aligned", "ldg128_aligned", "shfl",
                            "ldg128_plus_shfl", "ldg32_misaligned_plus_shfl", "lds32_misaligned",
-                           "lds32_plus_ldg32_misaligned", "ldg64_aligned", "ldg128_at_16B"};
+                           "lds32_plus_ldg32_misaligned", "ldg64_aligned", "ldg128_at_16B", "tex32_misaligned",
+                           "tex32_plus_ldg32_misaligned"};
     printf("{\"sms\": %d, \"max_clock_mhz\": %.0f, \"unit\": \"warp instructions of each kind per clock per SM "
            "(at the maximum clock)\"", sms, clk / 1e3);
     for (uint32_t region : regions) {
         const uint32_t wmask = region - 1;
-        float t[10];
-        t[0] = run<0>(buf, wmask, iters, out, blocks);
-        t[1] = run<1>(buf, wmask, iters, out, blocks);
-        t[2] = run<2>(buf, wmask, iters, out, blocks);
-        t[3] = run<3>(buf, wmask, iters, out, blocks);
-        t[4] = run<4>(buf, wmask, iters, out, blocks);
-        t[5] = run<5>(buf, wmask, iters, out, blocks);
-        t[6] = run<6>(buf, wmask, iters, out, blocks);
-        t[7] = run<7>(buf, wmask, iters, out, blocks);
-        t[8] = run<8>(buf, wmask, iters, out, blocks);
-        t[9] = run<9>(buf, wmask, iters, out, blocks);
+        float t[12];
+        t[0] = run<0>(buf, tx, wmask, iters, out, blocks);
+        t[1] = run<1>(buf, tx, wmask, iters, out, blocks);
+        t[2] = run<2>(buf, tx, wmask, iters, out, blocks);
+        t[3] = run<3>(buf, tx, wmask, iters, out, blocks);
+        t[4] = run<4>(buf, tx, wmask, iters, out, blocks);
+        t[5] = run<5>(buf, tx, wmask, iters, out, blocks);
+        t[6] = run<6>(buf, tx, wmask, iters, out, blocks);
+        t[7] = run<7>(buf, tx, wmask, iters, out, blocks);
+        t[8] = run<8>(buf, tx, wmask, iters, out, blocks);
+        t[9] = run<9>(buf, tx, wmask, iters, out, blocks);
+        t[10] = run<10>(buf, tx, wmask, iters, out, blocks);
+        t[11] = run<11>(buf, tx, wmask, iters, out, blocks);
         const double warps = blocks * 8.0;
         printf(", \"%s\": {", region < (1u << 20) ? "l1_resident_32KB" : "l2_served_32MB");
-        for (int m = 0; m < 10; ++m) {
+        for (int m = 0; m < 12; ++m) {
             const double per = warps * iters * 8.0 / sms / (t[m] * 1e-3 * clk * 1e3);
             printf("%s\"%s\": %.3f", m ? ", " : "", names[m], per);
         }
         printf("}");
     }
     printf("}\n");
+    CK(cudaDestroyTextureObject(tx));
     CK(cudaFree(buf));
     CK(cudaFree(out));
     return 0;

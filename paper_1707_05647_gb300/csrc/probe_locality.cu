@@ -1,0 +1,123 @@
+// Locality bound of the screening kernel: the same k_screen code (this file
+// compiles features.cu into itself) timed on the 8192 x 8192 shape with the
+// 16 radii R = 22..179, once on real table rows and once with every row
+// aliased to row 0 (row pitch 0 in the corner offsets and in the candidate
+// base), so every corner read after the first touch of a line is an L1 hit.
+// Both runs execute the same instructions: the mean interval is the full
+// 32-bit range and the variance interval holds only V = 0, so every word
+// issues the 16 star-sum reads of I and I^2 and then fails, as on the
+// configuration-3 image, where the mean test passes 98% of candidates and the
+// variance test almost none.  The difference between the two times is what
+// any traversal order could gain from L1 reuse.  Not part of libscreen.so:
+// bench.py --workload l1probe builds and runs it and prints one JSON line.
+//
+// Every read stays inside the four planes: with real rows, corner rows are
+// y - h + 1 >= 0 .. y + h + 1 <= H and columns x - h + 1 >= 0 .. x + h + 1 <= W + 1
+// (plus the 3-word column offset, below the pitch of W + 2 + 16 rounded to
+// 32); with aliased rows only row 0 is read, at the same columns.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "features.cu"
+
+#define CK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { printf("CUDA %s at %d\n", cudaGetErrorString(e_), __LINE__); exit(1);} } while (0)
+
+__global__ void fill_tables(uint32_t *p, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        p[i] = (uint32_t)(i * 2654435761u) ^ (uint32_t)(i >> 7);
+}
+
+static int square_half(int R) {
+    int n = 0;
+    while ((2 * n + 1) * (2 * n + 1) < 2 * R * R)
+        ++n;
+    return n;
+}
+
+int main() {
+    const int H = 8192, W = 8192, S = 16;
+    const int radii[S] = {22, 26, 30, 34, 39, 45, 51, 59, 68, 78, 90, 103, 118, 136, 156, 179};
+    const int64_t P = scr::table_pitch_words(W + 2);
+    const size_t plane = (size_t)(H + 1) * P;
+    const int Ww = (W + 31) / 32;
+    uint32_t *tab, *mask, *flush;
+    CK(cudaMalloc(&tab, plane * 4 * sizeof(uint32_t)));
+    CK(cudaMalloc(&mask, (size_t)S * H * Ww * sizeof(uint32_t)));
+    CK(cudaMalloc(&flush, 256u << 20));
+    fill_tables<<<4096, 256>>>(tab, plane * 4);
+    CK(cudaGetLastError());
+    cudaStream_t st;
+    CK(cudaStreamCreate(&st));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double best[2], mean[2];
+    for (int mode = 0; mode < 2; ++mode) {
+        scr::ScreenArgs a;
+        memset(&a, 0, sizeof a);
+        a.L1 = tab;
+        a.L2 = tab + plane;
+        a.T1 = tab + 2 * plane;
+        a.T2 = tab + 3 * plane;
+        const int64_t Q = mode == 0 ? P : 0;   // row pitch seen by the kernel
+        a.pitch = Q;
+        a.H = H;
+        a.W = W;
+        a.Wwords = Ww;
+        a.n_scales = S;
+        a.features = SCR_F_MEAN | SCR_F_VAR;
+        a.mask = mask;
+        for (int s = 0; s < S; ++s) {
+            const int R = radii[s], n = square_half(R), h = R, m = n > h ? n : h;
+            scr::ScaleParam &sp = a.sp[s];
+            const int64_t oL[4] = {(n + 1) * Q + (n + 1), (1 - n) * Q + (n + 1), (n + 1) * Q + (1 - n),
+                                   (1 - n) * Q + (1 - n)};
+            const int64_t oT[4] = {(h + 1) * Q + 1, Q + (1 - h), Q + (h + 1), (1 - h) * Q + 1};
+            for (int k = 0; k < 4; ++k) {
+                sp.oL[k] = sp.oLi[k] = (int32_t)oL[k];
+                sp.oT[k] = sp.oTi[k] = (int32_t)oT[k];
+            }
+            sp.y_lo = m - 1;
+            sp.y_hi = H - 1 - m;
+            sp.x_lo = m - 1;
+            sp.x_hi = (W - 1 - n) < (W - h) ? (W - 1 - n) : (W - h);
+            sp.A = 4 * n * n + 2 * h * h;
+            sp.Ain = sp.Aring = 1;
+            sp.empty = 0;
+            sp.S_lo = 0;
+            sp.S_rng = 0xffffffffu;   // every candidate passes the mean test
+            sp.V_lo = 0;
+            sp.V_rng = 0;             // and (almost) none the variance test
+            sp.N_lo = 0;
+            sp.N_rng = ~0ull;
+            sp.P_lo = 0;
+            sp.P_rng = ~(unsigned __int128)0;
+        }
+        double b = 1e30, sum = 0;
+        const int warm = 3, timed = 5;
+        for (int it = 0; it < warm + timed; ++it) {
+            CK(cudaMemsetAsync(flush, it, 256u << 20, st));   // flush L2 between launches
+            CK(cudaEventRecord(e0, st));
+            CK(scr::launch_screen(a, st, nullptr));
+            CK(cudaEventRecord(e1, st));
+            CK(cudaEventSynchronize(e1));
+            float ms;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (it >= warm) {
+                b = ms < b ? ms : b;
+                sum += ms;
+            }
+        }
+        best[mode] = b;
+        mean[mode] = sum / timed;
+    }
+    printf("{\"workload\": \"k_screen, 8192x8192, 16 radii 22..179, 16 star-sum reads per candidate\", "
+           "\"real_rows_ms\": {\"best\": %.4f, \"mean\": %.4f}, \"rows_aliased_ms\": {\"best\": %.4f, \"mean\": %.4f}, "
+           "\"locality_bound_speedup\": %.3f}\n",
+           best[0], mean[0], best[1], mean[1], mean[0] / mean[1]);
+    CK(cudaFree(tab));
+    CK(cudaFree(mask));
+    CK(cudaFree(flush));
+    return 0;
+}
