@@ -194,8 +194,10 @@ def code_sha256(paths):
 
 
 # what the screening kernel's DRAM traffic depends on: its source, the shared
-# launch/argument header, and the compiler flags
-SCREEN_CODE = [os.path.join(ROOT, "paper_1707_05647_gb300", "csrc", f) for f in ("features.cu", "internal.h")] + \
+# launch/argument header, the host code that fills its arguments (per-scale
+# bounds, corner offsets, filter windows) and the compiler flags
+SCREEN_CODE = [os.path.join(ROOT, "paper_1707_05647_gb300", "csrc", f) for f in ("features.cu", "internal.h",
+                                                                               "api.cu")] + \
     [os.path.join(ROOT, "paper_1707_05647_gb300", "_build.py")]
 
 
@@ -203,41 +205,44 @@ def kernel_code_sha256(path=None):
     return code_sha256([path] if path else SCREEN_CODE)
 
 
-def recorded_traffic(H, W, root=ROOT):
+def _record(path, n_windows):
+    """key: value lines of a committed profile record, or None when the record is
+    missing, was taken on other kernel code, or with another number of packed
+    filter windows than this run uses (filter_windows, 0 when absent)."""
+    if not os.path.exists(path):
+        return None
+    rec = {}
+    for line in open(path):
+        if ":" in line and not line.startswith(("#", " ", "`")):
+            k, v = line.split(":", 1)
+            rec[k.strip()] = v.strip()
+    if rec.get("kernel_code_sha256") != kernel_code_sha256():
+        return None
+    if int(rec.get("filter_windows", "0")) != n_windows:
+        return None
+    return rec
+
+
+def recorded_traffic(H, W, root=ROOT, n_windows=0):
     """DRAM bytes per k_screen launch from the committed one-pass ncu capture of
     this workload (profiles/k_screen_<H>_traffic.txt), or None when there is
-    none or the kernel's code changed since it was taken."""
-    path = os.path.join(root, "profiles", f"k_screen_{H}_traffic.txt")
-    if H != W or not os.path.exists(path):
-        return None
-    rec = {}
-    for line in open(path):
-        if ":" in line and not line.startswith(("#", " ", "`")):
-            k, v = line.split(":", 1)
-            rec[k.strip()] = v.strip()
-    if rec.get("kernel_code_sha256") != kernel_code_sha256():
-        return None
-    return int(rec["dram_bytes_per_launch"])
+    none or it does not describe this kernel code and filter setting."""
+    rec = _record(os.path.join(root, "profiles", f"k_screen_{H}_traffic.txt"), n_windows) if H == W else None
+    return int(rec["dram_bytes_per_launch"]) if rec else None
 
 
-def recorded_onchip(H, W, root=ROOT):
+def recorded_onchip(H, W, root=ROOT, n_windows=0):
     """On-chip utilisation of k_screen from the committed ncu full-set capture
     (profiles/k_screen_<H>_onchip.txt: the same workload's recipe, cropped so the
-    capture ends in seconds), or None when the kernel's code changed since."""
-    path = os.path.join(root, "profiles", f"k_screen_{H}_onchip.txt")
-    if H != W or not os.path.exists(path):
-        return None
-    rec = {}
-    for line in open(path):
-        if ":" in line and not line.startswith(("#", " ", "`")):
-            k, v = line.split(":", 1)
-            rec[k.strip()] = v.strip()
-    if rec.get("kernel_code_sha256") != kernel_code_sha256():
+    capture ends in seconds), or None when it does not describe this kernel code
+    and filter setting."""
+    rec = _record(os.path.join(root, "profiles", f"k_screen_{H}_onchip.txt"), n_windows) if H == W else None
+    if rec is None:
         return None
     out = {k: float(rec[k]) for k in ("l1_lsu_data_pipe_pct", "l1tex_pct", "issue_active_pct", "l2_pct",
                                       "dram_pct", "l1_hit_pct", "warp_instructions_per_32_candidates")
            if k in rec}
-    out["bound"] = "L1 data pipe and instruction issue (no HBM bound)"
+    out["bound"] = rec.get("bound", "L1 data pipe and instruction issue (no HBM bound)")
     out["source"] = f"profiles/k_screen_{H}_onchip.txt ({rec.get('case', 'ncu --set full')})"
     return out
 
@@ -376,9 +381,11 @@ def run_reference(args):
 
 
 class Single:
-    """One single-image workload on one device: inputs resident, buffers sized."""
+    """One single-image workload on one device: inputs resident, buffers sized.
+    With use_filter the tables carry the packed filter planes of the windows
+    screen_filter_windows suggests for this template (screen_set_filter)."""
 
-    def __init__(self, scr, torch, ctx, wl):
+    def __init__(self, scr, torch, ctx, wl, use_filter=False):
         self.scr, self.torch, self.ctx, self.wl = scr, torch, ctx, wl
         H, W = wl.image.shape
         self.H, self.W, self.S = H, W, len(wl.radii)
@@ -386,6 +393,8 @@ class Single:
         self.p = scr.Params(wl.radii, wl.features, wl.tol.mean_rel, wl.tol.std_rel, wl.tol.grad_rel,
                             wl.tol.grad_abs)
         self.tm = scr.template_features(ctx, wl.template, wl.r, wl.t_min, wl.features)
+        self.windows = scr.screen_filter_windows(self.tm, self.p) if use_filter else []
+        self.plan = None
         self.stream = torch.cuda.current_stream()
         self.img = torch.from_numpy(wl.image).cuda()
         self.mask = torch.empty(scr.mask_words(self.S, H, W), dtype=torch.int32, device="cuda")
@@ -395,7 +404,10 @@ class Single:
 
     def step(self, evs=None):
         scr, wl, st = self.scr, self.wl, self.stream
+        scr.screen_set_filter(self.ctx, self.windows)
         tb = scr.build_tables(self.ctx, self.img, wl.sum_bits, wl.sq_bits, st)
+        if self.plan is None:
+            self.plan = scr.screen_filter_plan(tb, self.tm, self.p)
         if evs:
             evs[0].record(st)
         scr.screen_features(self.ctx, tb, self.tm, self.p, self.mask, st)
@@ -453,11 +465,32 @@ class Single:
                 "total_s": sum(step_ms) / 1e3, "launches": launches, "clocks": clk,
                 "survivors": int(self.count.item())}
 
+    def filter_dict(self):
+        """The packed-plane pre-filter of this run, for the JSON line."""
+        if not self.windows:
+            return {"windows": [], "note": "off: exact corner reads only"}
+        return {"windows": [list(w) for w in self.windows],
+                "scales_filtered": sum(1 for w in self.plan if w >= 0) if self.plan else 0,
+                "window_per_scale": self.plan,
+                "note": "tables carry one packed upright and one packed cone plane per window (bits kS..kS+15 "
+                        "of the sum table, kQ..kQ+15 of the squares' table); each candidate's variance is "
+                        "first bounded from 8 packed reads and exact corners are read only where a "
+                        "candidate is left; masks and lists unchanged"}
+
     def mask_host(self):
         return self.mask.cpu().numpy().view(np.uint32).reshape(self.S, self.H, (self.W + 31) // 32)
 
     def release(self):
         self.scr.template_release(self.ctx, self.tm)
+
+
+def use_filter(args, cfg):
+    """The packed-plane pre-filter pays where most candidates pass the mean test
+    and fail the variance test on a flat background (configuration 3: the mean
+    test passes 98%); where the mean test already rejects nearly everything
+    (configuration 2: 0.04% pass) the extra planes only cost build time, so
+    "auto" uses it on configuration 3 only."""
+    return args.filter == "on" or (args.filter == "auto" and cfg == 3)
 
 
 def run_ours(args):
@@ -476,7 +509,7 @@ def run_ours(args):
     wl = workload(args.config, 1000 * rank, args.size)
     ctx = scr.screen_init(local, 0)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    run = Single(scr, torch, ctx, wl)
+    run = Single(scr, torch, ctx, wl, use_filter=use_filter(args, args.config))
     m = run.timed(args.steps, args.warmup, flush, clocks, dist)
     total_s = m["total_s"]
     if dist:
@@ -486,6 +519,7 @@ def run_ours(args):
     m["value"] = world * run.ncand * args.steps / total_s
     m["total_s"] = total_s
     surv = survival(run.mask_host(), wl)
+    filt = run.filter_dict()
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(scr, torch, ctx, run, args)
@@ -493,7 +527,7 @@ def run_ours(args):
     second = None
     if args.config == 3 and not args.no_secondary and not args.size:
         wl2 = workload(2, 1000 * rank)
-        run2 = Single(scr, torch, ctx, wl2)
+        run2 = Single(scr, torch, ctx, wl2, use_filter=use_filter(args, 2))
         steps2 = max(args.steps, 20)
         m2 = run2.timed(steps2, args.warmup, flush)
         second = secondary_dict(wl2, run2, m2, steps2, surv_of=survival(run2.mask_host(), wl2))
@@ -504,7 +538,7 @@ def run_ours(args):
     if args.config == 3 and not args.no_secondary and not args.size and world == 1:
         legs = secondary_legs(args)
     if rank == 0:
-        emit(args, wl, world, m, e2e, surv, second, legs)
+        emit(args, wl, world, m, e2e, surv, second, legs, filt)
     scr.screen_shutdown(ctx)
     if dist:
         dist.destroy_process_group()
@@ -580,6 +614,7 @@ def run_e2e(scr, torch, ctx, run, args):
     torch.cuda.synchronize()
     n_ref = int(run.count.item())
     ref_keys = run.lst[:min(n_ref, run.cap)].cpu().numpy()
+    scr.screen_set_filter(ctx, run.windows)   # the same tables as the device-timed run
     # one synchronous call per step
     for _ in range(2):
         scr.screen_host(ctx, img_host.numpy(), wl.sum_bits, wl.sq_bits, run.tm, run.p, lst_host.numpy())
@@ -624,7 +659,7 @@ def run_e2e(scr, torch, ctx, run, args):
                             "how": "screen_host(): the same path, one synchronous call per step"}}
 
 
-def rooflines(wl, k3_s, tab_s, n_surv):
+def rooflines(wl, k3_s, tab_s, n_surv, n_windows=0):
     H, W = wl.image.shape
     S = len(wl.radii)
     peak, src = measured_peak_gbs()
@@ -637,21 +672,28 @@ def rooflines(wl, k3_s, tab_s, n_surv):
     compulsory = {"achieved": achieved, "frac": achieved / peak,
                   "model": f"compulsory (tables once across scales + mask + list): {alg} B/launch, "
                            f"{alg / ncand:.2f} B/candidate"}
-    traffic = recorded_traffic(H, W)
-    binding = ("on-chip: the L1 data pipe and instruction issue; the tables are read from DRAM about "
-               "once (low 32-bit planes) and re-read across scales from L2")
+    traffic = recorded_traffic(H, W, n_windows=n_windows)
+    if n_windows:
+        binding = ("on-chip: instruction issue and the integer ALU pipe of the packed-plane pre-filter; the "
+                   "packed planes are read from DRAM about once and re-read across scales from L2")
+    else:
+        binding = ("on-chip: the L1 data pipe and instruction issue; the tables are read from DRAM about "
+                   "once (low 32-bit planes) and re-read across scales from L2")
     common = {"bound": "hbm", "peak": peak, "unit": "GB/s", "traffic": traffic, "peak_source": src,
               "kernel": "k_screen", "kernel_ms": 1e3 * k3_s, "binding": binding,
-              "onchip": recorded_onchip(H, W)}
+              "onchip": recorded_onchip(H, W, n_windows=n_windows)}
     if alg1 <= peak:
         roofline = dict(common, achieved=alg1, frac=alg1 / peak, model=per_scale_model, compulsory=compulsory)
     else:
         roofline = dict(common, achieved=achieved, frac=achieved / peak, model=compulsory["model"],
                         per_scale_above_peak={"achieved": alg1, "model": per_scale_model})
-    tb_bytes = H * W + table_bytes(H, W, wl.sum_bits, wl.sq_bits)
+    fb = n_windows * table_bytes(H, W, 16, 16)   # a window's upright + cone packed planes, 32-bit each
+    tb_bytes = H * W + table_bytes(H, W, wl.sum_bits, wl.sq_bits) + fb
+    model = f"1 B/px image read + tables written: {tb_bytes} B per build"
+    if n_windows:
+        model += f" (of which {fb} B the packed filter planes of {n_windows} windows)"
     tables_roofline = {"bound": "hbm", "achieved": tb_bytes / tab_s / 1e9, "peak": peak, "unit": "GB/s",
-                       "frac": tb_bytes / tab_s / 1e9 / peak, "build_ms": 1e3 * tab_s,
-                       "model": f"1 B/px image read + tables written: {tb_bytes} B per build",
+                       "frac": tb_bytes / tab_s / 1e9 / peak, "build_ms": 1e3 * tab_s, "model": model,
                        "kernels": "k_tab_reduce, k_tab_carry, k_tab_prefix, k_tab_write"}
     return roofline, tables_roofline
 
@@ -659,8 +701,8 @@ def rooflines(wl, k3_s, tab_s, n_surv):
 def secondary_dict(wl, run, m, steps, surv_of):
     k3 = statistics.mean(m["k3_ms"]) / 1e3
     tab = statistics.mean(m["tab_ms"]) / 1e3
-    roof, troof = rooflines(wl, k3, tab, m["survivors"])
-    return {"workload": config_dict(wl, 2)["workload"], "steps": steps,
+    roof, troof = rooflines(wl, k3, tab, m["survivors"], len(run.windows))
+    return {"workload": config_dict(wl, 2)["workload"], "filter": run.filter_dict(), "steps": steps,
             "value": run.ncand * steps / m["total_s"], "unit": UNIT, "ms_per_step": 1e3 * m["total_s"] / steps,
             "k_screen_ms": 1e3 * k3, "roofline_frac": roof["frac"], "roofline_model": roof["model"],
             "tables_ms": 1e3 * tab, "tables_frac": troof["frac"], "survivors": m["survivors"],
@@ -673,10 +715,10 @@ def dtype_of(wl):
     return "u32" if wl.sum_bits == wl.sq_bits == 32 else ("u64" if wl.sum_bits == 64 else "u32+u64")
 
 
-def emit(args, wl, world, m, e2e, surv, second=None, legs=None):
+def emit(args, wl, world, m, e2e, surv, second=None, legs=None, filt=None):
     k3 = statistics.mean(m["k3_ms"]) / 1e3
     tab = statistics.mean(m["tab_ms"]) / 1e3
-    roofline, tables_roofline = rooflines(wl, k3, tab, m["survivors"])
+    roofline, tables_roofline = rooflines(wl, k3, tab, m["survivors"], len((filt or {}).get("windows", [])))
     cpu = None
     if not args.no_cpu_baseline:
         split, split1 = {}, {}
@@ -693,7 +735,7 @@ def emit(args, wl, world, m, e2e, surv, second=None, legs=None):
         "metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * m["total_s"] / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dtype_of(wl),
-        "data": "synthetic", "config": config_dict(wl, args.config),
+        "data": "synthetic", "config": dict(config_dict(wl, args.config), filter=filt),
         "roofline": roofline, "tables_roofline": tables_roofline,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": m["launches"],
         "clocks": m["clocks"] or {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled on this rank"]},
@@ -1282,6 +1324,9 @@ def main():
     ap.add_argument("--size", type=int, default=None,
                     help="crop the image to size x size (smaller ncu captures)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--filter", default="auto", choices=["auto", "on", "off"],
+                    help="packed-plane pre-filter of the single-image legs (screen_set_filter with the windows "
+                         "screen_filter_windows suggests); auto: on for configuration 3 only")
     ap.add_argument("--no-secondary", action="store_true", help="skip the 4096x4096 run after config 3")
     ap.add_argument("--no-check", action="store_true", help="skip the oracle checks of the batched and serve legs")
     ap.add_argument("--seed", type=int, default=None, help="serve workload seed (default 1004)")

@@ -151,18 +151,61 @@ int screen_stats(const scr_ctx *ctx, scr_stats *out);
 int build_tables(scr_ctx *ctx, const uint8_t *img_dev, int32_t H, int32_t W, int64_t pitch,
                  int32_t sum_bits, int32_t sq_bits, scr_stream stream, scr_tables **out);
 
-/* Borrowed device view of table `which` (0..3).  Layout: 32-bit words; element
- * (a, b) of a 32-bit table is word a*pitch + b + offset of *dev_ptr, where
- * *dev_ptr points at word 0; a 64-bit table is two such planes, the low 32 bits
- * at *dev_ptr and the high 32 bits plane_stride words further.  rows x cols is
- * the logical size; pitch and plane_stride are in 32-bit words. */
+/* Packed filter planes for later single-image table builds (an implementation
+ * device of this library; the paper has no counterpart).  windows holds
+ * n_windows (0..2) pairs (kS, kQ), 0 <= kS <= 14, 0 <= kQ <= 16.  Tables built
+ * afterwards by build_tables, screen_host and frames_create on this context
+ * carry, per window, one extra 32-bit upright plane and one cone plane:
+ * element (a, b) holds bits kS..kS+15 of L1 (T1) in its low half and bits
+ * kQ..kQ+15 of L2 (T2) in its high half.  screen_positions / screen_features
+ * on such tables first bound each candidate's pooled sums S and Q from its
+ * star's eight packed corners (8 reads instead of the 16 exact ones), reject
+ * the candidates whose variance is certainly below the variance interval,
+ * and read the exact corners only where a candidate is left.  Each scale uses
+ * the narrowest window whose range holds every candidate that can pass its
+ * mean and variance intervals; scales with no such window, screens without
+ * the variance test and the Prewitt variant read exact corners only.  Masks
+ * and lists are unchanged (bit-exact).  The planes cost 8 bytes per pixel per
+ * window in the build; they pay when most candidates pass the mean test and
+ * fail the variance test on a background flatter than the template (measured
+ * on the 8192 x 8192, 16-scale workload: screen 2.64 -> 2.26 ms, build
+ * 0.55 -> 0.78 ms); where the mean test already rejects most candidates they
+ * only cost.  n_windows = 0 turns the planes off.  The batched and serving
+ * paths ignore the setting; tables already built keep what they have.
+ * SCR_EINVAL for bad counts or shifts. */
+int screen_set_filter(scr_ctx *ctx, int32_t n_windows, const int32_t *windows);
+
+/* Suggested windows for screening with template tm and parameters p (host
+ * computation): for every scale the smallest shifts whose range holds the
+ * candidates that can pass; the first window fits every scale, and when
+ * max_windows >= 2 and some scale fits shifts 3 smaller, a second window 3
+ * smaller is returned first.  Writes *n_windows pairs (0 when the variance
+ * test is off). */
+int screen_filter_windows(const scr_tmpl *tm, const scr_params *p, int32_t max_windows, int32_t *windows,
+                          int32_t *n_windows);
+
+/* The packed window each scale of a screen with (t, tm, p) would use: writes
+ * p->n_scales entries to window_per_scale (host), the window index or -1 when
+ * the scale reads exact corners only (no planes, no window whose range holds
+ * the candidates that can pass, an empty scale, no variance test, or the
+ * Prewitt variant).
+ * Host computation. */
+int screen_filter_plan(const scr_tables *t, const scr_tmpl *tm, const scr_params *p, int32_t *window_per_scale);
+
+/* Borrowed device view of table `which` (0..3; 6 + 2w and 7 + 2w: the upright
+ * and the cone packed plane of filter window w, 32-bit).  Layout: 32-bit words;
+ * element (a, b) of a 32-bit table is word a*pitch + b + offset of *dev_ptr,
+ * where *dev_ptr points at word 0; a 64-bit table is two such planes, the low
+ * 32 bits at *dev_ptr and the high 32 bits plane_stride words further.
+ * rows x cols is the logical size; pitch and plane_stride are in 32-bit words. */
 int tables_view(const scr_tables *t, int which, const void **dev_ptr, int64_t *rows,
                 int64_t *cols, int64_t *pitch, int64_t *offset, int64_t *plane_stride,
                 int32_t *bits);
 
 /* Copy table `which` into a dense rows x cols uint64 host array (values zero-
  * extended from 32-bit tables); which 4 and 5 are the moment tables Mx and My
- * ((H + 1) x (W + 1), after build_moment_tables).  Synchronous. */
+ * ((H + 1) x (W + 1), after build_moment_tables); 6 + 2w and 7 + 2w the packed
+ * filter planes of window w.  Synchronous. */
 int tables_copy_to_host(scr_ctx *ctx, const scr_tables *t, int which, uint64_t *dst_host);
 
 void tables_release(scr_ctx *ctx, scr_tables *t);

@@ -110,6 +110,9 @@ def load(build_if_missing: bool = True):
         "screen_last_error": ([], ctypes.c_char_p),
         "screen_stats": ([vp, ctypes.POINTER(_Stats)], ctypes.c_int),
         "build_tables": ([vp, vp, i32, i32, i64, i32, i32, vp, pp], ctypes.c_int),
+        "screen_set_filter": ([vp, i32, vp], ctypes.c_int),
+        "screen_filter_windows": ([vp, ctypes.POINTER(_Params), i32, vp, ctypes.POINTER(i32)], ctypes.c_int),
+        "screen_filter_plan": ([vp, vp, ctypes.POINTER(_Params), vp], ctypes.c_int),
         "tables_view": ([vp, ctypes.c_int, pp] + [ctypes.POINTER(i64)] * 5 + [ctypes.POINTER(i32)], ctypes.c_int),
         "tables_copy_to_host": ([vp, vp, ctypes.c_int, vp], ctypes.c_int),
         "build_moment_tables": ([vp, vp, i32, i32, i64, vp, vp], ctypes.c_int),
@@ -161,6 +164,7 @@ def load(build_if_missing: bool = True):
 
 def exported_symbols():
     return ["screen_init", "screen_shutdown", "screen_last_error", "screen_stats", "build_tables",
+            "screen_set_filter", "screen_filter_windows", "screen_filter_plan",
             "tables_view", "tables_copy_to_host", "build_moment_tables", "tables_release", "template_features",
             "template_sums",
             "template_release", "screen_bounds", "screen_features", "screen_joint", "compact_mask",
@@ -252,6 +256,28 @@ def build_tables(ctx, img, sum_bits: int = 32, sq_bits: int = 64, stream=None, H
     return out
 
 
+def screen_set_filter(ctx, windows) -> None:
+    """Packed filter windows [(kS, kQ), ...] (0..2 pairs) for the context's later
+    single-image table builds (build_tables, screen_host, frames_create); [] turns them off."""
+    arr = np.ascontiguousarray(np.array(list(windows), dtype=np.int32).reshape(-1))
+    _check(load().screen_set_filter(ctx, len(arr) // 2, _ptr(arr) if len(arr) else ctypes.c_void_p(0)))
+
+
+def screen_filter_windows(tm, params: "Params", max_windows: int = 2):
+    """Suggested packed filter windows [(kS, kQ), ...] for template tm and params."""
+    out = (ctypes.c_int32 * 4)()
+    n = ctypes.c_int32()
+    _check(load().screen_filter_windows(tm, ctypes.byref(params.c), max_windows, out, ctypes.byref(n)))
+    return [(int(out[2 * i]), int(out[2 * i + 1])) for i in range(n.value)]
+
+
+def screen_filter_plan(tables, tm, params: "Params"):
+    """Per scale, the packed window a screen would use (-1: exact corners only)."""
+    out = np.empty(params.n_scales, np.int32)
+    _check(load().screen_filter_plan(tables, tm, ctypes.byref(params.c), _ptr(out)))
+    return [int(v) for v in out]
+
+
 def tables_view(tables, which: int) -> dict:
     p = ctypes.c_void_p()
     v = [ctypes.c_int64() for _ in range(5)]
@@ -268,8 +294,9 @@ def build_moment_tables(ctx, tables, img, stream=None) -> None:
 
 
 def tables_copy_to_host(ctx, tables, which: int) -> np.ndarray:
-    """which 0..3: L1, L2, T1, T2; 4, 5: the moment tables Mx, My ((H+1) x (W+1))."""
-    if which >= 4:
+    """which 0..3: L1, L2, T1, T2; 4, 5: the moment tables Mx, My ((H+1) x (W+1));
+    6 + 2w, 7 + 2w: the upright and cone packed filter planes of window w."""
+    if which in (4, 5):
         v = tables_view(tables, 0)            # the upright table's (H + 1) x (W + 1)
         out = np.empty((v["rows"], v["cols"]), np.uint64)
         _check(load().tables_copy_to_host(ctx, tables, which, _ptr(out)))

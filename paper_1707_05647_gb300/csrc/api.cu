@@ -193,12 +193,13 @@ int64_t table_plane_words(int H, int W) {
     return ((rows * table_pitch_words(W) + 63) / 64) * 64;
 }
 
-size_t tables_bytes(int H, int W, int sum_bits, int sq_bits) {
-    return (size_t)table_plane_words(H, W) * 4 * (size_t)(2 * (sum_bits / 32) + 2 * (sq_bits / 32));
+size_t tables_bytes(int H, int W, int sum_bits, int sq_bits, int n_filter) {
+    return (size_t)table_plane_words(H, W) * 4 *
+           (size_t)(2 * (sum_bits / 32) + 2 * (sq_bits / 32) + 2 * n_filter);
 }
 
 void layout_tables(scr_tables *t, void *base, size_t bytes, int H, int W, int sum_bits, int sq_bits,
-                   cudaStream_t st) {
+                   cudaStream_t st, int n_filter, const int (*fk)[2]) {
     const int64_t pitch = table_pitch_words(W);
     const int64_t rows = (int64_t)H + 1;
     const int64_t plane = table_plane_words(H, W);
@@ -221,23 +222,34 @@ void layout_tables(scr_tables *t, void *base, size_t bytes, int H, int W, int su
         d.cols = cols[k];
         d.bits = bits[k];
     }
+    t->F = FilterPlanes();
+    t->F.n = n_filter;
+    for (int f = 0; f < n_filter; ++f) {
+        t->F.up[f] = p;
+        p += plane;
+        t->F.cone[f] = p;
+        p += plane;
+        t->F.kS[f] = fk[f][0];
+        t->F.kQ[f] = fk[f][1];
+    }
     t->H = H;
     t->W = W;
     t->stream = st;
 }
 
-int alloc_tables(scr_ctx *c, int H, int W, int sum_bits, int sq_bits, cudaStream_t st, scr_tables **out) {
+int alloc_tables(scr_ctx *c, int H, int W, int sum_bits, int sq_bits, cudaStream_t st, scr_tables **out,
+                 int n_filter, const int (*fk)[2]) {
     auto *t = new (std::nothrow) scr_tables();
     if (!t)
         return fail(SCR_ENOMEM, "host allocation failed");
-    const size_t bytes = tables_bytes(H, W, sum_bits, sq_bits);
+    const size_t bytes = tables_bytes(H, W, sum_bits, sq_bits, n_filter);
     void *base = nullptr;
     int rc = dev_alloc(c, bytes, st, &base);
     if (rc) {
         delete t;
         return rc;
     }
-    layout_tables(t, base, bytes, H, W, sum_bits, sq_bits, st);
+    layout_tables(t, base, bytes, H, W, sum_bits, sq_bits, st, n_filter, fk);
     *out = t;
     return SCR_OK;
 }
@@ -245,7 +257,7 @@ int alloc_tables(scr_ctx *c, int H, int W, int sum_bits, int sq_bits, cudaStream
 int run_build_in(scr_ctx *c, const uint8_t *img, int H, int W, int64_t pitch, scr_tables *t, void *scratch,
                  cudaStream_t st) {
     uint64_t n = 0;
-    cudaError_t e = launch_build_tables(img, H, W, pitch, t->t[0], t->t[1], t->t[2], t->t[3], scratch, st, &n);
+    cudaError_t e = launch_build_tables(img, H, W, pitch, t->t[0], t->t[1], t->t[2], t->t[3], t->F, scratch, st, &n);
     c->launches += n;
     CUDA_TRY(e);
     return SCR_OK;
@@ -425,6 +437,95 @@ void prewitt_bounds(const scr_tmpl *tm, const scr_params *p, int R, unsigned __i
     *U = big_u128_sat(big_div(big_mul(num, J2sq), big_mul(den, Big((unsigned __int128)(4 * n * n))), nullptr));
 }
 
+// ---- packed-plane pre-filter: which window a scale may use -------------------
+//
+// A packed plane holds, per table element, bits kS .. kS+15 of the sum table
+// and bits kQ .. kQ+15 of the sum-of-squares table.  The signed sum of a
+// star's eight packed corners gives u = sum of floor(corner / 2^kS) modulo 2^16,
+// which lies strictly within 4 of S / 2^kS (four corners add and four
+// subtract, each dropping less than one unit), and likewise for Q with a
+// further carry of -4 .. 3 from the low half.  The window is usable at a
+// scale when every candidate that can pass the exact tests has S and Q small
+// enough that u does not wrap: S <= S_hi' <= 2^kS (2^16 - 8) and
+// Q <= Q_hi' <= 2^kQ (2^16 - 16), where S_hi' is the mean test's upper bound
+// (at most 255 A) and Q_hi' = floor((V_hi + S_hi'^2) / A) (at most 65025 A),
+// since V = A Q - S^2 <= V_hi.  Candidates with larger S or Q fail the exact
+// tests whatever the filter decides.
+struct FilterRange {
+    bool usable;              // the variance test is on (the pre-filter tests its lower bound)
+    int64_t S_lo, S_hi;       // mean interval clipped to [0, 255 A]
+    i128 Q_hi;                // largest Q of a candidate that can pass
+    int64_t V_lo, V_hi;       // variance interval (full range when off)
+};
+
+static FilterRange filter_range(const scr_params *p, const scr_bounds &b, int64_t A) {
+    FilterRange r;
+    const bool fm = p->features & SCR_F_MEAN, fv = p->features & SCR_F_VAR;
+    r.usable = fv;
+    r.S_lo = fm ? std::max<int64_t>(b.S_lo, 0) : 0;
+    r.S_hi = fm ? std::min<int64_t>(b.S_hi, 255 * A) : 255 * A;
+    r.Q_hi = (i128)65025 * A;
+    if (fv) {
+        const i128 v = (i128)b.V_hi + (i128)r.S_hi * r.S_hi;
+        r.Q_hi = std::min<i128>(r.Q_hi, v < 0 ? 0 : v / A);
+    }
+    r.V_lo = fv ? b.V_lo : INT64_MIN;
+    r.V_hi = fv ? b.V_hi : INT64_MAX;
+    return r;
+}
+
+static bool window_fits(const FilterRange &r, int kS, int kQ) {
+    return r.usable && (i128)r.S_hi <= ((i128)1 << kS) * (65536 - 8) && r.Q_hi <= ((i128)1 << kQ) * (65536 - 16);
+}
+
+// smallest shifts (kS, kQ) at which a window is usable for this range; false if none
+static bool min_window(const FilterRange &r, int *kS, int *kQ) {
+    if (!r.usable)
+        return false;
+    int a = 0, q = 0;
+    while (a <= kMaxFilterShiftS && (i128)r.S_hi > ((i128)1 << a) * (65536 - 8))
+        ++a;
+    while (q <= kMaxFilterShiftQ && r.Q_hi > ((i128)1 << q) * (65536 - 16))
+        ++q;
+    if (a > kMaxFilterShiftS || q > kMaxFilterShiftQ)
+        return false;
+    *kS = a;
+    *kQ = q;
+    return true;
+}
+
+// float nearest to v on the side that widens an interval: down (dir < 0) or up
+static float float_toward(double v, int dir) {
+    float f = (float)v;
+    if (dir < 0 && (double)f > v)
+        f = nextafterf(f, -INFINITY);
+    if (dir > 0 && (double)f < v)
+        f = nextafterf(f, INFINITY);
+    return f;
+}
+
+// Single-precision constants of the kernel's pre-filter (filter_pass in
+// features.cu) for window (kS, kQ).  2^kS, A 2^kQ and their products with 2^23
+// and 2^23 + 8 are exact floats (A < 2^17, kS <= 14, kQ <= 16).  The mean lower
+// bound is rounded down; the variance lower bound moves down by
+// M = 4 u (X + |V_lo|) + 1 with X = A 2^kQ 65535 the largest corner product and
+// u = 2^-24, more than the kernel's roundings can move a computed A Q - S^2.
+static void filter_constants(const FilterRange &r, uint32_t A, int kS, int kQ, ScaleParam *sp) {
+    const double two23 = 8388608.0, u = 1.0 / 16777216.0;
+    const double s2 = ldexp(1.0, kS), c = (double)A * ldexp(1.0, kQ);
+    sp->f2S = (float)s2;
+    sp->fS0 = (float)(-s2 * (two23 + 8));
+    sp->fSlo = float_toward((double)r.S_lo, -1);
+    sp->fc = (float)c;
+    sp->fQ0 = (float)(-c * two23);
+    if (r.V_lo == INT64_MIN) {
+        sp->fVlo = -INFINITY;
+    } else {
+        const double v = (double)r.V_lo, X = c * 65535.0;
+        sp->fVlo = float_toward(v - (4 * u * (X + fabs(v)) + 1), -1);
+    }
+}
+
 int fill_screen_args(const scr_tables *t, const scr_tmpl *tm, const scr_params *p, ScreenArgs *a) {
     memset(a, 0, sizeof *a);
     a->L1 = t->t[0].lo;
@@ -503,6 +604,31 @@ int fill_screen_args(const scr_tables *t, const scr_tmpl *tm, const scr_params *
     }
     a->Mx = t->Mx;
     a->My = t->My;
+    for (int f = 0; f < t->F.n; ++f) {
+        a->FU[f] = t->F.up[f];
+        a->FC[f] = t->F.cone[f];
+    }
+    // each scale takes the narrowest packed window whose range holds every
+    // candidate that can pass (no window: the scale reads the exact corners only)
+    for (int s = 0; s < p->n_scales; ++s) {
+        ScaleParam &sp = a->sp[s];
+        sp.fw = -1;
+        if (!t->F.n || sp.empty || (p->features & SCR_F_PREWITT))   // the Prewitt variant reads exact corners only
+            continue;
+        scr_bounds b;
+        bounds_for(tm, p, p->radii[s], &b);
+        const FilterRange r = filter_range(p, b, sp.A);
+        int best = -1;
+        for (int f = 0; f < t->F.n; ++f)
+            if (window_fits(r, t->F.kS[f], t->F.kQ[f]) &&
+                (best < 0 || t->F.kS[f] < t->F.kS[best] ||
+                 (t->F.kS[f] == t->F.kS[best] && t->F.kQ[f] < t->F.kQ[best])))
+                best = f;
+        if (best < 0)
+            continue;
+        sp.fw = best;
+        filter_constants(r, sp.A, t->F.kS[best], t->F.kQ[best], &sp);
+    }
     return SCR_OK;
 }
 
@@ -641,7 +767,7 @@ int build_tables(scr_ctx *c, const uint8_t *img_dev, int32_t H, int32_t W, int64
     cudaStream_t st = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(c->mu);
     scr_tables *t = nullptr;
-    if ((rc = alloc_tables(c, H, W, sum_bits, sq_bits, st, &t)))
+    if ((rc = alloc_tables(c, H, W, sum_bits, sq_bits, st, &t, c->n_filter, c->filter_k)))
         return rc;
     if ((rc = run_build(c, img_dev, H, W, pitch, t, st))) {
         free_tables(c, t);
@@ -652,8 +778,98 @@ int build_tables(scr_ctx *c, const uint8_t *img_dev, int32_t H, int32_t W, int64
     return SCR_OK;
 }
 
+int screen_set_filter(scr_ctx *c, int32_t n_windows, const int32_t *windows) {
+    int rc;
+    if ((rc = check_ctx(c)))
+        return rc;
+    if (n_windows < 0 || n_windows > kMaxFilterWindows || (n_windows && !windows))
+        return fail(SCR_EINVAL, "n_windows %d outside 0..%d (or null windows)", n_windows, kMaxFilterWindows);
+    for (int f = 0; f < n_windows; ++f)
+        if (windows[2 * f] < 0 || windows[2 * f] > kMaxFilterShiftS || windows[2 * f + 1] < 0 ||
+            windows[2 * f + 1] > kMaxFilterShiftQ)
+            return fail(SCR_EINVAL, "window %d: shifts (%d, %d) outside 0..%d, 0..%d", f, windows[2 * f],
+                        windows[2 * f + 1], kMaxFilterShiftS, kMaxFilterShiftQ);
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->n_filter = n_windows;
+    for (int f = 0; f < n_windows; ++f) {
+        c->filter_k[f][0] = windows[2 * f];
+        c->filter_k[f][1] = windows[2 * f + 1];
+    }
+    return SCR_OK;
+}
+
+int screen_filter_windows(const scr_tmpl *tm, const scr_params *p, int32_t max_windows, int32_t *windows,
+                          int32_t *n_windows) {
+    if (!tm || !windows || !n_windows || max_windows < 0)
+        return fail(SCR_EINVAL, "null argument or negative max_windows");
+    int rc;
+    if ((rc = validate_params(p)))
+        return rc;
+    *n_windows = 0;
+    // the narrowest usable shifts of every scale, and their largest values
+    std::vector<std::pair<int, int>> need;
+    int hs = -1, hq = -1;
+    for (int s = 0; s < p->n_scales; ++s) {
+        scr_bounds b;
+        bounds_for(tm, p, p->radii[s], &b);
+        const FilterRange r = filter_range(p, b, geometry(p->radii[s]).A);
+        int kS, kQ;
+        if (!min_window(r, &kS, &kQ))
+            continue;
+        need.push_back({kS, kQ});
+        hs = std::max(hs, kS);
+        hq = std::max(hq, kQ);
+    }
+    if (need.empty() || max_windows == 0)
+        return SCR_OK;
+    // one window wide enough for every scale; a second one 3 bits narrower for
+    // the scales that fit it (a window loses little precision on scales up to
+    // 3 bits below it: measured on the 8192 x 8192, 16-scale workload)
+    windows[0] = hs;
+    windows[1] = hq;
+    *n_windows = 1;
+    if (max_windows >= 2 && hs >= 3 && hq >= 3) {
+        bool some = false;
+        for (const auto &k : need)
+            some |= k.first <= hs - 3 && k.second <= hq - 3;
+        if (some) {
+            windows[2] = windows[0];
+            windows[3] = windows[1];
+            windows[0] = hs - 3;
+            windows[1] = hq - 3;
+            *n_windows = 2;
+        }
+    }
+    return SCR_OK;
+}
+
+int screen_filter_plan(const scr_tables *t, const scr_tmpl *tm, const scr_params *p, int32_t *window_per_scale) {
+    if (!window_per_scale)
+        return fail(SCR_EINVAL, "null output");
+    int rc;
+    if ((rc = check_screen_inputs(t, tm, p)))
+        return rc;
+    ScreenArgs a;
+    if ((rc = fill_screen_args(t, tm, p, &a)))
+        return rc;
+    for (int s = 0; s < p->n_scales; ++s)
+        window_per_scale[s] = a.sp[s].fw;
+    return SCR_OK;
+}
+
 int tables_view(const scr_tables *t, int which, const void **dev_ptr, int64_t *rows, int64_t *cols, int64_t *pitch,
                 int64_t *offset, int64_t *plane_stride, int32_t *bits) {
+    if (t && which >= 6 && which < 6 + 2 * t->F.n) {   // packed filter planes
+        const int f = (which - 6) / 2, cone = (which - 6) % 2;
+        if (dev_ptr) *dev_ptr = cone ? t->F.cone[f] : t->F.up[f];
+        if (rows) *rows = t->t[0].rows;
+        if (cols) *cols = cone ? t->t[2].cols : t->t[0].cols;
+        if (pitch) *pitch = t->t[0].pitch;
+        if (offset) *offset = kColOffset;
+        if (plane_stride) *plane_stride = 0;
+        if (bits) *bits = 32;
+        return SCR_OK;
+    }
     if (!t || which < 0 || which > 3)
         return fail(SCR_EINVAL, "bad tables handle or index %d", which);
     const TableDesc &d = t->t[which];
@@ -671,6 +887,18 @@ int tables_copy_to_host(scr_ctx *c, const scr_tables *t, int which, uint64_t *ds
     int rc;
     if ((rc = check_ctx(c)))
         return rc;
+    if (t && dst && which >= 6 && which < 6 + 2 * t->F.n) {   // packed filter planes, 32-bit values
+        DeviceGuard dg(c->device);
+        const int f = (which - 6) / 2, cone = (which - 6) % 2;
+        const uint32_t *src = cone ? t->F.cone[f] : t->F.up[f];
+        const int64_t rows = t->t[0].rows, cols = cone ? t->t[2].cols : t->t[0].cols, P = t->t[0].pitch;
+        std::vector<uint32_t> v((size_t)rows * cols);
+        CUDA_TRY(cudaStreamSynchronize(t->stream));
+        CUDA_TRY(cudaMemcpy2D(v.data(), cols * 4, src + kColOffset, P * 4, cols * 4, rows, cudaMemcpyDeviceToHost));
+        for (size_t k = 0; k < v.size(); ++k)
+            dst[k] = v[k];
+        return SCR_OK;
+    }
     if (!t || which < 0 || which > 5 || !dst || (which >= 4 && !t->Mx))
         return fail(SCR_EINVAL, "bad arguments");
     DeviceGuard dg(c->device);
@@ -1427,7 +1655,13 @@ int frames_create(scr_ctx *c, int32_t H, int32_t W, int32_t sum_bits, int32_t sq
     }
     cudaStream_t st = f->st_comp;
     f->img_bytes = (size_t)f->dpitch * H;
-    f->tab_bytes = tables_bytes(H, W, sum_bits, sq_bits);
+    int nfil = 0, fk[kMaxFilterWindows][2];
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        nfil = c->n_filter;
+        memcpy(fk, c->filter_k, sizeof fk);
+    }
+    f->tab_bytes = tables_bytes(H, W, sum_bits, sq_bits, nfil);
     f->build_bytes = TableScratch::bytes(H, W, sum_bits, sq_bits);
     f->compact_bytes = compact_scratch_bytes(f->mask_words);
     f->mask_bytes = f->mask_words * 4;
@@ -1446,7 +1680,7 @@ int frames_create(scr_ctx *c, int32_t H, int32_t W, int32_t sum_bits, int32_t sq
         frames_free(f);
         return rc;
     }
-    layout_tables(&f->tabs, f->tab_base, f->tab_bytes, H, W, sum_bits, sq_bits, st);
+    layout_tables(&f->tabs, f->tab_base, f->tab_bytes, H, W, sum_bits, sq_bits, st, nfil, fk);
     fill_screen_args(&f->tabs, tm, p, &f->args);
     f->args.mask = f->mask;
     {
@@ -1490,7 +1724,7 @@ int frames_submit(scr_frames *f, const uint8_t *img_host, int64_t pitch, uint64_
     const TableDesc *t = f->tabs.t;
     if (e == cudaSuccess)
         e = launch_build_tables((const uint8_t *)f->img[k], f->H, f->W, f->dpitch, t[0], t[1], t[2], t[3],
-                                f->build_scratch, f->st_comp, &n);
+                                f->tabs.F, f->build_scratch, f->st_comp, &n);
     if (e == cudaSuccess)
         e = cudaEventRecord(f->ev_free[k], f->st_comp);
     if (e == cudaSuccess)

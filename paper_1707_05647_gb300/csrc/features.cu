@@ -16,6 +16,16 @@
 // kernel reads only the low 32-bit plane of every table and subtracts modulo
 // 2^32: the result is the exact sum.  Products are formed in 64 bits.
 //
+// Packed-plane pre-filter (optional, on tables built with filter windows): a
+// scale that has a window first sums its star's eight corners of one packed
+// plane, which carries 16 bits of the sum table and 16 bits of the squares'
+// table per element, so one 32-bit read per corner yields both the pooled sum
+// S and the pooled square sum Q to within a few units of 2^kS and 2^kQ.
+// From those bounds the kernel rejects every candidate whose variance is
+// certainly below the variance interval, and reads the exact corners only for
+// the words where some candidate is left; the exact tests then decide as
+// without the filter, so the mask is the same bit for bit.
+//
 // Mapping: one warp evaluates WPW consecutive mask words (32 x each) of one
 // row for every scale, so each corner read is a coalesced 128-byte row segment
 // and each word is formed with one warp ballot.  The tests run in order mean,
@@ -34,7 +44,16 @@
 namespace scr {
 namespace {
 
-constexpr int kWarpsPerBlock = 16;   // 16 warps = 4096 x of one row per block
+// Warps per block: 16 (4096 x of one row) for the exact reads, whose left and
+// right corner segments then meet in one SM's L1; 1 when a scale pre-filters
+// on packed planes, where a warp's work varies with how many of its words
+// need exact reads and a block slot should free as soon as its warp is done.
+// Measured on the 8192^2, 16-scale workload: exact reads 2.61 ms with 16-warp
+// blocks against 2.67 / 2.71 / 2.79 / 2.95 ms with 8 / 4 / 2 / 1; pre-filter
+// 1.68 ms with 1-warp blocks against 1.75 / 1.76 / 1.87 / 2.26 ms with
+// 2 / 4 / 8 / 16 (4 words per warp: 2.11 ms with 4-warp blocks).
+constexpr int kExactWarpsPerBlock = 16;
+constexpr int kFilterWarpsPerBlock = 1;
 
 __device__ __forceinline__ uint32_t ld(const uint32_t *p) { return __ldg(p); }
 
@@ -58,6 +77,31 @@ struct Corners {
     }
 };
 
+// Pre-filter of one candidate from tot, the signed sum of its star's eight
+// packed corners (mod 2^32).  Its low half, plus 4, is s + 4 where
+// s = sum of floor(corner / 2^kS) (mod 2^16) lies strictly within 4 of
+// S / 2^kS; its high half, plus 8, is q + 8 where q is the same for Q and 2^kQ
+// with the low half's carry (-4 .. 3), strictly within 8 below and 7 above.
+// The host picked the window so that neither wraps for a candidate that can
+// pass.  So S >= 2^kS (s - 4) and Q <= 2^kQ (q + 8), and the variance
+// numerator V = A Q - S^2 of a candidate whose S passes the mean test is at
+// most A 2^kQ (q + 8) - max(2^kS (s - 4), S_lo)^2.  The filter rejects the
+// candidate when that bound is below V_lo, the variance test's usual failure
+// on a background flatter than the template; every other failure is left to
+// the exact tests.  It runs in single precision: both halves become floats
+// exactly (a byte permute puts them under the exponent of 2^23), the two box
+// corners come from one fused multiply-add each (exact products, one
+// rounding), and the host lowered V_lo by 4 u (A 2^kQ 65535 + |V_lo|) + 1,
+// u = 2^-24, which covers every rounding here.  Candidates the window's range
+// does not cover fail the exact tests anyway, so the mask is exact.
+__device__ __forceinline__ bool filter_pass(uint32_t tot, const ScaleParam &p) {
+    const float ms = __int_as_float(__byte_perm(tot + 4u, 0x4B000000u, 0x7610));        // 2^23 + s + 4
+    const float mq = __int_as_float(__byte_perm(tot + 0x80000u, 0x4B000000u, 0x7632));  // 2^23 + q + 8
+    const float slo = fmaxf(fmaf(p.f2S, ms, p.fS0), p.fSlo);   // max(2^kS (s - 4), S_lo)
+    const float x = fmaf(p.fc, mq, p.fQ0);                     // A 2^kQ (q + 8)
+    return fmaf(-slo, slo, x) >= p.fVlo;
+}
+
 // WPW: mask words per warp.  The warp covers 32*WPW consecutive x; corner
 // pointers are formed once per scale and every word reads at an immediate
 // offset from them, and the per-scale bookkeeping is shared by all words.
@@ -71,18 +115,15 @@ constexpr int WPW = 8;
 // PW: the Prewitt gradient test of the star's square (Sec. 3, Eq. S_y with
 // the moment tables of Eq. T_x; magnitude of Sec. 4) runs after the others,
 // compared squared in 128 bits.  The default kernel has no Prewitt code.
-// 64 registers let the batched star-sum reads stay in flight together:
-// measured 182 us against 189 us at 48 registers and 192 us at 80 on the
-// 4096^2 workload.  Blocks of 16 warps (2 per SM) cover 4096 x of a row, so
-// the left and right corner segments of more warps meet in one SM's L1:
-// 2.64 ms against 2.71 ms with 8-warp blocks on the 8192^2 workload (4096^2:
-// 0.184 against 0.182 ms).
-template <bool PW>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock, 2)
+// 64 registers (WB warps per block, 32 / WB blocks per SM) let the batched
+// star-sum reads stay in flight together: measured 182 us against 189 us at
+// 48 registers and 192 us at 80 on the 4096^2 workload.
+template <bool PW, int WB>
+__global__ void __launch_bounds__(32 * WB, 32 / WB)
 k_screen(const __grid_constant__ ScreenArgs a) {
     pdl_begin();
     const int lane = threadIdx.x & 31;
-    const int w0 = (blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5)) * WPW;   // first word
+    const int w0 = (blockIdx.x * WB + (threadIdx.x >> 5)) * WPW;   // first word
     const int y = blockIdx.y;
     if (w0 >= a.Wwords)
         return;
@@ -101,9 +142,42 @@ k_screen(const __grid_constant__ ScreenArgs a) {
         uint32_t keep = 0;   // bit j: the candidate of word j is still alive
         if (!p.empty && y >= p.y_lo && y <= p.y_hi) {   // block-uniform
             uint32_t S[WPW];
-            // star sum: square (upright table) + diamond (cone table), Sec. 4
-            const Corners c(L1, T1, p.oL, p.oT);
-            if (xw_lo >= p.x_lo && xw_hi <= p.x_hi) {   // warp-uniform: every word valid
+            if (!PW && p.fw >= 0) {   // block-uniform: pre-filter on a packed plane
+                const Corners cf(a.FU[p.fw] + e, a.FC[p.fw] + e, p.oL, p.oT);
+                if (xw_lo >= p.x_lo && xw_hi <= p.x_hi) {
+                    uint32_t v[WPW][8];
+#pragma unroll
+                    for (int j = 0; j < WPW; ++j)
+#pragma unroll
+                        for (int k = 0; k < 8; ++k)
+                            v[j][k] = ld(cf.p[k] + 32 * j);
+#pragma unroll
+                    for (int j = 0; j < WPW; ++j) {
+                        const uint32_t tot =
+                            v[j][0] - v[j][1] - v[j][2] + v[j][3] + v[j][4] - v[j][5] - v[j][6] + v[j][7];
+                        keep |= (filter_pass(tot, p) ? 1u : 0u) << j;
+                    }
+                } else {
+                    const uint32_t span = (uint32_t)(p.x_hi - p.x_lo);
+#pragma unroll
+                    for (int j = 0; j < WPW; ++j)
+                        if ((uint32_t)(x0 + 32 * j - p.x_lo) <= span && filter_pass(cf.sum(j), p))
+                            keep |= 1u << j;
+                }
+                // exact star sums of the candidates the filter kept
+#pragma unroll
+                for (int j = 0; j < WPW; ++j)
+                    S[j] = 0;
+                if (__any_sync(0xffffffffu, keep != 0)) {
+                    const Corners c(L1, T1, p.oL, p.oT);
+#pragma unroll
+                    for (int j = 0; j < WPW; ++j)
+                        if ((keep >> j) & 1u)
+                            S[j] = c.sum(j);
+                }
+            } else if (xw_lo >= p.x_lo && xw_hi <= p.x_hi) {   // warp-uniform: every word valid
+                // star sum: square (upright table) + diamond (cone table), Sec. 4
+                const Corners c(L1, T1, p.oL, p.oT);
                 // all 8 x WPW corner reads are written before any sum, which lets
                 // the scheduler issue them back to back (measured ~4% faster than
                 // summing word by word)
@@ -118,6 +192,7 @@ k_screen(const __grid_constant__ ScreenArgs a) {
                     S[j] = v[j][0] - v[j][1] - v[j][2] + v[j][3] + v[j][4] - v[j][5] - v[j][6] + v[j][7];
                 keep = (1u << WPW) - 1;
             } else {
+                const Corners c(L1, T1, p.oL, p.oT);
                 const uint32_t span = (uint32_t)(p.x_hi - p.x_lo);
 #pragma unroll
                 for (int j = 0; j < WPW; ++j) {
@@ -271,10 +346,20 @@ __global__ void k_template_sums(const TmplArgs a) {
 
 cudaError_t launch_screen(const ScreenArgs &args, cudaStream_t st, uint64_t *launches) {
     const int warps = (args.Wwords + WPW - 1) / WPW;
-    dim3 grid((warps + kWarpsPerBlock - 1) / kWarpsPerBlock, args.H);
-    const cudaError_t e = (args.features & SCR_F_PREWITT)
-                              ? launch_pdl(k_screen<true>, grid, dim3(32 * kWarpsPerBlock), st, args)
-                              : launch_pdl(k_screen<false>, grid, dim3(32 * kWarpsPerBlock), st, args);
+    bool filtered = false;   // some scale pre-filters on packed planes
+    for (int s = 0; s < args.n_scales; ++s)
+        filtered |= args.sp[s].fw >= 0;
+    cudaError_t e;
+    if (args.features & SCR_F_PREWITT) {
+        constexpr int WB = kExactWarpsPerBlock;
+        e = launch_pdl(k_screen<true, WB>, dim3((warps + WB - 1) / WB, args.H), dim3(32 * WB), st, args);
+    } else if (filtered) {
+        constexpr int WB = kFilterWarpsPerBlock;
+        e = launch_pdl(k_screen<false, WB>, dim3((warps + WB - 1) / WB, args.H), dim3(32 * WB), st, args);
+    } else {
+        constexpr int WB = kExactWarpsPerBlock;
+        e = launch_pdl(k_screen<false, WB>, dim3((warps + WB - 1) / WB, args.H), dim3(32 * WB), st, args);
+    }
     if (launches)
         *launches += 1;
     return e;

@@ -39,6 +39,25 @@ constexpr int kWinLo = -34;                // first carry column kept per band
 inline int64_t table_pitch_words(int64_t W) { return ((W + 16 + 31) / 32) * 32; }
 
 // ---------------------------------------------------------------------------
+// Packed filter planes (optional, screen_set_filter).  For a window (kS, kQ)
+// element (a, b) of the upright plane holds bits kS .. kS+15 of L1(a, b) in its
+// low half and bits kQ .. kQ+15 of L2(a, b) in its high half; the cone plane
+// holds the same bits of T1 and T2.  Same rows, pitch and column offset as the
+// tables.  A star's eight signed corners of one packed plane give its pooled
+// sums of I and I^2 to within a few units of 2^kS and 2^kQ, which is enough
+// to reject most candidates before any exact corner is read (features.cu).
+// ---------------------------------------------------------------------------
+constexpr int kMaxFilterWindows = 2;
+constexpr int kMaxFilterShiftS = 14;   // kS in 0 .. 14: the filter's sum bounds stay inside 32-bit integers
+constexpr int kMaxFilterShiftQ = 16;   // kQ in 0 .. 16: the window's bits stay inside the low 32-bit plane
+struct FilterPlanes {
+    int n = 0;                                       // windows written (0 .. kMaxFilterWindows)
+    uint32_t *up[kMaxFilterWindows] = {nullptr, nullptr};
+    uint32_t *cone[kMaxFilterWindows] = {nullptr, nullptr};
+    int kS[kMaxFilterWindows] = {0, 0}, kQ[kMaxFilterWindows] = {0, 0};
+};
+
+// ---------------------------------------------------------------------------
 // Screening parameters handed to the feature kernel (one record per scale).
 // ---------------------------------------------------------------------------
 constexpr int kMaxScales = 32;
@@ -61,10 +80,18 @@ struct ScaleParam {
     int64_t N_lo;
     uint64_t N_rng;                   // contrast: (N - N_lo) <= N_rng       (64-bit)
     unsigned __int128 P_lo, P_rng;    // Prewitt:  (Gx2^2 + Gy2^2 - P_lo) <= P_rng (128-bit)
+    // packed-plane pre-filter (FilterPlanes): window index, -1 for none, and
+    // its single-precision constants (see filter_pass in features.cu)
+    int32_t fw;
+    float f2S, fS0;                   // 2^kS, -2^kS (2^23 + 8)
+    float fSlo;                       // mean lower bound, at least 0, rounded down
+    float fc, fQ0;                    // A 2^kQ, -A 2^kQ 2^23
+    float fVlo;                       // variance lower bound lowered by the rounding margin
 };
 
 struct ScreenArgs {
     const uint32_t *L1, *L2, *T1, *T2;   // low planes (window sums read mod 2^32)
+    const uint32_t *FU[kMaxFilterWindows], *FC[kMaxFilterWindows];   // packed planes (upright, cone)
     const uint64_t *Mx, *My;             // Prewitt moment tables (with SCR_F_PREWITT)
     int64_t pitch;                       // words per row (all four tables)
     int32_t H, W, Wwords, n_scales;
@@ -113,7 +140,7 @@ struct TableScratch {
 
 cudaError_t launch_build_tables(const uint8_t *img, int H, int W, int64_t pitch,
                                 const TableDesc &L1, const TableDesc &L2, const TableDesc &T1,
-                                const TableDesc &T2, void *scratch, cudaStream_t st,
+                                const TableDesc &T2, const FilterPlanes &F, void *scratch, cudaStream_t st,
                                 uint64_t *launches);
 
 cudaError_t launch_template_sums(const TableDesc &L1, const TableDesc &L2, const TableDesc &T1,

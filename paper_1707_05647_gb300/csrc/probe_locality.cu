@@ -93,6 +93,7 @@ int main() {
             sp.N_rng = ~0ull;
             sp.P_lo = 0;
             sp.P_rng = ~(unsigned __int128)0;
+            sp.fw = -1;               // no packed-plane pre-filter
         }
         double b = 1e30, sum = 0;
         const int warm = 3, timed = 5;

@@ -40,6 +40,7 @@ const std::string &last_error();
 
 struct scr_tables {
     scr::TableDesc t[4];
+    scr::FilterPlanes F;             // packed filter planes (screen_set_filter), inside [base, base + bytes)
     void *base = nullptr;
     size_t bytes = 0;
     int H = 0, W = 0;
@@ -83,6 +84,9 @@ struct scr_ctx {
     std::map<std::string, std::pair<int, int>> tuned;   // batch shape -> (words per warp, blocks per SM)
     uint64_t *pinned = nullptr;      // 8-byte pinned slot for counts
     uint64_t *pinned_dev = nullptr;  // the same slot as the device sees it (null if not mapped)
+    // packed filter windows (kS, kQ) for the single-image builds (screen_set_filter)
+    int n_filter = 0;
+    int filter_k[scr::kMaxFilterWindows][2] = {{0, 0}, {0, 0}};
 };
 
 struct scr_batch {
@@ -140,11 +144,14 @@ int check_ctx(const scr_ctx *c);
 int validate_params(const scr_params *p);
 void bounds_for(const scr_tmpl *tm, const scr_params *p, int R, scr_bounds *b);
 int64_t table_plane_words(int H, int W);
-size_t tables_bytes(int H, int W, int sum_bits, int sq_bits);   // device bytes of one image's four tables
-// the four tables of an H x W image laid out in the device block [base, base + bytes)
+// device bytes of one image's four tables and n_filter pairs of packed filter planes
+size_t tables_bytes(int H, int W, int sum_bits, int sq_bits, int n_filter = 0);
+// the four tables (and the filter planes of the windows fk[0 .. n_filter)) of an
+// H x W image laid out in the device block [base, base + bytes)
 void layout_tables(scr_tables *t, void *base, size_t bytes, int H, int W, int sum_bits, int sq_bits,
-                   cudaStream_t st);
-int alloc_tables(scr_ctx *c, int H, int W, int sum_bits, int sq_bits, cudaStream_t st, scr_tables **out);
+                   cudaStream_t st, int n_filter = 0, const int (*fk)[2] = nullptr);
+int alloc_tables(scr_ctx *c, int H, int W, int sum_bits, int sq_bits, cudaStream_t st, scr_tables **out,
+                 int n_filter = 0, const int (*fk)[2] = nullptr);
 int run_build(scr_ctx *c, const uint8_t *img, int H, int W, int64_t pitch, scr_tables *t, cudaStream_t st);
 // as run_build with caller-provided scratch of TableScratch::bytes
 int run_build_in(scr_ctx *c, const uint8_t *img, int H, int W, int64_t pitch, scr_tables *t, void *scratch,

@@ -34,7 +34,9 @@
 //                 No block barrier and no inter-warp exchange.
 // A warp tile carries kHalo extra columns on each side so its D1 (which flows
 // in from the right) and D2 (from the left) stay exact over its core columns
-// for the kBand rows of a band.
+// for the kBand rows of a band.  When packed filter planes are requested
+// (FilterPlanes, up to two bit windows), the writer packs the same registers'
+// L1/L2 and T1/T2 bits into them and copies their rows out with the others.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -616,7 +618,20 @@ struct WriteArgs {
     uint32_t *L1lo, *L1hi, *L2lo, *L2hi, *T1lo, *T1hi, *T2lo, *T2hi;
     int64_t pL, pT;
     int aligned8;
+    FilterPlanes F;   // packed planes (pitch pL for the upright, pT for the cone planes)
 };
+
+// bits kS .. kS+15 of a and kQ .. kQ+15 of b in one word (low, high half)
+__device__ __forceinline__ uint32_t pack_window(uint32_t a, uint32_t b, int kS, int kQ) {
+    return ((a >> kS) & 0xffffu) | ((b >> kQ) << 16);
+}
+
+template <typename TS, typename TQ>
+__device__ __forceinline__ void pack8(const TS (&a)[WK], const TQ (&b)[WK], int kS, int kQ, uint32_t (&o)[WK]) {
+#pragma unroll
+    for (int k = 0; k < WK; ++k)
+        o[k] = pack_window((uint32_t)a[k], (uint32_t)b[k], kS, kQ);
+}
 
 // WK consecutive values at a 16-byte aligned word: two 16-byte stores per plane
 template <typename T>
@@ -673,12 +688,13 @@ __device__ __forceinline__ void store1(uint32_t *lo, uint32_t *hi, int64_t word,
 // took the SM slots freed during the writer's last wave and waited there, and
 // the build-then-screen sequence took 3.87 ms instead of 3.35 on the
 // 8192x8192 workload (measured).
-template <typename TS, typename TQ>
+template <typename TS, typename TQ, int NF>
 __global__ void __launch_bounds__(32) k_tab_write(const WriteArgs a) {
-    // planes of a row in obuf: L1 (lo[, hi]), L2 (lo[, hi]), T1 (lo[, hi]), T2 (lo[, hi])
+    // planes of a row in obuf: L1 (lo[, hi]), L2 (lo[, hi]), NF packed upright
+    // planes, T1 (lo[, hi]), T2 (lo[, hi]), NF packed cone planes
     constexpr int HS = sizeof(TS) == 8 ? 1 : 0, HQ = sizeof(TQ) == 8 ? 1 : 0;
-    constexpr int PL1 = 0, PL2 = PL1 + 1 + HS, PT1 = PL2 + 1 + HQ, PT2 = PT1 + 1 + HS;
-    constexpr int NPL = PT2 + 1 + HQ;
+    constexpr int PL1 = 0, PL2 = PL1 + 1 + HS, PFU = PL2 + 1 + HQ, PT1 = PFU + NF, PT2 = PT1 + 1 + HS;
+    constexpr int PFC = PT2 + 1 + HQ, NPL = PFC + NF;
     pdl_wait();
     const Geometry &g = a.g;
     const int j = blockIdx.x, i = blockIdx.y, lane = threadIdx.x;
@@ -729,19 +745,34 @@ __global__ void __launch_bounds__(32) k_tab_write(const WriteArgs a) {
             z1[k] = 0;
             z2[k] = 0;
         }
+        uint32_t z0[WK];
+#pragma unroll
+        for (int k = 0; k < WK; ++k)
+            z0[k] = 0;
         if (wL) {
             store8(a.L1lo, a.L1hi, cs + 1 + kColOffset, z1);
             store8(a.L2lo, a.L2hi, cs + 1 + kColOffset, z2);
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+                store8(a.F.up[f], a.F.up[f], cs + 1 + kColOffset, z0);
         }
         if (wT) {
             store8(a.T1lo, a.T1hi, cs + 1 + kColOffset, z1);
             store8(a.T2lo, a.T2hi, cs + 1 + kColOffset, z2);
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+                store8(a.F.cone[f], a.F.cone[f], cs + 1 + kColOffset, z0);
         }
         if (wEdge) {
             store1(a.L1lo, a.L1hi, kColOffset, (TS)0);
             store1(a.L2lo, a.L2hi, kColOffset, (TQ)0);
             store1(a.T1lo, a.T1hi, kColOffset, (TS)0);
             store1(a.T2lo, a.T2hi, kColOffset, (TQ)0);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                a.F.up[f][kColOffset] = 0;
+                a.F.cone[f][kColOffset] = 0;
+            }
         }
     }
     // pixel rows are prefetched two rows ahead
@@ -836,16 +867,33 @@ __global__ void __launch_bounds__(32) k_tab_write(const WriteArgs a) {
         if (wL) {
             put8(obuf[par][PL1], obuf[par][PL1 + HS], ob, L1a);
             put8(obuf[par][PL2], obuf[par][PL2 + HQ], ob, L2a);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                uint32_t pk[WK];
+                pack8(L1a, L2a, a.F.kS[f], a.F.kQ[f], pk);
+                put8(obuf[par][PFU + f], obuf[par][PFU + f], ob, pk);
+            }
         }
         if (wT) {
             put8(obuf[par][PT1], obuf[par][PT1 + HS], ob, T1v);
             put8(obuf[par][PT2], obuf[par][PT2 + HQ], ob, T2v);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                uint32_t pk[WK];
+                pack8(T1v, T2v, a.F.kS[f], a.F.kQ[f], pk);
+                put8(obuf[par][PFC + f], obuf[par][PFC + f], ob, pk);
+            }
         }
         if (wEdge) {   // b = 0: L is zero, T is cone(y, -1) = D1(y, -1)
             store1(a.L1lo, a.L1hi, rowL, (TS)0);
             store1(a.L2lo, a.L2hi, rowL, (TQ)0);
             store1(a.T1lo, a.T1hi, rowT, T1v[WK - 1]);
             store1(a.T2lo, a.T2hi, rowT, T2v[WK - 1]);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                a.F.up[f][rowL] = 0;
+                a.F.cone[f][rowT] = pack_window((uint32_t)T1v[WK - 1], (uint32_t)T2v[WK - 1], a.F.kS[f], a.F.kQ[f]);
+            }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
@@ -856,10 +904,16 @@ __global__ void __launch_bounds__(32) k_tab_write(const WriteArgs a) {
             if (HS) dst[k++] = a.L1hi + rowL + c0 + 1;
             dst[k++] = a.L2lo + rowL + c0 + 1;
             if (HQ) dst[k++] = a.L2hi + rowL + c0 + 1;
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+                dst[k++] = a.F.up[f] + rowL + c0 + 1;
             dst[k++] = a.T1lo + rowT + c0 + 1;
             if (HS) dst[k++] = a.T1hi + rowT + c0 + 1;
             dst[k++] = a.T2lo + rowT + c0 + 1;
             if (HQ) dst[k++] = a.T2hi + rowT + c0 + 1;
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+                dst[k++] = a.F.cone[f] + rowT + c0 + 1;
 #pragma unroll
             for (int pl = 0; pl < NPL; ++pl) {
                 const uint32_t nb = pl < PT1 ? bytesL : bytesT;
@@ -881,7 +935,7 @@ __global__ void __launch_bounds__(32) k_tab_write(const WriteArgs a) {
 template <typename TS, typename TQ>
 cudaError_t launch_all(const Geometry &g, const Scratch &s, const uint8_t *img, int64_t pitch,
                        int aligned8, const TableDesc &L1, const TableDesc &L2,
-                       const TableDesc &T1, const TableDesc &T2, cudaStream_t st) {
+                       const TableDesc &T1, const TableDesc &T2, const FilterPlanes &F, cudaStream_t st) {
     cudaError_t e;
     ReduceArgs ra{img, pitch, g, s, aligned8};
     if ((e = launch_pdl(k_tab_reduce, dim3(g.m, g.n), dim3(NT), st, ra)) != cudaSuccess)
@@ -894,8 +948,12 @@ cudaError_t launch_all(const Geometry &g, const Scratch &s, const uint8_t *img, 
     if ((e = launch_pdl(k_tab_prefix<TS, TQ>, dim3(g.n, 7), dim3(PT), st, pa)) != cudaSuccess)
         return e;
     WriteArgs wa{img, pitch, g, s, L1.lo, L1.hi, L2.lo, L2.hi, T1.lo, T1.hi, T2.lo, T2.hi,
-                 L1.pitch, T1.pitch, aligned8};
-    return launch_pdl(k_tab_write<TS, TQ>, dim3(g.mw, g.n), dim3(32), st, wa);
+                 L1.pitch, T1.pitch, aligned8, F};
+    if (F.n == 1)
+        return launch_pdl(k_tab_write<TS, TQ, 1>, dim3(g.mw, g.n), dim3(32), st, wa);
+    if (F.n == 2)
+        return launch_pdl(k_tab_write<TS, TQ, 2>, dim3(g.mw, g.n), dim3(32), st, wa);
+    return launch_pdl(k_tab_write<TS, TQ, 0>, dim3(g.mw, g.n), dim3(32), st, wa);
 }
 
 }  // namespace
@@ -908,8 +966,10 @@ size_t TableScratch::bytes(int H, int W, int sum_bits, int sq_bits) {
 
 cudaError_t launch_build_tables(const uint8_t *img, int H, int W, int64_t pitch,
                                 const TableDesc &L1, const TableDesc &L2, const TableDesc &T1,
-                                const TableDesc &T2, void *scratch, cudaStream_t st,
+                                const TableDesc &T2, const FilterPlanes &F, void *scratch, cudaStream_t st,
                                 uint64_t *launches) {
+    if (F.n < 0 || F.n > kMaxFilterWindows)
+        return cudaErrorInvalidValue;
     Geometry g(H, W);
     Scratch s;
     carve(g, L1.bits, L2.bits, &s, (char *)scratch);
@@ -917,13 +977,13 @@ cudaError_t launch_build_tables(const uint8_t *img, int H, int W, int64_t pitch,
     cudaError_t e;
     const bool s64 = L1.bits == 64, q64 = L2.bits == 64;
     if (!s64 && !q64)
-        e = launch_all<uint32_t, uint32_t>(g, s, img, pitch, aligned8, L1, L2, T1, T2, st);
+        e = launch_all<uint32_t, uint32_t>(g, s, img, pitch, aligned8, L1, L2, T1, T2, F, st);
     else if (!s64 && q64)
-        e = launch_all<uint32_t, uint64_t>(g, s, img, pitch, aligned8, L1, L2, T1, T2, st);
+        e = launch_all<uint32_t, uint64_t>(g, s, img, pitch, aligned8, L1, L2, T1, T2, F, st);
     else if (s64 && !q64)
-        e = launch_all<uint64_t, uint32_t>(g, s, img, pitch, aligned8, L1, L2, T1, T2, st);
+        e = launch_all<uint64_t, uint32_t>(g, s, img, pitch, aligned8, L1, L2, T1, T2, F, st);
     else
-        e = launch_all<uint64_t, uint64_t>(g, s, img, pitch, aligned8, L1, L2, T1, T2, st);
+        e = launch_all<uint64_t, uint64_t>(g, s, img, pitch, aligned8, L1, L2, T1, T2, F, st);
     if (launches)
         *launches += 4;
     return e;

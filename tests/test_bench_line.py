@@ -109,6 +109,10 @@ def test_traffic_record_follows_kernel_code_not_comments(tmp_path):
     rec.write_text("dram_bytes_per_launch: 123\nkernel_code_sha256: 00\n")
     assert bench.recorded_traffic(8192, 8192, root=str(tmp_path)) is None
     assert bench.recorded_traffic(8192, 8192, root=str(tmp_path / "none")) is None
+    # ... and the number of packed filter windows the run uses
+    rec.write_text(f"dram_bytes_per_launch: 7\nfilter_windows: 2\nkernel_code_sha256: {bench.kernel_code_sha256()}\n")
+    assert bench.recorded_traffic(8192, 8192, root=str(tmp_path), n_windows=2) == 7
+    assert bench.recorded_traffic(8192, 8192, root=str(tmp_path)) is None
 
 
 def test_clock_samples_are_kept_only_inside_the_window():
