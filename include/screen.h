@@ -168,8 +168,8 @@ int build_tables(scr_ctx *ctx, const uint8_t *img_dev, int32_t H, int32_t W, int
  * and lists are unchanged (bit-exact).  The planes cost 8 bytes per pixel per
  * window in the build; they pay when most candidates pass the mean test and
  * fail the variance test on a background flatter than the template (measured
- * on the 8192 x 8192, 16-scale workload: screen 2.64 -> 2.26 ms, build
- * 0.55 -> 0.78 ms); where the mean test already rejects most candidates they
+ * on the 8192 x 8192, 16-scale workload: screen 2.6 -> 1.6 ms, build
+ * 0.55 -> 0.79 ms); where the mean test already rejects most candidates they
  * only cost.  n_windows = 0 turns the planes off.  The batched and serving
  * paths ignore the setting; tables already built keep what they have.
  * SCR_EINVAL for bad counts or shifts. */

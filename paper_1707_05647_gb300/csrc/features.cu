@@ -94,9 +94,15 @@ struct Corners {
 // rounding), and the host lowered V_lo by 4 u (A 2^kQ 65535 + |V_lo|) + 1,
 // u = 2^-24, which covers every rounding here.  Candidates the window's range
 // does not cover fail the exact tests anyway, so the mask is exact.
-__device__ __forceinline__ bool filter_pass(uint32_t tot, const ScaleParam &p) {
-    const float ms = __int_as_float(__byte_perm(tot + 4u, 0x4B000000u, 0x7610));        // 2^23 + s + 4
-    const float mq = __int_as_float(__byte_perm(tot + 0x80000u, 0x4B000000u, 0x7632));  // 2^23 + q + 8
+// The caller passes tot + kFilterBias: 4 in the low half and 8 in the high
+// half, added inside the corner sum.  Adding 4 to the low half carries into
+// the high half only for s in -3..-1, which raises q + 8 by one: a larger
+// upper bound on Q, still below 2^16 (q + 8 <= 2^16 - 2 in the window's range).
+constexpr uint32_t kFilterBias = (8u << 16) + 4u;
+
+__device__ __forceinline__ bool filter_pass(uint32_t biased, const ScaleParam &p) {
+    const float ms = __int_as_float(__byte_perm(biased, 0x4B000000u, 0x7610));   // 2^23 + s + 4
+    const float mq = __int_as_float(__byte_perm(biased, 0x4B000000u, 0x7632));  // 2^23 + q + 8 (+ 1)
     const float slo = fmaxf(fmaf(p.f2S, ms, p.fS0), p.fSlo);   // max(2^kS (s - 4), S_lo)
     const float x = fmaf(p.fc, mq, p.fQ0);                     // A 2^kQ (q + 8)
     return fmaf(-slo, slo, x) >= p.fVlo;
@@ -153,15 +159,15 @@ k_screen(const __grid_constant__ ScreenArgs a) {
                             v[j][k] = ld(cf.p[k] + 32 * j);
 #pragma unroll
                     for (int j = 0; j < WPW; ++j) {
-                        const uint32_t tot =
-                            v[j][0] - v[j][1] - v[j][2] + v[j][3] + v[j][4] - v[j][5] - v[j][6] + v[j][7];
+                        const uint32_t tot = v[j][0] - v[j][1] - v[j][2] + v[j][3] + v[j][4] - v[j][5] - v[j][6] +
+                                             v[j][7] + kFilterBias;
                         keep |= (filter_pass(tot, p) ? 1u : 0u) << j;
                     }
                 } else {
                     const uint32_t span = (uint32_t)(p.x_hi - p.x_lo);
 #pragma unroll
                     for (int j = 0; j < WPW; ++j)
-                        if ((uint32_t)(x0 + 32 * j - p.x_lo) <= span && filter_pass(cf.sum(j), p))
+                        if ((uint32_t)(x0 + 32 * j - p.x_lo) <= span && filter_pass(cf.sum(j) + kFilterBias, p))
                             keep |= 1u << j;
                 }
                 // exact star sums of the candidates the filter kept
@@ -203,7 +209,7 @@ k_screen(const __grid_constant__ ScreenArgs a) {
                     }
                 }
             }
-            if (fm) {
+            if (fm && __any_sync(0xffffffffu, keep != 0)) {
                 uint32_t k2 = 0;
 #pragma unroll
                 for (int j = 0; j < WPW; ++j)
@@ -280,10 +286,12 @@ k_screen(const __grid_constant__ ScreenArgs a) {
             }
         }
         uint32_t mine = 0;
+        if (__any_sync(0xffffffffu, keep != 0)) {
 #pragma unroll
-        for (int j = 0; j < WPW; ++j) {
-            const uint32_t bits = __ballot_sync(0xffffffffu, (keep >> j) & 1u);
-            mine = lane == j ? bits : mine;
+            for (int j = 0; j < WPW; ++j) {
+                const uint32_t bits = __ballot_sync(0xffffffffu, (keep >> j) & 1u);
+                mine = lane == j ? bits : mine;
+            }
         }
         if (store_word)
             out[s * plane + lane] = mine;
