@@ -10,6 +10,7 @@ every result must be unchanged.  The plan (screen_filter_plan) is checked
 too, so the cases that must exercise the filter do.  Integer results,
 tolerance 0."""
 import dataclasses
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -143,6 +144,43 @@ def test_filtered_screen_any_windows(ctx, windows):
     got, lst, n, plan = _screen(ctx, wl, windows)
     assert all(-1 <= w < len(windows) for w in plan)
     _check_equal(got, lst, n, ref)
+
+
+# images whose star sums sit at the ends of a window's range or beyond it:
+# saturated (S = 255 A, above the mean interval), empty (S = 0, the low half
+# wraps to small negative sums), uniform noise (high variance) and a half
+# saturated, half empty image (sums across the whole range); templates are
+# taken from a planted workload so the intervals are realistic, and the
+# narrowest windows make the range conditions bind
+@pytest.mark.parametrize("kind", ["max", "zero", "uniform", "split"])
+@pytest.mark.parametrize("windows", [None, [(0, 0), (4, 12)], [(9, 16)]])
+def test_filtered_screen_extreme_images(ctx, kind, windows):
+    wl = synth.small_planted(41, H=288, r=20, n_scales=4, sum_bits=32, sq_bits=32)
+    if kind == "split":
+        img = synth.random_image(7, 288, 288, "max")
+        img[:, 144:] = 0
+    else:
+        img = synth.random_image(7, 288, 288, kind)
+    wl = dataclasses.replace(wl, image=img)
+    ref = oracle.screen_workload(wl.image, wl.template, wl.r, wl.t_min, wl.radii, wl.features, wl.tol)
+    if windows is None:
+        windows = _suggested(ctx, wl)
+    got, lst, n, plan = _screen(ctx, wl, windows)
+    assert all(-1 <= w < len(windows) for w in plan)
+    _check_equal(got, lst, n, ref)
+
+
+# wide intervals (tolerances of 90%) so that many candidates pass: the filter
+# must keep every one of them
+def test_filtered_screen_keeps_everything_that_passes(ctx):
+    wl = synth.small_planted(43, H=256, r=16, n_scales=3, sum_bits=32, sq_bits=64)
+    tol = dataclasses.replace(wl.tol, mean_rel=Fraction(9, 10), std_rel=Fraction(9, 10))
+    wl = dataclasses.replace(wl, tol=tol, features=scr.F_MEAN | scr.F_VAR)
+    ref = oracle.screen_workload(wl.image, wl.template, wl.r, wl.t_min, wl.radii, wl.features, wl.tol)
+    windows = _suggested(ctx, wl)
+    got, lst, n, plan = _screen(ctx, wl, windows)
+    _check_equal(got, lst, n, ref)
+    assert n == ref["count"] > 0
 
 
 def _config3_crop(side=1024):
