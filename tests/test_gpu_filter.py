@@ -183,6 +183,25 @@ def test_filtered_screen_keeps_everything_that_passes(ctx):
     assert n == ref["count"] > 0
 
 
+@pytest.mark.parametrize("H,W", [(40, 65535), (65535, 40)])
+def test_filtered_screen_maximum_dimension(ctx, H, W):
+    """The largest side the boundary accepts (65535) on a thin image, with
+    packed planes: keys with y or x near 2^16, the last partial warp span of
+    a row, and the packed planes' last columns."""
+    img = synth.random_image(H ^ W, H, W, "uniform")
+    r = 10
+    tm = img[:2 * r + 1, :2 * r + 1].copy()
+    wl = synth.Workload("max side", img, tm, r, [6, 9, 13, 17], 7, scr.F_MEAN | scr.F_VAR | scr.F_GRAD,
+                        synth.Tolerances(Fraction(1, 50), Fraction(1, 20), Fraction(1, 5), Fraction(4)),
+                        32, 64, (0, 0), 1.0, 0.0)
+    ref = oracle.screen_workload(wl.image, wl.template, wl.r, wl.t_min, wl.radii, wl.features, wl.tol)
+    windows = _suggested(ctx, wl)
+    got, lst, n, plan = _screen(ctx, wl, windows)
+    assert any(w >= 0 for w in plan), (windows, plan)
+    assert ref["count"] > 0
+    _check_equal(got, lst, n, ref)
+
+
 def _config3_crop(side=1024):
     """The 8192 x 8192 16-scale image cropped around its planted match."""
     wl = synth.config3()
