@@ -51,7 +51,8 @@ namespace {
 // Measured on the 8192^2, 16-scale workload: exact reads 2.61 ms with 16-warp
 // blocks against 2.67 / 2.71 / 2.79 / 2.95 ms with 8 / 4 / 2 / 1; pre-filter
 // 1.68 ms with 1-warp blocks against 1.75 / 1.76 / 1.87 / 2.26 ms with
-// 2 / 4 / 8 / 16 (4 words per warp: 2.11 ms with 4-warp blocks).
+// 2 / 4 / 8 / 16 (4 words per warp: 2.11 ms with 4-warp blocks), before the
+// bias folding and vote guards below took the 1-warp form to 1.59-1.61 ms.
 constexpr int kExactWarpsPerBlock = 16;
 constexpr int kFilterWarpsPerBlock = 1;
 
