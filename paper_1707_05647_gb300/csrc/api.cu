@@ -1927,9 +1927,17 @@ int build_plan(scr_ctx *c, scr_batch *b, const scr_tables *const *tables, int n_
             gr.Ain = (uint32_t)g.Ain;
             gr.Aring = (uint32_t)g.Aring;
             uint64_t hlo = UINT32_MAX, hhi = 0;
+            i128 vlo = (i128)INT64_MAX, vhi = (i128)INT64_MIN;
             gr.need = 0;
+            gr.all_var = 1;
             for (const BRecord &rc : kv.second) {
                 gr.need |= rc.features;
+                if (rc.features & SCR_F_VAR) {
+                    vlo = std::min<i128>(vlo, (i128)rc.V_lo);
+                    vhi = std::max<i128>(vhi, (i128)rc.V_lo + (i128)rc.V_rng);
+                } else {
+                    gr.all_var = 0;
+                }
                 if (rc.features & SCR_F_MEAN) {
                     hlo = std::min<uint64_t>(hlo, rc.S_lo);
                     hhi = std::max<uint64_t>(hhi, (uint64_t)rc.S_lo + rc.S_rng);
@@ -1940,6 +1948,12 @@ int build_plan(scr_ctx *c, scr_batch *b, const scr_tables *const *tables, int n_
             }
             gr.S_lo_hull = (uint32_t)hlo;
             gr.S_rng_hull = (uint32_t)(hhi - hlo);
+            if (kv.second.empty() || vlo > vhi)
+                gr.all_var = 0;
+            if (gr.all_var) {
+                gr.V_lo_hull = (int64_t)vlo;
+                gr.V_rng_hull = (uint64_t)(vhi - vlo);
+            }
             gr.rec0 = (int32_t)b->records.size();
             // ascending mean-interval start, so a warp stops at the first record
             // whose interval starts above every mean it holds

@@ -191,6 +191,28 @@ __global__ void __launch_bounds__(32 * kBatchWarps, (WPW >= 8 ? 3 : 4)) k_batch(
 #pragma unroll
             for (int j = 0; j < WPW; ++j)
                 V[j] = N[j] = 0, ubits[j] = 0;
+            // when every record tests the variance, a position whose V lies outside
+            // the union of their variance intervals fails them all: reject it
+            // before the walk over the records (on a background flatter than the
+            // templates this ends most positions here)
+            if (__ldg(&gp->all_var)) {
+                const uint32_t *L2 = (const uint32_t *)__ldg((const unsigned long long *)&ip->L2);
+                const uint32_t *T2 = (const uint32_t *)__ldg((const unsigned long long *)&ip->T2);
+                uint64_t Q[WPW];
+                corner_sums64<WPW>(L2 + e, T2 + e, oL, oT, alive, Q);
+                const uint64_t A = __ldg(&gp->A);
+                const uint64_t vlo = (uint64_t)__ldg((const long long *)&gp->V_lo_hull);
+                const uint64_t vrng = __ldg((const unsigned long long *)&gp->V_rng_hull);
+#pragma unroll
+                for (int j = 0; j < WPW; ++j) {
+                    V[j] = A * Q[j] - (uint64_t)S[j] * S[j];
+                    if ((V[j] - vlo) > vrng)
+                        alive &= ~(1u << j);
+                }
+                haveV = true;
+                if (!__any_sync(0xffffffffu, alive))
+                    continue;
+            }
             // the warp's range of means among alive positions: records are sorted
             // by interval start (records without a mean test start at 0 and span
             // everything), so the walk skips disjoint intervals and stops early

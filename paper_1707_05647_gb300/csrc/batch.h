@@ -28,6 +28,9 @@ struct BGroup {                        // one (image, star radius R) and the rec
     uint32_t S_lo_hull, S_rng_hull;    // union of the records' mean intervals
     uint32_t need;                     // features any record of the group tests
     int32_t rec0, rec1;                // records [rec0, rec1)
+    uint32_t all_var;                  // 1: every record tests the variance
+    int64_t V_lo_hull;                 // with all_var: union of the records' variance
+    uint64_t V_rng_hull;               //   intervals, (V - V_lo_hull) <= V_rng_hull
 };
 
 struct BRecord {                       // one (pair, scale) test
