@@ -163,8 +163,10 @@ int build_tables(scr_ctx *ctx, const uint8_t *img_dev, int32_t H, int32_t W, int
  * the candidates whose variance is certainly below the variance interval,
  * and read the exact corners only where a candidate is left.  Each scale uses
  * the narrowest window whose range holds every candidate that can pass its
- * mean and variance intervals; scales with no such window, screens without
- * the variance test and the Prewitt variant read exact corners only.  Masks
+ * mean and variance intervals and that is at most 3 bits coarser than the
+ * scale's smallest such shifts (coarser ones reject little); scales with no
+ * such window, screens without the variance test and the Prewitt variant
+ * read exact corners only.  Masks
  * and lists are unchanged (bit-exact).  The planes cost 8 bytes per pixel per
  * window in the build; they pay when most candidates pass the mean test and
  * fail the variance test on a background flatter than the template (measured
@@ -176,11 +178,12 @@ int build_tables(scr_ctx *ctx, const uint8_t *img_dev, int32_t H, int32_t W, int
 int screen_set_filter(scr_ctx *ctx, int32_t n_windows, const int32_t *windows);
 
 /* Suggested windows for screening with template tm and parameters p (host
- * computation): for every scale the smallest shifts whose range holds the
- * candidates that can pass; the first window fits every scale, and when
- * max_windows >= 2 and some scale fits shifts 3 smaller, a second window 3
- * smaller is returned first.  Writes *n_windows pairs (0 when the variance
- * test is off). */
+ * computation).  For every scale, the smallest shifts whose range holds the
+ * candidates that can pass.  The widest window fits every scale; when
+ * max_windows >= 2 and it is more than 3 bits coarser than some scale's
+ * smallest shifts, a second window, the smallest that fits all those scales,
+ * is returned first.  Writes *n_windows pairs (0 when the variance test is
+ * off). */
 int screen_filter_windows(const scr_tmpl *tm, const scr_params *p, int32_t max_windows, int32_t *windows,
                           int32_t *n_windows);
 

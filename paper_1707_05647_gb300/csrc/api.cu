@@ -478,7 +478,21 @@ static bool window_fits(const FilterRange &r, int kS, int kQ) {
     return r.usable && (i128)r.S_hi <= ((i128)1 << kS) * (65536 - 8) && r.Q_hi <= ((i128)1 << kQ) * (65536 - 16);
 }
 
+// A window more than this many bits coarser than the narrowest usable shifts
+// rejects little (measured on the 8192 x 8192, 16-scale workload: 99% of
+// candidates at up to 3 bits, 3-78% at 4), so such a scale reads exact corners.
+constexpr int kFilterSlackBits = 3;
+
 // smallest shifts (kS, kQ) at which a window is usable for this range; false if none
+static bool min_window(const FilterRange &r, int *kS, int *kQ);
+
+// window f of F usable for range r and at most kFilterSlackBits coarser than its narrowest shifts
+static bool window_suits(const FilterRange &r, const FilterPlanes &F, int f) {
+    int ks = 0, kq = 0;
+    return window_fits(r, F.kS[f], F.kQ[f]) && min_window(r, &ks, &kq) && F.kS[f] <= ks + kFilterSlackBits &&
+           F.kQ[f] <= kq + kFilterSlackBits;
+}
+
 static bool min_window(const FilterRange &r, int *kS, int *kQ) {
     if (!r.usable)
         return false;
@@ -620,7 +634,7 @@ int fill_screen_args(const scr_tables *t, const scr_tmpl *tm, const scr_params *
         const FilterRange r = filter_range(p, b, sp.A);
         int best = -1;
         for (int f = 0; f < t->F.n; ++f)
-            if (window_fits(r, t->F.kS[f], t->F.kQ[f]) &&
+            if (window_suits(r, t->F, f) &&
                 (best < 0 || t->F.kS[f] < t->F.kS[best] ||
                  (t->F.kS[f] == t->F.kS[best] && t->F.kQ[f] < t->F.kQ[best])))
                 best = f;
@@ -822,21 +836,23 @@ int screen_filter_windows(const scr_tmpl *tm, const scr_params *p, int32_t max_w
     }
     if (need.empty() || max_windows == 0)
         return SCR_OK;
-    // one window wide enough for every scale; a second one 3 bits narrower for
-    // the scales that fit it (a window loses little precision on scales up to
-    // 3 bits below it: measured on the 8192 x 8192, 16-scale workload)
+    // the widest window fits every scale; a second one, the smallest that fits
+    // every scale the first would serve more than kFilterSlackBits too coarse
     windows[0] = hs;
     windows[1] = hq;
     *n_windows = 1;
-    if (max_windows >= 2 && hs >= 3 && hq >= 3) {
-        bool some = false;
+    if (max_windows >= 2) {
+        int ns = -1, nq = -1;
         for (const auto &k : need)
-            some |= k.first <= hs - 3 && k.second <= hq - 3;
-        if (some) {
+            if (hs > k.first + kFilterSlackBits || hq > k.second + kFilterSlackBits) {
+                ns = std::max(ns, k.first);
+                nq = std::max(nq, k.second);
+            }
+        if (ns >= 0 && (ns < hs || nq < hq)) {
             windows[2] = windows[0];
             windows[3] = windows[1];
-            windows[0] = hs - 3;
-            windows[1] = hq - 3;
+            windows[0] = ns;
+            windows[1] = nq;
             *n_windows = 2;
         }
     }
