@@ -674,8 +674,9 @@ def rooflines(wl, k3_s, tab_s, n_surv, n_windows=0):
                            f"{alg / ncand:.2f} B/candidate"}
     traffic = recorded_traffic(H, W, n_windows=n_windows)
     if n_windows:
-        binding = ("on-chip: instruction issue and the integer ALU pipe of the packed-plane pre-filter; the "
-                   "packed planes are read from DRAM about once and re-read across scales from L2")
+        binding = ("on-chip: the latency of the L2-served packed-plane reads (long-scoreboard stalls), with "
+                   "instruction issue and the L1 data pipe near 62%; the packed planes are read from DRAM about "
+                   "once and re-read across scales from L2")
     else:
         binding = ("on-chip: the L1 data pipe and instruction issue; the tables are read from DRAM about "
                    "once (low 32-bit planes) and re-read across scales from L2")
