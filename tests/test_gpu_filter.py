@@ -202,6 +202,39 @@ def test_filtered_screen_maximum_dimension(ctx, H, W):
     _check_equal(got, lst, n, ref)
 
 
+@pytest.mark.parametrize("seed", [93, 95])
+@pytest.mark.parametrize("kind", ["plain", "split"])
+@pytest.mark.parametrize("windows", [None, [(9, 16)]])
+def test_filtered_screen_largest_radius(ctx, seed, kind, windows):
+    """Stars up to radius 181, the largest the boundary accepts (pooled area
+    A = 131058, where the filter's constants span their widest range), on a
+    400 x 700 image whose 256-candidate warp spans are fully valid at every
+    scale, so the batched pre-filter path runs.  The template samples the
+    image centre at stride 9, so the large stars' means and variances fall
+    inside its intervals: some candidates pass at every scale.  The split
+    image inverts the right part, which moves sums across the range."""
+    H, W = 400, 700
+    img = synth.random_image(seed, H, W, "blobs")
+    cy, cx = H // 2, W // 2
+    tm = np.ascontiguousarray(img[cy - 180:cy + 181:9, cx - 180:cx + 181:9])
+    if kind == "split":
+        img = img.copy()
+        img[:, cx + 60:] = 255 - img[:, cx + 60:]
+    bits = (32, 32) if seed % 2 else (64, 64)
+    wl = synth.Workload("largest radius", img, tm, 20, [120, 150, 181], 10,
+                        scr.F_MEAN | scr.F_VAR | scr.F_GRAD,
+                        synth.Tolerances(Fraction(1, 20), Fraction(1, 10), Fraction(1, 2), Fraction(8)),
+                        bits[0], bits[1], (cy, cx), 9.0, 0.0)
+    ref = oracle.screen_workload(wl.image, wl.template, wl.r, wl.t_min, wl.radii, wl.features, wl.tol)
+    if windows is None:
+        windows = _suggested(ctx, wl)
+    got, lst, n, plan = _screen(ctx, wl, windows)
+    assert plan[-1] >= 0, (windows, plan)                   # R = 181 pre-filters
+    per_scale = [int(((ref["list"] >> np.uint64(48)) == s).sum()) for s in range(3)]
+    assert min(per_scale) > 0, per_scale
+    _check_equal(got, lst, n, ref)
+
+
 def _config3_crop(side=1024):
     """The 8192 x 8192 16-scale image cropped around its planted match."""
     wl = synth.config3()
