@@ -182,8 +182,10 @@ int screen_set_filter(scr_ctx *ctx, int32_t n_windows, const int32_t *windows);
  * candidates that can pass.  The widest window fits every scale; when
  * max_windows >= 2 and it is more than 3 bits coarser than some scale's
  * smallest shifts, a second window, the smallest that fits all those scales,
- * is returned first.  Writes *n_windows pairs (0 when the variance test is
- * off). */
+ * is returned first.  windows (host) must hold 2 * min(max_windows, 2)
+ * int32 values; *n_windows (kS, kQ) pairs are written, 0 when the variance
+ * test is off or max_windows is 0.  SCR_EINVAL for a null argument, a negative
+ * max_windows or invalid parameters. */
 int screen_filter_windows(const scr_tmpl *tm, const scr_params *p, int32_t max_windows, int32_t *windows,
                           int32_t *n_windows);
 
