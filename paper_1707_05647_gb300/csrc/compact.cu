@@ -154,24 +154,55 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const uint32_t *mask, uint
         uint32_t tot;
         uint64_t pos = offsets[b] + block_excl_scan(c, sh, tot);
         __syncthreads();
-        if (c == 0 || pos >= cap)
+        if (__all_sync(0xffffffffu, c == 0 || pos >= cap))   // warp-uniform: nothing to write
             continue;
         // (scale, row, word) of the thread's first word by division, then by
         // stepping through its consecutive words
-        uint64_t sc = first / planeWords;
-        const uint32_t rem = (uint32_t)(first - sc * planeWords);
-        uint32_t y = rem / (uint32_t)rowWords, xw = rem - y * (uint32_t)rowWords;
+        uint64_t sc = 0;
+        uint32_t y = 0, xw = 0;
+        if (c != 0) {
+            sc = first / planeWords;
+            const uint32_t rem = (uint32_t)(first - sc * planeWords);
+            y = rem / (uint32_t)rowWords;
+            xw = rem - y * (uint32_t)rowWords;
+        }
+        // Word slot k of every lane in turn.  Survivors cluster, so a slot often
+        // holds one or a few dense words: then the warp writes each such word's
+        // bits together, one bit per lane (the key's slot from a popcount of the
+        // lower bits), instead of waiting on the lane that walks the most bits.
+        const int lane = threadIdx.x & 31;
 #pragma unroll
         for (int k = 0; k < kWordsPerThread; ++k) {
-            uint32_t bits = w[k];
+            const uint32_t wk = w[k];
+            const uint32_t nz = __ballot_sync(0xffffffffu, wk != 0);
             const uint64_t keyb = (sc << 48) | ((uint64_t)y << 24) | ((uint64_t)xw * 32);
-            while (bits) {
-                const int bit = __ffs(bits) - 1;
-                bits &= bits - 1;
-                if (pos < cap)
-                    list[pos] = keyb + bit;
-                ++pos;
+            if (nz) {   // warp-uniform
+                const uint32_t mx = __reduce_max_sync(0xffffffffu, (uint32_t)__popc(wk));
+                if (2 * mx > 3 * (uint32_t)__popc(nz)) {   // warp-uniform
+                    for (uint32_t m = nz; m; m &= m - 1) {
+                        const int src = __ffs(m) - 1;
+                        const uint32_t word = __shfl_sync(0xffffffffu, wk, src);
+                        const uint64_t kb = __shfl_sync(0xffffffffu, keyb, src);
+                        const uint64_t base = __shfl_sync(0xffffffffu, pos, src);
+                        if ((word >> lane) & 1u) {
+                            const uint64_t at = base + __popc(word & ((1u << lane) - 1u));
+                            if (at < cap)
+                                list[at] = kb + lane;
+                        }
+                    }
+                } else {
+                    uint32_t bits = wk;
+                    uint64_t at = pos;
+                    while (bits) {
+                        const int bit = __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        if (at < cap)
+                            list[at] = keyb + bit;
+                        ++at;
+                    }
+                }
             }
+            pos += __popc(wk);
             if (++xw == (uint32_t)rowWords) {
                 xw = 0;
                 if (++y == (uint32_t)H) {
