@@ -358,19 +358,25 @@ __device__ __forceinline__ uint32_t sort_digit(uint64_t k, const SortArgs &a, in
     return (uint32_t)(c >> shift) & 255u;
 }
 
-// hist[d * ntiles + t] = keys of tile t with digit d
+// hist[d * ntiles + t] = keys of tile t with digit d.  Lanes of a warp that
+// hold the same digit add their count with one atomic: in the passes over the
+// high (pair) bits nearly every key of a tile has the same digit.
 __global__ void __launch_bounds__(RS_T) k_rs_hist(const SortArgs a, int shift) {
     pdl_begin();
     __shared__ uint32_t h[256];
     const uint64_t n = sort_count(a);
     const uint64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
+    const uint32_t lt_mask = (1u << (threadIdx.x & 31)) - 1u;
     for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         h[threadIdx.x] = 0;
         __syncthreads();
+#pragma unroll
         for (int k = 0; k < RS_R; ++k) {
             const uint64_t i = t * RS_TILE + (uint64_t)k * RS_T + threadIdx.x;
-            if (i < n)
-                atomicAdd(&h[sort_digit(a.src[i], a, shift)], 1u);
+            const uint32_t d = i < n ? sort_digit(a.src[i], a, shift) : 256u + (threadIdx.x & 31);
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            if (d < 256u && (peers & lt_mask) == 0)   // lowest lane of its digit group
+                atomicAdd(&h[d], (uint32_t)__popc(peers));
         }
         __syncthreads();
         a.hist[(uint64_t)threadIdx.x * ntiles + t] = h[threadIdx.x];
@@ -508,12 +514,20 @@ __global__ void __launch_bounds__(RS_T) k_rs_down(const SortArgs a) {
 
 // Stable scatter of one tile: warp w owns keys [w * 256, w * 256 + 256) of the
 // tile (in order), counts them per digit, the warps' counts are scanned per
-// digit, and each warp then writes its keys at the digit's running position.
+// digit, and each warp puts its keys at the digit's running position in a copy
+// of the tile sorted by digit in shared memory.  The block then writes that
+// copy out, consecutive threads to consecutive addresses within each digit's
+// run, instead of one scattered 8-byte store per key (measured on the
+// 64-image x 256-template batch: 12.4 ms per pass over 1.27e9 keys before).
 __global__ void __launch_bounds__(RS_T) k_rs_scatter(const SortArgs a, int shift) {
     pdl_begin();
     constexpr int NW = RS_T / 32;
     __shared__ uint32_t wofs[NW][256];
     __shared__ uint64_t start[256];
+    __shared__ uint32_t lofs[256];          // first slot of each digit in the sorted tile
+    __shared__ uint32_t ssh[RS_T / 32];
+    __shared__ uint64_t skey[RS_TILE];      // the tile, sorted by digit (stable)
+    __shared__ uint8_t sdig[RS_TILE];
     const uint64_t n = sort_count(a);
     const uint64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -550,6 +564,8 @@ __global__ void __launch_bounds__(RS_T) k_rs_scatter(const SortArgs a, int shift
             wofs[q][t] = acc;
             acc += c;
         }
+        uint32_t ntile;
+        lofs[t] = block_exscan256(acc, ssh, ntile);   // acc: the tile's keys with digit t
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < RS_R; ++r) {
@@ -557,12 +573,19 @@ __global__ void __launch_bounds__(RS_T) k_rs_scatter(const SortArgs a, int shift
             uint32_t before = 0;
             if (d < 256u) {
                 before = wofs[w][d];
-                a.dst[start[d] + before + __popc(peers[r] & lt_mask)] = key[r];
+                const uint32_t at = lofs[d] + before + __popc(peers[r] & lt_mask);
+                skey[at] = key[r];
+                sdig[at] = (uint8_t)d;
             }
             __syncwarp();
             if (d < 256u && (peers[r] & lt_mask) == 0)
                 wofs[w][d] = before + __popc(peers[r]);
             __syncwarp();
+        }
+        __syncthreads();
+        for (uint32_t i = t; i < ntile; i += RS_T) {
+            const uint32_t d = sdig[i];
+            a.dst[start[d] + (i - lofs[d])] = skey[i];
         }
         __syncthreads();
     }
