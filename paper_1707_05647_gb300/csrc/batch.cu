@@ -359,8 +359,9 @@ __device__ __forceinline__ uint32_t sort_digit(uint64_t k, const SortArgs &a, in
 }
 
 // hist[d * ntiles + t] = keys of tile t with digit d (one shared-memory atomic
-// per key: aggregating equal digits of a warp with __match_any_sync first took
-// 4.8 ms per pass over 1.27e9 keys against 3.3 ms)
+// per key).  Measured per pass over 1.27e9 keys: 3.3 ms; aggregating equal
+// digits of a warp with __match_any_sync first, 4.8 ms; one atomic of 32 when
+// __match_all_sync finds the warp's digits equal, 3.6 ms.
 __global__ void __launch_bounds__(RS_T) k_rs_hist(const SortArgs a, int shift) {
     pdl_begin();
     __shared__ uint32_t h[256];
