@@ -1487,7 +1487,7 @@ int screen_host(scr_ctx *c, const uint8_t *img_host, int32_t H, int32_t W, int64
         if (!rc) {
             uint64_t n = 0;
             cudaError_t e = launch_copy_keys((const uint64_t *)list.p, cnt_dev, list_cap, list_map, c->pinned_dev,
-                                             st, &n);
+                                             st, &n, kCopyBlocksSync);
             c->launches += n;
             if (e == cudaSuccess)
                 e = cudaStreamSynchronize(st);
@@ -1757,7 +1757,8 @@ int frames_submit(scr_frames *f, const uint8_t *img_host, int64_t pitch, uint64_
     if (e == cudaSuccess)
         e = cudaStreamWaitEvent(f->st_out, f->ev_cmp[k], 0);
     if (e == cudaSuccess)
-        e = launch_copy_keys(keys, cnt, f->list_cap, list_map, f->cnt_host_dev + k, f->st_out, &n);
+        e = launch_copy_keys(keys, cnt, f->list_cap, list_map, f->cnt_host_dev + k, f->st_out, &n,
+                             kCopyBlocksOverlapped);
     if (e == cudaSuccess)
         e = cudaEventRecord(f->ev_done[k], f->st_out);
     c->launches += n;

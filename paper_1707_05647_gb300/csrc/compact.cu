@@ -230,10 +230,11 @@ __global__ void __launch_bounds__(kThreads) k_copy_keys(const uint64_t *src, con
 }  // namespace
 
 cudaError_t launch_copy_keys(const uint64_t *src, const uint64_t *count, uint64_t cap, uint64_t *dst,
-                             uint64_t *count_out, cudaStream_t st, uint64_t *launches) {
+                             uint64_t *count_out, cudaStream_t st, uint64_t *launches, int blocks) {
     if (launches)
         *launches += 1;
-    return launch_pdl(k_copy_keys, dim3(152 * 4), dim3(kThreads), st, src, count, cap, dst, count_out);
+    return launch_pdl(k_copy_keys, dim3(blocks > 0 ? blocks : 1), dim3(kThreads), st, src, count, cap, dst,
+                      count_out);
 }
 
 size_t compact_scratch_bytes(uint64_t total_words) {

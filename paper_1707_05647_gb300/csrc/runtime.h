@@ -206,7 +206,15 @@ void destroy_frames(scr_ctx *c);
 
 namespace scr {
 // Copy min(*count, cap) keys of a device list to dst and *count to count_out,
-// both host memory the device can address (one kernel; compact.cu).
+// both host memory the device can address (one kernel of `blocks` blocks;
+// compact.cu).  A copy on the critical path uses kCopyBlocksSync; one that
+// overlaps other work (the frame pipeline's, during the next frame) uses
+// kCopyBlocksOverlapped, so that it holds few SM slots while the host link,
+// not the SMs, sets its pace.  Measured on the 8192 x 8192 pipeline (2.2 M
+// keys per frame): 2.51 ms per frame with 608 blocks, 2.48 with 152, 2.43
+// with 38; one synchronous call took 2.875 ms with 608 and 2.883 with 38.
+constexpr int kCopyBlocksSync = 608;
+constexpr int kCopyBlocksOverlapped = 38;
 cudaError_t launch_copy_keys(const uint64_t *src, const uint64_t *count, uint64_t cap, uint64_t *dst,
-                             uint64_t *count_out, cudaStream_t st, uint64_t *launches);
+                             uint64_t *count_out, cudaStream_t st, uint64_t *launches, int blocks);
 }  // namespace scr
